@@ -1,0 +1,233 @@
+"""FP64 CPU oracle for the CT volume ray caster -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package. The product path (``paper_2005_01442_gb300``) never imports it, and the
+two share no code: this wrapper loads ``liborc.so`` built from ``vrc_oracle.c`` with gcc.
+
+Functions mirror the steps of the method (Sec. "Methodology" of the paper: ray casting with
+cubic-spline resampling, post-classification, block decomposition with empty space leaping
+and early ray termination). See ``vrc_oracle.c`` for the readings taken where the paper is
+silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vrc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+
+DTYPES = {np.dtype(np.uint16): 0, np.dtype(np.int16): 1, np.dtype(np.float32): 2}
+
+
+class Camera(C.Structure):
+    _fields_ = [("ortho", C.c_int), ("eye", C.c_float * 3), ("center", C.c_float * 3),
+                ("up", C.c_float * 3), ("fovy_deg", C.c_float), ("ortho_extent", C.c_float * 2),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class Params(C.Structure):
+    _fields_ = [("step", C.c_double), ("ert", C.c_double), ("brick", C.c_int), ("pad", C.c_int)]
+
+
+class Ball(C.Structure):
+    _fields_ = [("enabled", C.c_int), ("c", C.c_double * 3), ("r", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liborc.so (gcc, -O2, OpenMP, no fast-math, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.orc_bspline_weights.argtypes = [C.c_double, dp]
+        L.orc_bspline_dweights.argtypes = [C.c_double, dp]
+        L.orc_sample.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double]
+        L.orc_sample.restype = C.c_double
+        L.orc_classify.argtypes = [C.c_double, vp, C.c_double, C.c_double, dp]
+        L.orc_ray.argtypes = [C.POINTER(Camera), vp, ip, ip, dp, dp, dp, dp]
+        L.orc_ray.restype = C.c_int
+        L.orc_bricks.argtypes = [vp, ip, ip, ip, ip, ip, vp, vp]
+        L.orc_occupancy.argtypes = [vp, vp, ip, C.c_long, vp, C.c_float, C.c_float, vp]
+        L.orc_render.argtypes = [vp, ip, ip, ip, ip, vp, C.c_double, C.c_double,
+                                 C.POINTER(Camera), C.POINTER(Params), vp, C.POINTER(Ball), vp,
+                                 C.c_long, vp, vp, vp]
+        L.orc_render_grad.argtypes = [vp, ip, ip, ip, ip, vp, C.c_double, C.c_double,
+                                      C.POINTER(Camera), C.POINTER(Params), vp, vp, C.c_long,
+                                      vp, vp, vp]
+        L.orc_set_threads.argtypes = [ip]
+        L.orc_get_threads.restype = ip
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _cam(cam) -> Camera:
+    c = Camera()
+    c.ortho = int(cam.ortho)
+    c.eye[:] = [float(x) for x in cam.eye]
+    c.center[:] = [float(x) for x in cam.center]
+    c.up[:] = [float(x) for x in cam.up]
+    c.fovy_deg = float(cam.fovy_deg)
+    c.ortho_extent[:] = [float(x) for x in cam.ortho_extent]
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def bspline_weights(f: float) -> np.ndarray:
+    w = (C.c_double * 4)()
+    lib().orc_bspline_weights(float(f), w)
+    return np.array(w[:])
+
+
+def bspline_dweights(f: float) -> np.ndarray:
+    w = (C.c_double * 4)()
+    lib().orc_bspline_dweights(float(f), w)
+    return np.array(w[:])
+
+
+def sample(vol: np.ndarray, p) -> float:
+    """Cubic B-spline value of `vol` (nz, ny, nx) at the point p = (x, y, z)."""
+    vol = np.ascontiguousarray(vol)
+    nz, ny, nx = vol.shape
+    return float(lib().orc_sample(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, *map(float, p)))
+
+
+def classify(s: float, tf: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    tf = np.ascontiguousarray(tf, np.float32)
+    out = (C.c_double * 4)()
+    lib().orc_classify(float(s), _ptr(tf), float(lo), float(hi), out)
+    return np.array(out[:])
+
+
+def ray(cam, dims, px: int, py: int):
+    """(origin, direction, t_in, t_out, hit) of the ray through pixel (px, py)."""
+    o = (C.c_double * 3)()
+    d = (C.c_double * 3)()
+    t0 = C.c_double()
+    t1 = C.c_double()
+    dm = np.asarray(dims, np.int32)
+    hit = lib().orc_ray(C.byref(_cam(cam)), _ptr(dm), int(px), int(py), o, d, C.byref(t0),
+                        C.byref(t1))
+    return np.array(o[:]), np.array(d[:]), t0.value, t1.value, bool(hit)
+
+
+def bricks(vol: np.ndarray, B: int):
+    """Per-brick (min, max) over the apron box, arrays of shape (nbz, nby, nbx)."""
+    vol = np.ascontiguousarray(vol)
+    nz, ny, nx = vol.shape
+    nb = tuple((n + B - 1) // B for n in (nz, ny, nx))
+    mn = np.empty(nb, vol.dtype)
+    mx = np.empty(nb, vol.dtype)
+    rc = lib().orc_bricks(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, int(B), _ptr(mn), _ptr(mx))
+    if rc != 0:
+        raise ValueError(f"orc_bricks failed ({rc})")
+    return mn, mx
+
+
+def occupancy(mn: np.ndarray, mx: np.ndarray, tf: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    mn = np.ascontiguousarray(mn)
+    mx = np.ascontiguousarray(mx)
+    tf = np.ascontiguousarray(tf, np.float32)
+    occ = np.empty(mn.shape, np.uint8)
+    rc = lib().orc_occupancy(_ptr(mn), _ptr(mx), DTYPES[mn.dtype], mn.size, _ptr(tf),
+                             float(lo), float(hi), _ptr(occ))
+    if rc != 0:
+        raise ValueError(f"orc_occupancy failed ({rc})")
+    return occ
+
+
+def _pix(pixels):
+    if pixels is None:
+        return None, 0
+    p = np.ascontiguousarray(np.asarray(pixels, np.int32).reshape(-1, 2))
+    return p, p.shape[0]
+
+
+def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
+           return_margin=False, return_counts=False):
+    """FP64 render. Returns float64 (H, W, 4) (or (npix, 4) for a pixel list), plus the ERT
+    margins and the (nominal, executed) sample counts when asked."""
+    vol = np.ascontiguousarray(vol)
+    tf = np.ascontiguousarray(tf, np.float32)
+    nz, ny, nx = vol.shape
+    occ = None
+    if brick:
+        mn, mx = bricks(vol, brick)
+        occ = occupancy(mn, mx, tf, lo, hi)
+    pix, npix = _pix(pixels)
+    n = npix if pix is not None else cam.width * cam.height
+    out = np.zeros((n, 4), np.float64)
+    margin = np.empty(n, np.float64) if return_margin else None
+    counts = np.zeros(2, np.int64)
+    par = Params(float(step), float(ert), int(brick), 0)
+    b = None
+    if ball is not None:
+        b = Ball(1, (C.c_double * 3)(*map(float, ball[0])), float(ball[1]))
+    rc = lib().orc_render(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
+                          float(hi), C.byref(_cam(cam)), C.byref(par), _ptr(occ),
+                          C.byref(b) if b is not None else None, _ptr(pix), npix, _ptr(out),
+                          _ptr(margin), _ptr(counts))
+    if rc != 0:
+        raise ValueError(f"orc_render failed ({rc})")
+    img = out if pix is not None else out.reshape(cam.height, cam.width, 4)
+    res = [img]
+    if return_margin:
+        res.append(margin if pix is not None else margin.reshape(cam.height, cam.width))
+    if return_counts:
+        res.append((int(counts[0]), int(counts[1])))
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, want_vol=True):
+    """Reverse-mode gradient of sum(g * image) w.r.t. the TF (256, 4) and the voxels
+    (vol.shape), in float64."""
+    vol = np.ascontiguousarray(vol)
+    tf = np.ascontiguousarray(tf, np.float32)
+    nz, ny, nx = vol.shape
+    occ = None
+    if brick:
+        mn, mx = bricks(vol, brick)
+        occ = occupancy(mn, mx, tf, lo, hi)
+    pix, npix = _pix(pixels)
+    g = np.ascontiguousarray(np.asarray(g, np.float64).reshape(-1, 4))
+    gtf = np.zeros((256, 4), np.float64)
+    gvol = np.zeros(vol.shape, np.float64) if want_vol else None
+    par = Params(float(step), float(ert), int(brick), 0)
+    rc = lib().orc_render_grad(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
+                               float(hi), C.byref(_cam(cam)), C.byref(par), _ptr(occ),
+                               _ptr(pix), npix, _ptr(g), _ptr(gtf), _ptr(gvol))
+    if rc != 0:
+        raise ValueError(f"orc_render_grad failed ({rc})")
+    return gtf, gvol

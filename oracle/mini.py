@@ -1,0 +1,125 @@
+"""Brute-force NumPy FP64 ray caster for tiny inputs -- test infrastructure only.
+
+An independent second statement of the same reading as ``vrc_oracle.c``, written differently
+on purpose so that the two can pin each other:
+
+* the resampled value is the full kernel sum  s(p) = sum_m beta3(p - m) Vext[m]  over every
+  grid point m of the volume extended by edge replication, with beta3 the centred cubic
+  B-spline written piecewise (2/3 - t^2 + |t|^3/2 on |t| < 1, (2 - |t|)^3 / 6 on 1 <= |t| < 2);
+* the camera is a matrix (right, up, forward) applied to screen offsets;
+* the ray-box range uses a vectorised slab test;
+* compositing runs over the midpoints of the step partition of [t_in, t_out].
+
+Only usable for volumes of a few thousand voxels and images of a few dozen pixels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PAD = 3
+
+
+def beta3(t):
+    t = np.abs(np.asarray(t, np.float64))
+    out = np.zeros_like(t)
+    a = t < 1.0
+    b = (t >= 1.0) & (t < 2.0)
+    out[a] = 2.0 / 3.0 - t[a] ** 2 + 0.5 * t[a] ** 3
+    out[b] = (2.0 - t[b]) ** 3 / 6.0
+    return out
+
+
+class Field:
+    """Volume extended by edge replication; s(p) by the full kernel sum."""
+
+    def __init__(self, vol):
+        v = np.asarray(vol, np.float64)
+        self.ext = np.pad(v, PAD, mode="edge")  # (nz+6, ny+6, nx+6)
+        nz, ny, nx = v.shape
+        self.gx = np.arange(-PAD, nx + PAD, dtype=np.float64)
+        self.gy = np.arange(-PAD, ny + PAD, dtype=np.float64)
+        self.gz = np.arange(-PAD, nz + PAD, dtype=np.float64)
+
+    def __call__(self, p):
+        bx = beta3(p[0] - self.gx)
+        by = beta3(p[1] - self.gy)
+        bz = beta3(p[2] - self.gz)
+        return float(np.einsum("k,j,i,kji->", bz, by, bx, self.ext))
+
+
+def camera_rays(cam, dims):
+    """Per-pixel (origin, unit direction) arrays of shape (H, W, 3)."""
+    eye = np.asarray(cam.eye, np.float64)
+    fwd = np.asarray(cam.center, np.float64) - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, np.asarray(cam.up, np.float64))
+    right /= np.linalg.norm(right)
+    upv = np.cross(right, fwd)
+    M = np.stack([right, upv, fwd], axis=1)  # columns
+    W, H = cam.width, cam.height
+    ix = (np.arange(W) + 0.5) / W * 2.0 - 1.0
+    iy = 1.0 - (np.arange(H) + 0.5) / H * 2.0
+    sx, sy = np.meshgrid(ix, iy)  # (H, W)
+    if cam.ortho:
+        off = np.stack([sx * cam.ortho_extent[0] / 2, sy * cam.ortho_extent[1] / 2,
+                        np.zeros_like(sx)], -1)
+        org = eye + off @ M.T
+        dirs = np.broadcast_to(fwd, org.shape).copy()
+    else:
+        th = math.tan(math.radians(cam.fovy_deg) / 2)
+        scr = np.stack([sx * th * W / H, sy * th, np.ones_like(sx)], -1)
+        dirs = scr @ M.T
+        dirs /= np.linalg.norm(dirs, axis=-1, keepdims=True)
+        org = np.broadcast_to(eye, dirs.shape).copy()
+    return org, dirs
+
+
+def box_range(org, d, dims):
+    lo = -0.5 * np.ones(3)
+    hi = np.asarray(dims, np.float64) - 0.5
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (lo - org) / d
+        tb = (hi - org) / d
+    tmin = np.where(d != 0, np.minimum(ta, tb), np.where((org >= lo) & (org <= hi), -np.inf, np.inf))
+    tmax = np.where(d != 0, np.maximum(ta, tb), np.where((org >= lo) & (org <= hi), np.inf, -np.inf))
+    return max(0.0, tmin.max()), tmax.min()
+
+
+def tf_lookup(s, tf, lo, hi):
+    u = min(max((s - lo) / (hi - lo) * 255.0, 0.0), 255.0)
+    k = np.arange(256, dtype=np.float64)
+    return np.array([np.interp(u, k, tf[:, c].astype(np.float64)) for c in range(4)])
+
+
+def render(vol, tf, lo, hi, cam, step, ert=1.0):
+    """(H, W, 4) float64 image: front-to-back compositing over segment midpoints."""
+    nz, ny, nx = vol.shape
+    dims = (nx, ny, nz)
+    field = Field(vol)
+    org, dirs = camera_rays(cam, dims)
+    img = np.zeros((cam.height, cam.width, 4))
+    amax = 1.0 - 2.0 ** -24
+    for j in range(cam.height):
+        for i in range(cam.width):
+            o, d = org[j, i], dirs[j, i]
+            t0, t1 = box_range(o, d, dims)
+            if not t1 > t0:
+                continue
+            edges = np.append(np.arange(t0, t1, step), t1)
+            if edges.size > 1 and edges[-2] >= t1:
+                edges = edges[:-1]
+            col = np.zeros(3)
+            trans = 1.0
+            for a, b in zip(edges[:-1], edges[1:]):
+                p = o + 0.5 * (a + b) * d
+                rgba = tf_lookup(field(p), tf, lo, hi)
+                alpha = 1.0 - (1.0 - min(max(rgba[3], 0.0), amax)) ** (b - a)
+                col += trans * alpha * rgba[:3]
+                trans *= 1.0 - alpha
+                if ert < 1.0 and 1.0 - trans > ert:
+                    break
+            img[j, i, :3] = col
+            img[j, i, 3] = 1.0 - trans
+    return img

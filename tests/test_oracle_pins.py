@@ -1,0 +1,411 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test states what fixes the expected value: the cubic B-spline's textbook definition and
+moments, closed forms of the emission-absorption integral (Beer-Lambert, constant media),
+geometric chord lengths, brute force on tiny inputs (an independent NumPy caster written as a
+kernel sum), and the invariants the method guarantees (empty-space leaping changes no pixel,
+early termination is bounded by the transmittance left).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mini
+from paper_2005_01442_gb300 import synth
+
+
+# ----------------------------------------------------------------- resampling (a5)
+
+def test_bspline_weights_match_textbook_kernel(orc):
+    # The four weights at fraction f are the centred cubic B-spline at distances 1+f, f,
+    # 1-f, 2-f (kernel written piecewise in oracle/mini.py, independent of the polynomials).
+    for f in np.linspace(0.0, 1.0, 101, endpoint=False):
+        w = orc.bspline_weights(f)
+        ref = mini.beta3(np.array([1.0 + f, f, 1.0 - f, 2.0 - f]))
+        np.testing.assert_allclose(w, ref, atol=1e-15)
+        assert abs(w.sum() - 1.0) < 1e-15  # partition of unity
+        assert np.all(w >= 0.0)
+
+
+def test_bspline_weight_derivatives(orc):
+    h = 1e-6
+    for f in np.linspace(0.05, 0.95, 19):
+        fd = (orc.bspline_weights(f + h) - orc.bspline_weights(f - h)) / (2 * h)
+        np.testing.assert_allclose(orc.bspline_dweights(f), fd, atol=1e-8)
+        assert abs(orc.bspline_dweights(f).sum()) < 1e-14
+
+
+@pytest.mark.parametrize("dtype,val", [(np.uint16, 1234), (np.int16, -777), (np.float32, 3.25)])
+def test_constant_field_is_reproduced(orc, dtype, val):
+    vol = np.full((7, 9, 11), val, dtype)
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        p = rng.uniform(-0.5, [10.5, 8.5, 6.5])  # anywhere in the box, edges included
+        assert abs(orc.sample(vol, p) - float(val)) <= 1e-12 * max(1.0, abs(float(val)))
+
+
+def test_linear_field_is_reproduced_in_interior(orc):
+    nz, ny, nx = 9, 11, 13
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    a, b, c, d = 3.0, -2.0, 5.0, 7.0
+    vol = (a * x + b * y + c * z + d).astype(np.float32)
+    rng = np.random.default_rng(1)
+    for _ in range(100):
+        p = rng.uniform([1.0, 1.0, 1.0], [nx - 2.0, ny - 2.0, nz - 2.0])
+        ref = a * p[0] + b * p[1] + c * p[2] + d
+        assert abs(orc.sample(vol, p) - ref) < 1e-9
+    # clamping breaks it at the border, as expected for clamp-to-edge taps
+    assert abs(orc.sample(vol, (0.0, 5.0, 4.0)) - (b * 5 + c * 4 + d)) > 1e-3
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_quadratic_gains_bspline_variance(orc, axis):
+    # sum_i beta3(x - i) i^2 = x^2 + 1/3 (the cubic B-spline has variance 4/12): on a
+    # non-cubic grid this also catches a transposed axis.
+    nz, ny, nx = 10, 12, 14
+    grids = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    coord = [grids[2], grids[1], grids[0]][axis]
+    vol = (coord.astype(np.float64) ** 2).astype(np.float32)
+    rng = np.random.default_rng(2 + axis)
+    hi = [nx - 2.0, ny - 2.0, nz - 2.0]
+    for _ in range(60):
+        p = rng.uniform([1.0, 1.0, 1.0], hi)
+        assert abs(orc.sample(vol, p) - (p[axis] ** 2 + 1.0 / 3.0)) < 1e-9
+
+
+def test_bilinear_cross_term_is_reproduced(orc):
+    nz, ny, nx = 8, 9, 10
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    vol = (x * y - 2.0 * y * z).astype(np.float32)
+    rng = np.random.default_rng(5)
+    for _ in range(60):
+        p = rng.uniform([1.0, 1.0, 1.0], [nx - 2.0, ny - 2.0, nz - 2.0])
+        assert abs(orc.sample(vol, p) - (p[0] * p[1] - 2.0 * p[1] * p[2])) < 1e-9
+
+
+# ------------------------------------------------ whole path vs brute force (a3-a9)
+
+def _cams_tiny(dims):
+    nx, ny, nz = dims
+    cams = [synth.ortho_z_camera(dims, 4, 4)]
+    c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2)
+    for eye in [(c[0] + 3.1, c[1] - 2.3, -14.0), (-11.0, c[1] + 1.7, c[2] + 9.0)]:
+        cams.append(synth.Camera(0, eye, c, (0.0, 1.0, 0.0), 40.0, (0.0, 0.0), 4, 4).as_float32())
+    return cams
+
+
+@pytest.mark.parametrize("kind", ["u16", "f32"])
+def test_oracle_matches_kernel_sum_brute_force(orc, kind):
+    rng = np.random.default_rng(11)
+    if kind == "u16":
+        vol = rng.integers(0, 4096, (8, 8, 8)).astype(np.uint16)
+        lo, hi = 0.0, 4095.0
+    else:
+        vol = rng.normal(0.0, 1.0, (8, 7, 6)).astype(np.float32)
+        lo, hi = -2.0, 2.5
+    tf = synth.tf_random(5, 6)
+    tf[:, 3] *= 0.6
+    nz, ny, nx = vol.shape
+    for cam in _cams_tiny((nx, ny, nz)):
+        for step, ert in [(0.5, 1.0), (0.37, 1.0), (0.5, 0.6)]:
+            a = orc.render(vol, tf, lo, hi, cam, step, ert=ert)
+            b = mini.render(vol, tf, lo, hi, cam, step, ert=ert)
+            assert np.abs(a - b).max() < 1e-11
+
+
+def test_ray_hits_box_where_expected(orc):
+    cam = synth.ortho_z_camera((64, 64, 64), 128, 128)
+    o, d, t0, t1, hit = orc.ray(cam, (64, 64, 64), 0, 0)
+    assert hit and np.allclose(o, [-0.25, -0.25, -0.5]) and np.allclose(d, [0, 0, 1])
+    assert t0 == 0.0 and t1 == 64.0
+    o, d, _, _, _ = orc.ray(cam, (64, 64, 64), 127, 5)
+    assert np.allclose(o[:2], [(127 + 0.5) * 0.5 - 0.5, (5 + 0.5) * 0.5 - 0.5])
+
+
+def test_phantom_config_sample_count(orc):
+    vol = synth.phantom()
+    cam = synth.ortho_z_camera((64, 64, 64), 128, 128)
+    _, counts = orc.render(vol, synth.tf_random(2), 0, 4095, cam, 0.5, return_counts=True)
+    assert counts == (128 * 128 * 128, 128 * 128 * 128)  # 16384 rays x 128 samples
+
+
+# ------------------------------------------------------------ closed forms (a6-a8)
+
+def _flat_tf(rgba):
+    return np.tile(np.asarray(rgba, np.float32), (256, 1))
+
+
+@pytest.mark.parametrize("nz,step", [(64, 0.5), (10, 0.3), (17, 0.7), (33, 0.45)])
+def test_constant_medium_closed_form(orc, nz, step):
+    rgba = (0.8, 0.3, 0.55, 0.07)
+    vol = np.full((nz, 6, 5), 100, np.uint16)
+    cam = synth.ortho_z_camera((5, 6, nz), 3, 3)
+    img = orc.render(vol, _flat_tf(rgba), 0, 4095, cam, step)
+    a = np.float64(np.float32(rgba[3]))
+    A = 1.0 - (1.0 - a) ** nz  # chord L = nz exactly
+    assert np.allclose(img[..., 3], A, atol=1e-13)
+    for c in range(3):
+        assert np.allclose(img[..., c], np.float64(np.float32(rgba[c])) * A, atol=1e-13)
+
+
+@pytest.mark.parametrize("step", [0.5, 0.3, 0.77])
+def test_beer_lambert_oblique_and_perspective(orc, step):
+    a = 0.02
+    sigma = -math.log1p(-np.float64(np.float32(a)))
+    n = 24
+    vol = np.full((n, n, n), 7, np.uint16)
+    tf = _flat_tf((1.0, 1.0, 1.0, a))
+    c = (n - 1) / 2
+    # orthographic 1x1 along the x-y diagonal through the centre: chord n*sqrt(2)
+    d = np.array([1.0, 1.0, 0.0]) / math.sqrt(2)
+    eye = np.array([c, c, c]) - 40.0 * d
+    cam = synth.Camera(1, tuple(eye), (c, c, c), (0.0, 0.0, 1.0), 0.0, (1.0, 1.0), 1, 1).as_float32()
+    o, dd, t0, t1, _ = orc.ray(cam, (n, n, n), 0, 0)
+    img = orc.render(vol, tf, 0, 4095, cam, step)
+    T = 1.0 - img[0, 0, 3]
+    assert abs(T - math.exp(-sigma * (t1 - t0))) < 1e-12
+    assert abs((t1 - t0) - n * math.sqrt(2)) < 1e-4  # eye rounded to float32
+    # perspective 1x1 on the z axis: the single ray is the optical axis, chord n
+    cam = synth.Camera(0, (c, c, -30.0), (c, c, c), (0.0, 1.0, 0.0), 20.0, (0, 0), 1, 1).as_float32()
+    T = 1.0 - orc.render(vol, tf, 0, 4095, cam, step)[0, 0, 3]
+    assert abs(T - math.exp(-sigma * n)) < 1e-12
+
+
+def test_sphere_chord_analytic_indicator(orc):
+    # Indicator of a ball (no resampling): -ln T / sigma is the chord 2 sqrt(r^2 - d^2) up to
+    # one misassigned segment per boundary crossing.
+    n, r = 64, 20.0
+    step = 0.5
+    a = 0.05
+    sigma = -math.log1p(-np.float64(np.float32(a)))
+    tf = np.zeros((256, 4), np.float32)
+    tf[255] = (1.0, 1.0, 1.0, a)
+    c = np.array([31.5, 31.5, 31.5])
+    vol = np.zeros((n, n, n), np.float32)
+    cam = synth.ortho_z_camera((n, n, n), 64, 64)
+    img = orc.render(vol, tf, 0.0, 1.0, cam, step, ball=(c, r))
+    xs = (np.arange(64) + 0.5) - 0.5  # pixel centre x (and y) for extent 64 over 64 px
+    X, Y = np.meshgrid(xs, xs)
+    dist = np.hypot(X - c[0], Y - c[1])
+    T = 1.0 - img[..., 3]
+    inside = dist < r - 1.0
+    chord = 2.0 * np.sqrt(np.maximum(r * r - dist ** 2, 0.0))
+    est = -np.log(T[inside]) / sigma
+    assert np.all(np.abs(est - chord[inside]) <= 2 * step + 1e-9)
+    assert np.all(T[dist > r + 1e-9] == 1.0)
+
+
+@pytest.mark.slow
+def test_voxelised_sphere_line_integral(orc):
+    # Voxelised ball r = 40 through resampling, rays along z. With a tiny opacity per unit
+    # value the optical depth is the line integral of the B-spline field; since beta3
+    # integrates to one, that integral is the 2D B-spline blend of the voxel column sums
+    # (brute force below), and it stays within a voxel of the true chord 2 sqrt(r^2 - d^2).
+    n, r = 96, 40.0
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vol = (((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2) <= r * r).astype(np.float32)
+    eps = 1e-6
+    tf = synth.tf_from_control_points([0, 255], [[1, 1, 1, 0], [1, 1, 1, eps]])
+    cam = synth.ortho_z_camera((n, n, n), 24, 24)
+    img = orc.render(vol, tf, 0.0, 1.0, cam, 0.25)
+    px = (np.arange(24) + 0.5) * n / 24 - 0.5
+    X, Y = np.meshgrid(px, px)
+    T = 1.0 - img[..., 3]
+    depth = -np.log(T) / np.float64(np.float32(eps))
+    colsum = vol.astype(np.float64).sum(axis=0)  # (ny, nx)
+    grid = np.arange(n, dtype=np.float64)
+    blend = np.array([[mini.beta3(yy - grid) @ colsum @ mini.beta3(xx - grid) for xx in px]
+                      for yy in px])
+    assert np.abs(depth - blend).max() < 1e-3
+    dist = np.hypot(X - c, Y - c)
+    sel = dist <= r - 2.0
+    chord = 2.0 * np.sqrt(r * r - dist[sel] ** 2)
+    assert np.abs(depth[sel] - chord).max() < 1.0
+    assert abs((depth[sel] - chord).mean()) < 0.2
+
+
+# ------------------------------------------------------------------ bricks (a1, a2)
+
+def _bricks_brute(vol, B):
+    nz, ny, nx = vol.shape
+    nb = [(n + B - 1) // B for n in (nz, ny, nx)]
+    mn = np.empty(nb, vol.dtype)
+    mx = np.empty(nb, vol.dtype)
+    for bz in range(nb[0]):
+        for by in range(nb[1]):
+            for bx in range(nb[2]):
+                sl = vol[max(bz * B - 1, 0):bz * B + B + 2, max(by * B - 1, 0):by * B + B + 2,
+                         max(bx * B - 1, 0):bx * B + B + 2]
+                mn[bz, by, bx] = sl.min()
+                mx[bz, by, bx] = sl.max()
+    return mn, mx
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.int16, np.float32])
+@pytest.mark.parametrize("B", [4, 8, 16])
+def test_brick_table_matches_brute_force(orc, dtype, B):
+    rng = np.random.default_rng(B)
+    shape = (19, 23, 37)
+    if dtype == np.float32:
+        vol = rng.normal(0, 100, shape).astype(np.float32)
+    else:
+        info = np.iinfo(dtype)
+        vol = rng.integers(info.min, info.max, shape, endpoint=True).astype(dtype)
+    mn, mx = orc.bricks(vol, B)
+    rmn, rmx = _bricks_brute(vol, B)
+    assert np.array_equal(mn, rmn) and np.array_equal(mx, rmx)
+
+
+def test_empty_bricks_have_zero_alpha_on_their_range(orc):
+    vol = synth.ct_volume((40, 48, 56), seed=9)
+    tf = synth.tf_ct()
+    lo, hi = synth.CT_LO, synth.CT_HI
+    for B in (4, 8, 16):
+        mn, mx = orc.bricks(vol, B)
+        occ = orc.occupancy(mn, mx, tf, lo, hi)
+        assert 0 < occ.sum() < occ.size
+        for i in np.flatnonzero(occ == 0):
+            vals = np.linspace(float(mn.flat[i]), float(mx.flat[i]), 33)
+            for v in vals:
+                assert mini.tf_lookup(v, tf, lo, hi)[3] == 0.0
+        # brute force of the same float32 decision
+        du = np.float32(255.0) / (np.float32(hi) - np.float32(lo))
+        ulo = np.clip((mn.astype(np.float32) - np.float32(lo)) * du, 0, 255)
+        uhi = np.clip((mx.astype(np.float32) - np.float32(lo)) * du, 0, 255)
+        k0 = np.maximum(np.floor(ulo).astype(int) - 1, 0)
+        k1 = np.minimum(np.ceil(uhi).astype(int) + 1, 255)
+        ref = np.array([(tf[a:b + 1, 3] > 0).any() for a, b in zip(k0.ravel(), k1.ravel())])
+        assert np.array_equal(occ.ravel().astype(bool), ref)
+
+
+def test_empty_brick_decision_is_conservative_per_value(orc):
+    # Single-valued bricks (min = max = v) swept over every 12-bit value, a table with
+    # isolated opaque entries: an empty verdict must leave TF alpha zero on the whole index
+    # interval [u(v) - 1/2, u(v) + 1/2], the room the float32 resampling rounding may use.
+    vals = np.arange(0, 4096, dtype=np.uint16)
+    tf = np.zeros((256, 4), np.float32)
+    for k in (3, 40, 41, 97, 200, 255):
+        tf[k] = (1.0, 1.0, 1.0, 0.5)
+    occ = orc.occupancy(vals, vals, tf, 0.0, 4095.0)
+    assert 0 < occ.sum() < occ.size
+    for v in vals[occ == 0]:
+        u = float(v) / 4095.0 * 255.0
+        for du in np.linspace(-0.5, 0.5, 11):
+            s = (u + du) * 4095.0 / 255.0
+            assert mini.tf_lookup(s, tf, 0.0, 4095.0)[3] == 0.0, (v, du)
+
+
+# --------------------------------------------------------- ESL and ERT invariants (a4, a8)
+
+def _ct_small():
+    vol = synth.ct_volume((48, 64, 64), seed=21)
+    return vol, synth.tf_ct(), synth.CT_LO, synth.CT_HI
+
+
+def test_empty_space_leaping_changes_no_pixel(orc):
+    vol, tf, lo, hi = _ct_small()
+    dims = synth.dims_of(vol)
+    for cam in synth.orbit_cameras(4, 3, dims, 48, 40):
+        ref, cref = orc.render(vol, tf, lo, hi, cam, 0.5, return_counts=True)
+        for B in (4, 8, 16):
+            img, cnt = orc.render(vol, tf, lo, hi, cam, 0.5, brick=B, return_counts=True)
+            assert np.array_equal(img, ref)
+            assert cnt[0] == cref[0] and cnt[1] < cref[1]
+
+
+def test_early_termination_bounded_by_remaining_transmittance(orc):
+    vol, tf, lo, hi = _ct_small()
+    tf = tf.copy()
+    tf[:, 3] = np.minimum(tf[:, 3] * 3.0, 0.95)
+    dims = synth.dims_of(vol)
+    for cam in synth.orbit_cameras(6, 2, dims, 48, 40):
+        full = orc.render(vol, tf, lo, hi, cam, 0.5)
+        ert = orc.render(vol, tf, lo, hi, cam, 0.5, ert=0.999, brick=8)
+        t_stop = 1.0 - ert[..., 3]
+        stopped = ert[..., 3] > 0.999
+        assert stopped.any()
+        diff = np.abs(full - ert).max(axis=-1)
+        assert np.all(diff[stopped] <= t_stop[stopped] + 1e-15)
+        assert np.array_equal(full[~stopped], ert[~stopped])
+
+
+# ------------------------------------------------------------------- gradient (a10)
+
+def test_gradient_closed_form_constant_volume(orc):
+    # u lands exactly on entry k, so dA/dTF[k].alpha = L (1-a)^(L-1) and dC/dTF[k].rgb = A.
+    nz, a = 12, 0.1
+    vol = np.full((nz, 4, 4), 100.0, np.float32)
+    tf = np.zeros((256, 4), np.float32)
+    tf[100] = (0.2, 0.4, 0.6, a)
+    cam = synth.ortho_z_camera((4, 4, nz), 2, 2)
+    g = np.zeros((4, 4))
+    g[:, 3] = 1.0
+    gtf, _ = orc.render_grad(vol, tf, 0.0, 255.0, cam, 0.5, g)
+    a64 = np.float64(np.float32(a))
+    assert abs(gtf[100, 3] - 4 * nz * (1 - a64) ** (nz - 1)) < 1e-10
+    g[:] = 0
+    g[:, 0] = 1.0
+    gtf, _ = orc.render_grad(vol, tf, 0.0, 255.0, cam, 0.5, g)
+    assert abs(gtf[100, 0] - 4 * (1 - (1 - a64) ** nz)) < 1e-10
+
+
+def _fd_setup():
+    vol = synth.ct_volume((24, 24, 24), seed=31).astype(np.float32)
+    vol = vol + np.random.default_rng(3).normal(0, 30, vol.shape).astype(np.float32)
+    tf = synth.tf_ct(seed=4)
+    tf[:, 3] = np.maximum(tf[:, 3], 0.01)
+    dims = synth.dims_of(vol)
+    cam = synth.orbit_cameras(12, 1, dims, 12, 10)[0]
+    g = np.random.default_rng(8).normal(0, 1, (cam.height * cam.width, 4))
+    return vol, tf, cam, g
+
+
+def _loss(orc, vol, tf, cam, g):
+    img = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5)
+    return float((img.reshape(-1, 4) * g).sum())
+
+
+@pytest.mark.slow
+def test_gradient_matches_central_differences(orc):
+    vol, tf, cam, g = _fd_setup()
+    gtf, gvol = orc.render_grad(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, g)
+    rng = np.random.default_rng(17)
+    h = 1e-3
+    # TF entries used by the image (rgba is linear in the table, so no kinks)
+    used = np.flatnonzero(np.abs(gtf).sum(1) > 1e-6)
+    checked = 0
+    for k in rng.permutation(used)[:25]:
+        c = int(rng.integers(0, 4))
+        tp, tm = tf.astype(np.float64).copy(), tf.astype(np.float64).copy()
+        tp[k, c] += h
+        tm[k, c] -= h
+        # the oracle takes float32 tables: perturb in float64, hand over exact float32 values
+        tp32, tm32 = tp.astype(np.float32), tm.astype(np.float32)
+        step = float(tp32[k, c]) - float(tm32[k, c])
+        fd = (_loss(orc, vol, tp32, cam, g) - _loss(orc, vol, tm32, cam, g)) / step
+        if abs(gtf[k, c]) > 1e-4:
+            assert abs(fd - gtf[k, c]) <= 1e-3 * abs(gtf[k, c]) + 1e-7
+            checked += 1
+    assert checked >= 10
+    # voxels with a visible effect, skipping samples that sit on a TF kink (the FD at h and
+    # at h/4 disagree there)
+    cand = np.flatnonzero(np.abs(gvol).ravel() > 0.05 * np.abs(gvol).max())
+    checked = 0
+    for vi in rng.permutation(cand)[:40]:
+        def fd_at(hh):
+            vp, vm = vol.copy(), vol.copy()
+            vp.flat[vi] += hh
+            vm.flat[vi] -= hh
+            hh_eff = (float(vp.flat[vi]) - float(vm.flat[vi])) / 2
+            return (_loss(orc, vp, tf, cam, g) - _loss(orc, vm, tf, cam, g)) / (2 * hh_eff)
+        hv = 1e-3 * max(1.0, abs(float(vol.flat[vi])))
+        f1, f2 = fd_at(hv), fd_at(hv / 4)
+        if abs(f1 - f2) > 1e-4 * abs(f1):
+            continue  # kink inside the stencil
+        assert abs(f1 - gvol.flat[vi]) <= 1e-3 * abs(gvol.flat[vi])
+        checked += 1
+        if checked >= 25:
+            break
+    assert checked >= 10
