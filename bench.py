@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the CT volume ray caster on one GPU per rank (replicas; weak scaling).
+
+Default workload: a 512 x 512 x 400 int16 synthetic CT resident in HBM, rendered to 1024^2
+perspective images (30 degree field of view) from 16 seeded orbit cameras, step 0.5 voxel,
+8^3 brick empty-space leaping, early ray termination at opacity 0.999. One step = rebuild the
+brick min/max table, rebuild the occupancy for the transfer function, render the 16 frames.
+L2 is flushed (a 256 MB write) before every step, outside the step's events.
+
+Printed: one JSON line on rank 0. `value` is executed samples per second (Gsamples/s, all
+ranks); Mrays/s and nominal Gsamples/s ride along. `roofline` reports the render kernel
+against the FP32 issue roof (152 SMs x 128 lanes x 2 flop x 2.07 GHz), using the algorithmic
+flop count per executed sample. `cpu_baseline` times the FP64 oracle on host cores on a
+bounded sample of the same workload. `e2e` repeats the measurement through
+vrc_render_host (image read back to pinned host memory inside the timed region).
+
+`--impl reference` times the FP64 CPU oracle itself on the same workload (bounded samples).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_SAMPLE = 230      # algorithmic FP32 flops per executed sample (FMA = 2)
+SM_COUNT_NOMINAL = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+METRIC = ("Gsamples/s & Mrays/s (512²×400 CT, 1024² img) vs roofline; "
+          "p50/p99 req latency")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="vrc", choices=["vrc", "reference"])
+    p.add_argument("--brick", type=int, default=8)
+    p.add_argument("--cameras", type=int, default=16)
+    p.add_argument("--kernel", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(args):
+    return {"workload": f"ct512x512x400_i16_to_1024sq_persp30_step0.5_B{args.brick}_ert0.999_"
+                        f"{args.cameras}cams",
+            "volume": [512, 512, 400], "volume_dtype": "int16", "image": [1024, 1024],
+            "fovy_deg": 30.0, "step": 0.5, "brick": args.brick, "ert": 0.999,
+            "cameras": args.cameras, "ct_seed": 3, "camera_seed": 4,
+            "l2": "flushed (256 MB write) before every step",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.active = False
+        self.lock = threading.Lock()
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            with self.lock:
+                if self.active:
+                    self.rows.append([x.strip() for x in line.split(",")])
+
+    def mark(self, on: bool):
+        with self.lock:
+            self.active = on
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        with self.lock:
+            rows = list(self.rows)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if args.impl == "vrc" else "gloo")
+    return rank, world, local
+
+
+def cpu_sample(vol, tf, cams, rows_every: int, brick: int):
+    """Times the oracle on rows 0, k, 2k, ... of the first camera; returns (seconds,
+    executed samples, rays, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_2005_01442_gb300 import synth
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except Exception:
+        ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    cam = cams[0]
+    rows = np.arange(0, cam.height, rows_every)
+    pix = np.stack(np.meshgrid(np.arange(cam.width), rows), -1).reshape(-1, 2)
+    t0 = time.perf_counter()
+    _, counts = oracle.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=0.999,
+                              brick=brick, pixels=pix, return_counts=True)
+    dt = time.perf_counter() - t0
+    return dt, counts[1], counts[0], pix.shape[0], oracle.get_threads()
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle timed on host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2005_01442_gb300 import synth
+    vol = synth.ct_volume()
+    tf = synth.tf_ct()
+    cams = synth.orbit_cameras(4, args.cameras, synth.dims_of(vol), 1024, 1024)
+    rows_every = 4
+    times, ex, nom, rays = [], 0, 0, 0
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        dt, e, n, r, threads = cpu_sample(vol, tf, [cams[i % len(cams)]], rows_every, args.brick)
+        if i >= args.warmup:
+            times.append(dt)
+            ex += e
+            nom += n
+            rays += r
+    total = sum(times)
+    value = ex / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gsamples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "mrays_per_s": rays / total / 1e6, "gsamples_nominal_per_s": nom / total / 1e9,
+            "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"each step: every {rows_every}th row of one 1024^2 "
+                                       "frame (cameras in turn), ESL+ERT on"},
+            "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2005_01442_gb300 import build as vbuild
+    from paper_2005_01442_gb300 import synth
+    from paper_2005_01442_gb300.renderer import Renderer
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        vbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    vbuild.build()
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None else str(local)
+
+    vol = synth.ct_volume()
+    tf = synth.tf_ct()
+    dims = synth.dims_of(vol)
+    cams = synth.orbit_cameras(4 + 1000 * rank, args.cameras, dims, 1024, 1024)
+    R = Renderer(local)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    B = args.brick
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((args.cameras, 1024, 1024, 4), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # sample counts (deterministic; measured once, outside the timed region)
+    R.build_bricks(vid, B)
+    cnt = torch.zeros((args.cameras, 2), dtype=torch.int64, device=dev)
+    for i, cam in enumerate(cams):
+        R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], counters=cnt[i],
+                 kernel=args.kernel)
+    torch.cuda.synchronize()
+    nominal, executed = [int(x) for x in cnt.sum(0).tolist()]
+    rays_per_step = args.cameras * 1024 * 1024
+
+    def one_step(ev_frames=None):
+        R.build_bricks(vid, B)
+        R.build_occupancy(vid, tid, B)
+        for i, cam in enumerate(cams):
+            if ev_frames is not None:
+                ev_frames[i][0].record(stream)
+            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=args.kernel)
+            if ev_frames is not None:
+                ev_frames[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.5)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    frame_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in cams] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.mark(True)
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        step_ev[s][0].record(stream)
+        one_step(frame_ev[s])
+        step_ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    frame_ms = [a.elapsed_time(b) for fr in frame_ev for a, b in fr]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    secs = total_ms / 1e3
+    value = world * executed * args.steps / secs / 1e9
+
+    # end to end through the public host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((args.cameras, 1024, 1024, 4), dtype=torch.float32, pin_memory=True)
+        for _ in range(2):
+            R.build_bricks(vid, B)
+            for i, cam in enumerate(cams):
+                R.render_host(vid, tid, cam, ert=0.999, brick=B, out=host[i], kernel=args.kernel)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            R.build_bricks(vid, B)
+            for i, cam in enumerate(cams):
+                R.render_host(vid, tid, cam, ert=0.999, brick=B, out=host[i], kernel=args.kernel)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * executed * args.steps / e2e_s / 1e9, "unit": "Gsamples/s",
+               "h2d_bytes_per_step": args.cameras * 60,  # vrc_camera records passed by value
+               "d2h_bytes_per_step": args.cameras * 1024 * 1024 * 16,
+               "api": "vrc_render_host (pinned host image, copy inside the timed region)"}
+
+    clocks = sampler.summary()
+    sampler.stop()
+    sms = props.multi_processor_count
+    kernel_ms = statistics.mean(frame_ms)
+    flops_per_launch = FLOPS_PER_SAMPLE * executed / args.cameras
+    achieved = flops_per_launch / (kernel_ms / 1e3) / 1e12
+    peak = sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            dt, ex, nom_s, rays, threads = cpu_sample(vol, tf, cams, 4, B)
+            cpu = {"value": ex / dt / 1e9, "unit": "Gsamples/s", "cores": threads,
+                   "kind": "oracle",
+                   "sample": f"every 4th row of camera 0 (1024x256 rays), ESL B={B} + ERT, "
+                             f"{dt:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args),
+            "mrays_per_s": world * rays_per_step * args.steps / secs / 1e6,
+            "gsamples_nominal_per_s": world * nominal * args.steps / secs / 1e9,
+            "samples_per_step": {"nominal": nominal, "executed": executed},
+            "render_kernel_ms": kernel_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "basis": f"{FLOPS_PER_SAMPLE} flop/executed sample; peak = {sms} SMs x "
+                                  f"{FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * (2 + args.cameras),
+            "clocks": clocks,
+        }
+        if clocks.get("sm_mhz"):
+            line["roofline"]["frac_at_measured_clock"] = achieved / (
+                sms * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+        print(json.dumps(line), flush=True)
+    R.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * libvrc -- GB300 (sm_103a) CT volume ray caster, C ABI.
+ *
+ * The library renders a scalar CT volume by direct volume ray casting as described in the
+ * paper's "Methodology" section: one ray per pixel from the observer, fixed-step sampling
+ * along the ray, cubic-spline (uniform cubic B-spline) resampling, post-classification through
+ * an RGBA transfer function ("palette", opacity 0 = transparent, 1 = opaque), front-to-back
+ * accumulation, early ray termination, and empty-space leaping over block ("brick") min/max
+ * auxiliary structures (Sec. "Analysis", Pros (a)-(b)). The calls follow that problem
+ * statement: upload a volume, build its brick structure, set a transfer function and a
+ * camera, render.
+ *
+ * Geometry: voxel (i, j, k) sits at the point (i, j, k); the volume box is [-0.5, n - 0.5]
+ * per axis; volumes are dense arrays with x fastest, then y, then z.
+ *
+ * Conventions for every call:
+ *   - Arguments are validated before anything is launched; a bad argument returns
+ *     VRC_ERR_ARG and changes nothing.
+ *   - No exception or C++ type crosses the boundary; status codes are ints (0 = VRC_OK).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Kernels run asynchronously on it; device-side faults detected by the kernels' own
+ *     checks are reported through vrc_last_device_error().
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host are host
+ *     pointers owned by the caller. Everything created by a vrc_* call (contexts, resident
+ *     volumes, brick tables, transfer functions) is owned by the context and freed by
+ *     vrc_destroy() or the matching *_free call.
+ *   - A context is used by one host thread at a time (or under external locking).
+ *   - vrc_last_error_message() describes the most recent failure on the context.
+ */
+#ifndef VRC_H
+#define VRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int vrc_status;
+#define VRC_OK 0
+#define VRC_ERR_ARG (-1)     /* invalid argument, id or size */
+#define VRC_ERR_OOM (-2)     /* device or host allocation failed */
+#define VRC_ERR_CUDA (-3)    /* a CUDA runtime call failed */
+#define VRC_ERR_TIMEOUT (-4) /* a bounded device-side wait ran out */
+#define VRC_ERR_BUSY (-5)    /* resource in use (e.g. a volume still referenced) */
+#define VRC_ERR_STATE (-6)   /* call out of order (e.g. render with ESL before bricks) */
+#define VRC_ERR_DEVICE (-7)  /* a kernel's own bounds check fired (see device error word) */
+
+typedef struct vrc_ctx vrc_ctx;
+
+typedef enum { VRC_U16 = 0, VRC_I16 = 1, VRC_F32 = 2 } vrc_dtype;
+
+/* Camera (paper, "Methodology": each pixel's ray is a point in space -- the observer -- and a
+ * direction). Perspective (ortho = 0): pinhole at `eye` looking at `center`, vertical field
+ * of view `fovy_deg`, square pixels. Orthographic (ortho = 1): parallel rays along
+ * center - eye, the image plane through `eye` spanning ortho_extent[0] x ortho_extent[1]
+ * voxel units. Pixel (px, py), py = 0 the top row, samples its centre; `up` fixes the
+ * vertical image axis (must not be parallel to the view direction). */
+typedef struct {
+    int ortho;
+    float eye[3];
+    float center[3];
+    float up[3];
+    float fovy_deg;
+    float ortho_extent[2];
+    int width;
+    int height;
+} vrc_camera;
+
+/* Render parameters.
+ *   step           sampling distance along the ray in voxel units (> 0). The ray's range
+ *                  [t_in, t_out] inside the box is cut into segments of this length (the
+ *                  last may be shorter); one sample sits at each segment midpoint and its
+ *                  opacity is corrected to the segment length.
+ *   ert_threshold  early ray termination: a ray stops after the sample where its
+ *                  accumulated opacity exceeds this value (paper: "early beam completion");
+ *                  >= 1 disables it.
+ *   brick          0 = no empty-space leaping; 8 or 16 = leap over empty bricks of that
+ *                  size (requires vrc_bricks_build for that size; the image is identical
+ *                  to brick = 0).
+ *   seg_len        adjoint checkpoint interval in samples (0 = default 64).
+ *   kernel         0 = automatic, 1 = per-ray kernel, 2 = brick-tile kernel.            */
+typedef struct {
+    float step;
+    float ert_threshold;
+    int brick;
+    int seg_len;
+    int kernel;
+} vrc_params;
+
+/* Creates a context bound to CUDA device `device`. */
+vrc_status vrc_create(vrc_ctx **ctx_out, int device);
+/* Synchronises the device and frees everything the context owns. NULL is accepted. */
+vrc_status vrc_destroy(vrc_ctx *ctx);
+
+/* Makes a volume resident on the device (paper, "Methodology": the volume is stored on the
+ * GPU and sampled at arbitrary points). `data` holds nx*ny*nz elements of `dtype`, x
+ * fastest; it is a host pointer (on_device = 0) or a device pointer (on_device = 1). The
+ * context copies it into its own edge-replicated, padded layout; the caller's buffer may
+ * be reused once the call returns (host) or once `stream` has passed this point (device).
+ * Sizes must be 1..32768 per axis. Returns the new volume id in *vol_id. */
+vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_dtype dtype,
+                             int nx, int ny, int nz, int *vol_id, void *stream);
+/* Frees a resident volume and its brick tables. */
+vrc_status vrc_volume_free(vrc_ctx *ctx, int vol_id);
+/* Reports a resident volume's dtype and sizes. Any output pointer may be NULL. */
+vrc_status vrc_volume_info(vrc_ctx *ctx, int vol_id, int *dtype, int *nx, int *ny, int *nz);
+
+/* Builds the brick table of size B (paper, "Methodology" and Fig. 3: blocks of a regular
+ * size with an overlap; "Analysis", Pros (b): auxiliary structures to skip empty space).
+ * Brick b covers voxels [b*B, b*B + B) per axis; its entry holds the minimum and maximum
+ * voxel value over the apron box [b*B - 1, b*B + B + 1] clamped to the volume -- the
+ * overlap a cubic kernel reads. Tables have ceil(n/B) bricks per axis, x fastest, and the
+ * voxel dtype. B must be 8 or 16. Rebuilding replaces the table. */
+vrc_status vrc_bricks_build(vrc_ctx *ctx, int vol_id, int B, void *stream);
+/* Copies a brick table to host buffers (each nbx*nby*nbz elements of the voxel dtype);
+ * synchronises the context's work on `stream` first. */
+vrc_status vrc_bricks_get(vrc_ctx *ctx, int vol_id, int B, void *min_host, void *max_host,
+                          void *stream);
+
+/* Registers a 256-entry RGBA transfer function (paper, "Methodology": T(x) maps each value
+ * to colour and opacity). rgba_host: 256 x 4 floats, entry k at index coordinate u = k,
+ * u = (v - lo) / (hi - lo) * 255 clamped to [0, 255], linear interpolation between entries
+ * (post-classification). Requires hi > lo. Returns the id in *tf_id. */
+vrc_status vrc_tf_set(vrc_ctx *ctx, const float *rgba_host, float lo, float hi, int *tf_id);
+/* Replaces the table and window of an existing transfer function. */
+vrc_status vrc_tf_update(vrc_ctx *ctx, int tf_id, const float *rgba_host, float lo, float hi);
+vrc_status vrc_tf_free(vrc_ctx *ctx, int tf_id);
+
+/* Builds (asynchronously on `stream`) the occupancy bytes of (volume, B, TF) if the brick
+ * table or the transfer function changed since they were last built; vrc_render does the
+ * same on demand. */
+vrc_status vrc_occupancy_build(vrc_ctx *ctx, int vol_id, int tf_id, int B, void *stream);
+
+/* Copies the occupancy bytes of (volume, B, TF) to the host (nbx*nby*nbz bytes): 1 when any
+ * TF alpha is > 0 on the entries [floor(u(min)) - 1, ceil(u(max)) + 1] of the brick's value
+ * range, with u evaluated in float32. Builds the occupancy if needed. */
+vrc_status vrc_occupancy_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint8_t *occ_host,
+                             void *stream);
+
+/* Renders `cam` into out_rgba_dev: height x width x 4 floats (RGBA, row py = 0 on top),
+ * colour premultiplied by opacity, black background: (C_r, C_g, C_b, 1 - T).
+ * counters_dev: NULL, or 2 caller-owned uint64 that the kernel increments by the number of
+ * nominal samples (segments inside the box, summed over rays) and executed samples
+ * (samples resampled and composited). Asynchronous on `stream`. */
+vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                      const vrc_params *params, float *out_rgba_dev,
+                      unsigned long long *counters_dev, void *stream);
+
+/* The same render end to end for callers holding host memory: renders into a
+ * context-owned device image and copies it to out_rgba_host (height x width x 4 floats;
+ * pinned memory gives an asynchronous copy). Returns after the copy has completed. */
+vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                           const vrc_params *params, float *out_rgba_host, void *stream);
+
+/* Reads and clears the device error word shared by the context's kernels: 0 when no kernel
+ * check has fired, else a VRC_ERR_* code. Synchronises `stream`. */
+vrc_status vrc_last_device_error(vrc_ctx *ctx, int *code, void *stream);
+
+/* Text of the most recent failure on the context ("" when none); valid until the next
+ * call on the same context. */
+const char *vrc_last_error_message(vrc_ctx *ctx);
+/* Static name of a status code. */
+const char *vrc_status_str(vrc_status s);
+/* Library version, e.g. 100 for 0.1.0. */
+int vrc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VRC_H */

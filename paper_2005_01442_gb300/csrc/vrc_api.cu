@@ -1,0 +1,623 @@
+// C-ABI layer of libvrc: contexts, resident volumes, brick tables, transfer functions,
+// occupancy caching and render dispatch. Validation happens here, before any launch; no C++
+// exception crosses the boundary.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vrc.h"
+#include "vrc_internal.h"
+
+using namespace vrc;
+
+namespace {
+
+struct Bricks {
+    int B = 0;
+    int nb[3] = {0, 0, 0};
+    void *mn = nullptr, *mx = nullptr;
+    unsigned version = 0;  // bumped on every rebuild
+    long count() const { return (long)nb[0] * nb[1] * nb[2]; }
+};
+
+struct Occ {
+    uint8_t *dev = nullptr;
+    long n = 0;
+    unsigned brick_version = 0, tf_version = 0;
+};
+
+struct Volume {
+    int dtype = 0;
+    int n[3] = {0, 0, 0};
+    int pnx = 0, pny = 0, pnz = 0;
+    void *dpad = nullptr;
+    Bricks bricks[2];               // B = 8, B = 16
+    std::map<long, Occ> occ;        // key: tf_id * 2 + (B == 16)
+};
+
+struct Tf {
+    float lo = 0, hi = 1, du = 255;
+    float4 *rgba = nullptr;   // 256
+    float4 *drgba = nullptr;  // 256
+    int *prefix = nullptr;    // 257
+    unsigned version = 0;
+};
+
+int slot_of(int B) { return B == 16 ? 1 : 0; }
+
+}  // namespace
+
+struct vrc_ctx {
+    int device = 0;
+    int next_id = 1;
+    std::map<int, Volume> vols;
+    std::map<int, Tf> tfs;
+    std::string err;
+    int *err_word = nullptr;   // device error word shared by kernels
+    float4 *host_img = nullptr;  // device image for vrc_render_host
+    size_t host_img_bytes = 0;
+    unsigned tf_version_counter = 0;
+};
+
+namespace {
+
+vrc_status fail(vrc_ctx *c, vrc_status s, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+vrc_status cuda_fail(vrc_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? VRC_ERR_OOM : VRC_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+void free_volume(Volume &v) {
+    cudaFree(v.dpad);
+    for (auto &b : v.bricks) {
+        cudaFree(b.mn);
+        cudaFree(b.mx);
+    }
+    for (auto &kv : v.occ) cudaFree(kv.second.dev);
+    v.occ.clear();
+}
+
+void free_tf(Tf &t) {
+    cudaFree(t.rgba);
+    cudaFree(t.drgba);
+    cudaFree(t.prefix);
+}
+
+bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+// Camera record -> per-pixel affine maps in double, split into double-float.
+ff split(double v) {
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    return {hi, lo};
+}
+
+vrc_status build_camera(vrc_ctx *ctx, const vrc_camera *c, CamDev &cd) {
+    if (!c) return fail(ctx, VRC_ERR_ARG, "camera is NULL");
+    if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768)
+        return fail(ctx, VRC_ERR_ARG, "image size %dx%d out of range", c->width, c->height);
+    if (!finite3(c->eye) || !finite3(c->center) || !finite3(c->up))
+        return fail(ctx, VRC_ERR_ARG, "camera has non-finite values");
+    double f[3], up[3], r[3], u[3];
+    double fl = 0, rl = 0;
+    for (int k = 0; k < 3; ++k) {
+        f[k] = (double)c->center[k] - (double)c->eye[k];
+        up[k] = c->up[k];
+        fl += f[k] * f[k];
+    }
+    fl = sqrt(fl);
+    if (!(fl > 0)) return fail(ctx, VRC_ERR_ARG, "camera eye equals center");
+    for (int k = 0; k < 3; ++k) f[k] /= fl;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rl > 1e-12)) return fail(ctx, VRC_ERR_ARG, "camera up is parallel to the view direction");
+    for (int k = 0; k < 3; ++k) r[k] /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double W = c->width, H = c->height;
+    memset(&cd, 0, sizeof(cd));
+    cd.ortho = c->ortho ? 1 : 0;
+    cd.width = c->width;
+    cd.height = c->height;
+    if (c->ortho) {
+        const double hx = 0.5 * c->ortho_extent[0], hy = 0.5 * c->ortho_extent[1];
+        if (!(hx > 0) || !(hy > 0) || !isfinite(hx) || !isfinite(hy))
+            return fail(ctx, VRC_ERR_ARG, "orthographic extent must be positive");
+        for (int k = 0; k < 3; ++k) {
+            cd.A[k] = split((double)c->eye[k] - hx * r[k] + hy * u[k]);
+            cd.Bx[k] = split(hx / W * r[k]);
+            cd.By[k] = split(-hy / H * u[k]);
+            cd.dir[k] = split(f[k]);
+            cd.eye[k] = split(c->eye[k]);
+        }
+    } else {
+        if (!(c->fovy_deg > 0.0f && c->fovy_deg < 179.0f))
+            return fail(ctx, VRC_ERR_ARG, "fovy_deg must be in (0, 179)");
+        const double th = tan(0.5 * (double)c->fovy_deg * M_PI / 180.0);
+        const double kx = th * W / H, ky = th;
+        for (int k = 0; k < 3; ++k) {
+            cd.A[k] = split(f[k] - kx * r[k] + ky * u[k]);
+            cd.Bx[k] = split(kx / W * r[k]);
+            cd.By[k] = split(-ky / H * u[k]);
+            cd.eye[k] = split(c->eye[k]);
+            cd.dir[k] = split(f[k]);
+        }
+    }
+    return VRC_OK;
+}
+
+Volume *get_vol(vrc_ctx *ctx, int id) {
+    auto it = ctx->vols.find(id);
+    return it == ctx->vols.end() ? nullptr : &it->second;
+}
+
+Tf *get_tf(vrc_ctx *ctx, int id) {
+    auto it = ctx->tfs.find(id);
+    return it == ctx->tfs.end() ? nullptr : &it->second;
+}
+
+VolView view_of(const Volume &v) {
+    VolView vv;
+    vv.base = v.dpad;
+    vv.dtype = v.dtype;
+    for (int k = 0; k < 3; ++k) vv.n[k] = v.n[k];
+    vv.pnx = v.pnx;
+    vv.pny = v.pny;
+    vv.pnz = v.pnz;
+    return vv;
+}
+
+vrc_status upload_tf(vrc_ctx *ctx, Tf &t, const float *rgba, float lo, float hi) {
+    if (!rgba) return fail(ctx, VRC_ERR_ARG, "transfer function table is NULL");
+    if (!(hi > lo) || !isfinite(lo) || !isfinite(hi))
+        return fail(ctx, VRC_ERR_ARG, "transfer function window needs finite hi > lo");
+    for (int i = 0; i < 1024; ++i)
+        if (!isfinite(rgba[i])) return fail(ctx, VRC_ERR_ARG, "transfer function has non-finite entries");
+    std::vector<float4> a(256), d(256);
+    std::vector<int> pre(257);
+    pre[0] = 0;
+    for (int i = 0; i < 256; ++i) {
+        a[i] = make_float4(rgba[4 * i], rgba[4 * i + 1], rgba[4 * i + 2], rgba[4 * i + 3]);
+        pre[i + 1] = pre[i] + (rgba[4 * i + 3] > 0.0f ? 1 : 0);
+    }
+    for (int i = 0; i < 255; ++i)
+        d[i] = make_float4(rgba[4 * i + 4] - rgba[4 * i], rgba[4 * i + 5] - rgba[4 * i + 1],
+                           rgba[4 * i + 6] - rgba[4 * i + 2], rgba[4 * i + 7] - rgba[4 * i + 3]);
+    d[255] = make_float4(0, 0, 0, 0);
+    if (!t.rgba) {
+        CK(cudaMalloc(&t.rgba, 256 * sizeof(float4)), "cudaMalloc(tf)");
+        CK(cudaMalloc(&t.drgba, 256 * sizeof(float4)), "cudaMalloc(tf)");
+        CK(cudaMalloc(&t.prefix, 257 * sizeof(int)), "cudaMalloc(tf)");
+    } else {
+        // tables may be in use by queued kernels on any stream
+        CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize(tf update)");
+    }
+    CK(cudaMemcpy(t.rgba, a.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice), "tf upload");
+    CK(cudaMemcpy(t.drgba, d.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice), "tf upload");
+    CK(cudaMemcpy(t.prefix, pre.data(), 257 * sizeof(int), cudaMemcpyHostToDevice), "tf upload");
+    volatile float range = hi - lo;
+    t.lo = lo;
+    t.hi = hi;
+    t.du = 255.0f / range;
+    t.version = ++ctx->tf_version_counter;
+    return VRC_OK;
+}
+
+// Occupancy of (volume, B, tf), rebuilt when the bricks or the table changed.
+vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStream_t st,
+                      const uint8_t **out) {
+    Bricks &b = v.bricks[slot_of(B)];
+    if (!b.mn || b.B != B) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
+    long key = (long)tf_id * 2 + slot_of(B);
+    Occ &o = v.occ[key];
+    if (!o.dev || o.n != b.count()) {
+        cudaFree(o.dev);
+        o.dev = nullptr;
+        CK(cudaMalloc(&o.dev, (size_t)b.count()), "cudaMalloc(occupancy)");
+        o.n = b.count();
+        o.brick_version = o.tf_version = 0;
+    }
+    if (o.brick_version != b.version || o.tf_version != t.version) {
+        CK(launch_occupancy(b.mn, b.mx, v.dtype, b.count(), t.prefix, t.lo, t.du, o.dev, st),
+           "occupancy launch");
+        o.brick_version = b.version;
+        o.tf_version = t.version;
+    }
+    *out = o.dev;
+    return VRC_OK;
+}
+
+TfView tf_view(const Tf &t) {
+    TfView tv;
+    tv.rgba = t.rgba;
+    tv.drgba = t.drgba;
+    tv.lo = t.lo;
+    tv.hi = t.hi;
+    tv.du = t.du;
+    return tv;
+}
+
+vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                          const vrc_params *p, cudaStream_t st, RenderLaunch &L) {
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    if (!p) return fail(ctx, VRC_ERR_ARG, "params is NULL");
+    if (!(p->step > 0.0f) || !isfinite(p->step) || p->step < 1e-3f)
+        return fail(ctx, VRC_ERR_ARG, "step must be finite and >= 1e-3");
+    if (isnan(p->ert_threshold)) return fail(ctx, VRC_ERR_ARG, "ert_threshold is NaN");
+    if (p->brick != 0 && p->brick != 8 && p->brick != 16)
+        return fail(ctx, VRC_ERR_ARG, "brick must be 0, 8 or 16");
+    if (p->kernel < 0 || p->kernel > 2) return fail(ctx, VRC_ERR_ARG, "kernel must be 0, 1 or 2");
+    memset(&L, 0, sizeof(L));
+    vrc_status s = build_camera(ctx, cam, L.cam);
+    if (s != VRC_OK) return s;
+    L.vol = view_of(*v);
+    L.tf = tf_view(*t);
+    for (int k = 0; k < 3; ++k) L.grid.n[k] = v->n[k];
+    L.grid.step = p->step;
+    L.grid.ert = p->ert_threshold;
+    L.err = ctx->err_word;
+    if (p->brick) {
+        const uint8_t *occ = nullptr;
+        s = ensure_occ(ctx, *v, tf_id, *t, p->brick, st, &occ);
+        if (s != VRC_OK) return s;
+        Bricks &b = v->bricks[slot_of(p->brick)];
+        L.occ = occ;
+        L.bricks.B = b.B;
+        L.bricks.shift = b.B == 16 ? 4 : 3;
+        for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b.nb[k];
+        L.bricks.mn = b.mn;
+        L.bricks.mx = b.mx;
+    }
+    return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vrc_version(void) { return 100; }
+
+const char *vrc_status_str(vrc_status s) {
+    switch (s) {
+    case VRC_OK: return "VRC_OK";
+    case VRC_ERR_ARG: return "VRC_ERR_ARG";
+    case VRC_ERR_OOM: return "VRC_ERR_OOM";
+    case VRC_ERR_CUDA: return "VRC_ERR_CUDA";
+    case VRC_ERR_TIMEOUT: return "VRC_ERR_TIMEOUT";
+    case VRC_ERR_BUSY: return "VRC_ERR_BUSY";
+    case VRC_ERR_STATE: return "VRC_ERR_STATE";
+    case VRC_ERR_DEVICE: return "VRC_ERR_DEVICE";
+    default: return "VRC_UNKNOWN";
+    }
+}
+
+const char *vrc_last_error_message(vrc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+vrc_status vrc_create(vrc_ctx **out, int device) {
+    if (!out) return VRC_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return VRC_ERR_ARG;
+    vrc_ctx *ctx = new (std::nothrow) vrc_ctx();
+    if (!ctx) return VRC_ERR_OOM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    if (cudaMalloc(&ctx->err_word, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->err_word, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->err_word);
+        delete ctx;
+        return VRC_ERR_CUDA;
+    }
+    *out = ctx;
+    return VRC_OK;
+}
+
+vrc_status vrc_destroy(vrc_ctx *ctx) {
+    if (!ctx) return VRC_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->vols) free_volume(kv.second);
+    for (auto &kv : ctx->tfs) free_tf(kv.second);
+    cudaFree(ctx->err_word);
+    cudaFree(ctx->host_img);
+    delete ctx;
+    return VRC_OK;
+}
+
+vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_dtype dtype,
+                             int nx, int ny, int nz, int *vol_id, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!data || !vol_id) return fail(ctx, VRC_ERR_ARG, "data and vol_id must be non-NULL");
+    if (dtype != VRC_U16 && dtype != VRC_I16 && dtype != VRC_F32)
+        return fail(ctx, VRC_ERR_ARG, "unknown dtype %d", (int)dtype);
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 32768 || ny > 32768 || nz > 32768)
+        return fail(ctx, VRC_ERR_ARG, "volume size %dx%dx%d out of range", nx, ny, nz);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Volume v;
+    v.dtype = dtype;
+    v.n[0] = nx;
+    v.n[1] = ny;
+    v.n[2] = nz;
+    v.pnx = ((nx + 2 * PAD) + 7) / 8 * 8;
+    v.pny = ny + 2 * PAD;
+    v.pnz = nz + 2 * PAD;
+    const size_t es = dtype_size(dtype);
+    const size_t padded = (size_t)v.pnx * v.pny * v.pnz * es;
+    const size_t raw = (size_t)nx * ny * nz * es;
+    if ((size_t)v.pnx * v.pny * v.pnz >= (size_t)1 << 31)
+        return fail(ctx, VRC_ERR_ARG, "volume too large (padded elements must stay below 2^31)");
+    cudaError_t e = cudaMalloc(&v.dpad, padded);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(volume)");
+    const void *src = data;
+    void *staging = nullptr;
+    if (!on_device) {
+        e = cudaMalloc(&staging, raw);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(staging, data, raw, cudaMemcpyHostToDevice, st);
+        src = staging;
+    }
+    if (e == cudaSuccess) e = launch_pad_volume(src, dtype, v.n, v.dpad, v.pnx, v.pny, v.pnz, st);
+    if (staging) {
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+        cudaFree(staging);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(v.dpad);
+        return cuda_fail(ctx, e, "volume upload");
+    }
+    int id = ctx->next_id++;
+    ctx->vols[id] = v;
+    *vol_id = id;
+    return VRC_OK;
+}
+
+vrc_status vrc_volume_free(vrc_ctx *ctx, int vol_id) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    DeviceGuard g(ctx->device);
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize(volume free)");
+    free_volume(*v);
+    ctx->vols.erase(vol_id);
+    return VRC_OK;
+}
+
+vrc_status vrc_volume_info(vrc_ctx *ctx, int vol_id, int *dtype, int *nx, int *ny, int *nz) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    if (dtype) *dtype = v->dtype;
+    if (nx) *nx = v->n[0];
+    if (ny) *ny = v->n[1];
+    if (nz) *nz = v->n[2];
+    return VRC_OK;
+}
+
+vrc_status vrc_bricks_build(vrc_ctx *ctx, int vol_id, int B, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick size must be 8 or 16");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Bricks &b = v->bricks[slot_of(B)];
+    int nb[3];
+    for (int k = 0; k < 3; ++k) nb[k] = (v->n[k] + B - 1) / B;
+    const long count = (long)nb[0] * nb[1] * nb[2];
+    const size_t bytes = (size_t)count * dtype_size(v->dtype);
+    if (!b.mn || b.count() != count) {
+        if (b.mn) CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize(brick realloc)");
+        cudaFree(b.mn);
+        cudaFree(b.mx);
+        b.mn = b.mx = nullptr;
+        CK(cudaMalloc(&b.mn, bytes), "cudaMalloc(bricks)");
+        CK(cudaMalloc(&b.mx, bytes), "cudaMalloc(bricks)");
+    }
+    b.B = B;
+    for (int k = 0; k < 3; ++k) b.nb[k] = nb[k];
+    CK(launch_brick_minmax(view_of(*v), B, b.mn, b.mx, st), "brick launch");
+    b.version++;
+    return VRC_OK;
+}
+
+vrc_status vrc_bricks_get(vrc_ctx *ctx, int vol_id, int B, void *min_host, void *max_host,
+                          void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick size must be 8 or 16");
+    if (!min_host || !max_host) return fail(ctx, VRC_ERR_ARG, "output buffers must be non-NULL");
+    Bricks &b = v->bricks[slot_of(B)];
+    if (!b.mn) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)b.count() * dtype_size(v->dtype);
+    CK(cudaMemcpyAsync(min_host, b.mn, bytes, cudaMemcpyDeviceToHost, st), "bricks copy");
+    CK(cudaMemcpyAsync(max_host, b.mx, bytes, cudaMemcpyDeviceToHost, st), "bricks copy");
+    CK(cudaStreamSynchronize(st), "bricks copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_tf_set(vrc_ctx *ctx, const float *rgba_host, float lo, float hi, int *tf_id) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!tf_id) return fail(ctx, VRC_ERR_ARG, "tf_id is NULL");
+    DeviceGuard g(ctx->device);
+    Tf t;
+    vrc_status s = upload_tf(ctx, t, rgba_host, lo, hi);
+    if (s != VRC_OK) {
+        free_tf(t);
+        return s;
+    }
+    int id = ctx->next_id++;
+    ctx->tfs[id] = t;
+    *tf_id = id;
+    return VRC_OK;
+}
+
+vrc_status vrc_tf_update(vrc_ctx *ctx, int tf_id, const float *rgba_host, float lo, float hi) {
+    if (!ctx) return VRC_ERR_ARG;
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    DeviceGuard g(ctx->device);
+    return upload_tf(ctx, *t, rgba_host, lo, hi);
+}
+
+vrc_status vrc_tf_free(vrc_ctx *ctx, int tf_id) {
+    if (!ctx) return VRC_ERR_ARG;
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    DeviceGuard g(ctx->device);
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize(tf free)");
+    for (auto &kv : ctx->vols) {
+        for (int s = 0; s < 2; ++s) {
+            auto it = kv.second.occ.find((long)tf_id * 2 + s);
+            if (it != kv.second.occ.end()) {
+                cudaFree(it->second.dev);
+                kv.second.occ.erase(it);
+            }
+        }
+    }
+    free_tf(*t);
+    ctx->tfs.erase(tf_id);
+    return VRC_OK;
+}
+
+vrc_status vrc_occupancy_build(vrc_ctx *ctx, int vol_id, int tf_id, int B, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick size must be 8 or 16");
+    DeviceGuard g(ctx->device);
+    const uint8_t *occ = nullptr;
+    return ensure_occ(ctx, *v, tf_id, *t, B, (cudaStream_t)stream, &occ);
+}
+
+vrc_status vrc_occupancy_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint8_t *occ_host,
+                             void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick size must be 8 or 16");
+    if (!occ_host) return fail(ctx, VRC_ERR_ARG, "occ_host is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t *occ = nullptr;
+    vrc_status s = ensure_occ(ctx, *v, tf_id, *t, B, st, &occ);
+    if (s != VRC_OK) return s;
+    CK(cudaMemcpyAsync(occ_host, occ, (size_t)v->bricks[slot_of(B)].count(),
+                       cudaMemcpyDeviceToHost, st), "occupancy copy");
+    CK(cudaStreamSynchronize(st), "occupancy copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                      const vrc_params *params, float *out_rgba_dev,
+                      unsigned long long *counters_dev, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!out_rgba_dev) return fail(ctx, VRC_ERR_ARG, "out_rgba_dev is NULL");
+    if (((uintptr_t)out_rgba_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be 16-byte aligned");
+    if (counters_dev && ((uintptr_t)counters_dev & 7) != 0)
+        return fail(ctx, VRC_ERR_ARG, "counters_dev must be 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    RenderLaunch L;
+    vrc_status s = prepare_render(ctx, vol_id, tf_id, cam, params, st, L);
+    if (s != VRC_OK) return s;
+    L.out = (float4 *)out_rgba_dev;
+    L.counters = counters_dev;
+    CK(launch_render_ray(L, st), "render launch");
+    return VRC_OK;
+}
+
+vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                           const vrc_params *params, float *out_rgba_host, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!out_rgba_host) return fail(ctx, VRC_ERR_ARG, "out_rgba_host is NULL");
+    if (!cam) return fail(ctx, VRC_ERR_ARG, "camera is NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return fail(ctx, VRC_ERR_ARG, "image size out of range");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)cam->width * cam->height * sizeof(float4);
+    if (ctx->host_img_bytes < bytes) {
+        CK(cudaStreamSynchronize(st), "sync before image realloc");
+        cudaFree(ctx->host_img);
+        ctx->host_img = nullptr;
+        ctx->host_img_bytes = 0;
+        CK(cudaMalloc(&ctx->host_img, bytes), "cudaMalloc(image)");
+        ctx->host_img_bytes = bytes;
+    }
+    RenderLaunch L;
+    vrc_status s = prepare_render(ctx, vol_id, tf_id, cam, params, st, L);
+    if (s != VRC_OK) return s;
+    L.out = ctx->host_img;
+    L.counters = nullptr;
+    CK(launch_render_ray(L, st), "render launch");
+    CK(cudaMemcpyAsync(out_rgba_host, ctx->host_img, bytes, cudaMemcpyDeviceToHost, st),
+       "image copy");
+    CK(cudaStreamSynchronize(st), "image copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_last_device_error(vrc_ctx *ctx, int *code, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!code) return fail(ctx, VRC_ERR_ARG, "code is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost, st), "error word read");
+    CK(cudaMemsetAsync(ctx->err_word, 0, sizeof(int), st), "error word clear");
+    CK(cudaStreamSynchronize(st), "error word sync");
+    *code = h;
+    return VRC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+// Device-side building blocks shared by the libvrc kernels: double-float arithmetic for the
+// per-ray setup, the camera and ray records, sample placement, cubic B-spline weights and
+// post-classification. Everything here is sm_103a device code (some helpers are also usable
+// on the host for the camera precomputation).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define VRC_HD __host__ __device__ __forceinline__
+
+namespace vrc {
+
+// ----------------------------------------------------------------------------------------
+// Double-float ("float-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// Error-free transformations after Dekker (1971) and Knuth (TAOCP vol. 2, 4.2.2); products
+// use a fused multiply-add for the exact error term. Used for the per-ray setup only, where a
+// float32 ray origin or entry distance (coordinates up to ~2000 voxels) would move every
+// sample by ~1e-4 voxel.
+struct ff {
+    float hi, lo;
+};
+
+VRC_HD ff ff_make(float a) { return {a, 0.0f}; }
+
+VRC_HD ff two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+VRC_HD ff quick_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    float s = a + b;
+    float e = b - (s - a);
+    return {s, e};
+}
+
+VRC_HD ff two_prod(float a, float b) {
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    return {p, e};
+}
+
+VRC_HD ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    ff t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+
+VRC_HD ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+VRC_HD ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+VRC_HD ff ff_mul(ff a, ff b) {
+    ff p = two_prod(a.hi, b.hi);
+    p.lo = fmaf(a.hi, b.lo, p.lo);
+    p.lo = fmaf(a.lo, b.hi, p.lo);
+    return quick_two_sum(p.hi, p.lo);
+}
+
+VRC_HD ff ff_mul_f(ff a, float b) {
+    ff p = two_prod(a.hi, b);
+    p.lo = fmaf(a.lo, b, p.lo);
+    return quick_two_sum(p.hi, p.lo);
+}
+
+// a / b: one float quotient, then a correction from the exact remainder (long division).
+VRC_HD ff ff_div(ff a, ff b) {
+    float q1 = a.hi / b.hi;
+    ff r = ff_sub(a, ff_mul_f(b, q1));
+    float q2 = r.hi / b.hi;
+    ff q = quick_two_sum(q1, q2);
+    r = ff_sub(a, ff_mul(b, q));
+    float q3 = r.hi / b.hi;
+    return ff_add(q, ff_make(q3));
+}
+
+// 1/sqrt(a) for a > 0: float estimate refined by Newton's iteration y += y (1 - a y^2) / 2
+// evaluated in double-float.
+VRC_HD ff ff_rsqrt(ff a) {
+    float y0 = 1.0f / sqrtf(a.hi);
+    ff y = ff_make(y0);
+    for (int it = 0; it < 2; ++it) {
+        ff e = ff_sub(ff_make(1.0f), ff_mul(a, ff_mul(y, y)));
+        y = ff_add(y, ff_mul_f(ff_mul(y, e), 0.5f));
+    }
+    return y;
+}
+
+VRC_HD bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// ----------------------------------------------------------------------------------------
+// Camera as consumed by the kernels: per-pixel affine maps evaluated in double-float.
+//   perspective: origin = eye, direction = normalize(A + X * Bx + Y * By)
+//   orthographic: origin = A + X * Bx + Y * By, direction = dir
+// with X = 2 px + 1, Y = 2 py + 1 (exact small integers). The host builds A, Bx, By in
+// double from the float camera record and splits each into hi + lo.
+struct CamDev {
+    ff A[3], Bx[3], By[3];
+    ff eye[3];
+    ff dir[3];
+    int ortho;
+    int width, height;
+};
+
+// Box and sampling parameters of one render.
+struct RayGrid {
+    int n[3];        // volume size
+    float step;      // ds
+    float ert;       // early termination threshold (>= 1: off)
+};
+
+struct RaySetup {
+    ff pin[3];   // entry point
+    ff d[3];     // unit direction
+    ff L;        // t_out - t_in
+    int nseg;    // number of segments (0 = miss)
+};
+
+__device__ __forceinline__ void ray_setup(const CamDev &cam, const RayGrid &g, int px, int py,
+                                          RaySetup &r) {
+    const float X = (float)(2 * px + 1), Y = (float)(2 * py + 1);
+    ff o[3], d[3];
+    if (cam.ortho) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = ff_add(cam.A[k], ff_add(ff_mul_f(cam.Bx[k], X), ff_mul_f(cam.By[k], Y)));
+            d[k] = cam.dir[k];
+        }
+    } else {
+        ff D[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            D[k] = ff_add(cam.A[k], ff_add(ff_mul_f(cam.Bx[k], X), ff_mul_f(cam.By[k], Y)));
+            o[k] = cam.eye[k];
+        }
+        ff n2 = ff_add(ff_mul(D[0], D[0]), ff_add(ff_mul(D[1], D[1]), ff_mul(D[2], D[2])));
+        ff inv = ff_rsqrt(n2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = ff_mul(D[k], inv);
+    }
+    ff t0 = ff_make(0.0f);
+    ff t1 = ff_make(INFINITY);
+    bool miss = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = -0.5f, hi = (float)g.n[k] - 0.5f;
+        if (d[k].hi != 0.0f) {
+            ff ta = ff_div(ff_sub(ff_make(lo), o[k]), d[k]);
+            ff tb = ff_div(ff_sub(ff_make(hi), o[k]), d[k]);
+            if (ff_lt(tb, ta)) {
+                ff tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            if (ff_lt(t0, ta)) t0 = ta;
+            if (ff_lt(tb, t1)) t1 = tb;
+        } else {
+            ff o_lo = ff_sub(o[k], ff_make(lo)), o_hi = ff_sub(ff_make(hi), o[k]);
+            if (ff_lt(o_lo, ff_make(0.0f)) || ff_lt(o_hi, ff_make(0.0f))) miss = true;
+        }
+    }
+    r.nseg = 0;
+    if (miss || !ff_lt(t0, t1)) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.d[k] = d[k];
+        r.pin[k] = ff_add(o[k], ff_mul(t0, d[k]));
+    }
+    r.L = ff_sub(t1, t0);
+    float Lf = r.L.hi + r.L.lo;
+    float ns = ceilf(Lf / g.step);
+    if (!(ns >= 1.0f)) ns = 1.0f;          // L > 0: at least one (short) segment
+    if (!(ns <= 16777216.0f)) return;      // NaN or absurd: treat as a miss
+    r.nseg = (int)ns;
+}
+
+// ----------------------------------------------------------------------------------------
+// Sample placement. Samples are grouped in blocks of ANCHOR_K; each block has an anchor
+// point P_a = pin + (a * K * ds) d evaluated in double-float and split into an integer part
+// I (per axis) and a float remainder r in [0, 1). A sample j of block a then sits at
+// I + r + m_rel d, m_rel = (midpoint of j) - a K ds, a float of magnitude <= K ds, so its
+// fractional coordinate carries ~1e-6 voxel error at any volume size. Positions depend on
+// j only (never accumulated), identically with or without empty-space leaping.
+constexpr int ANCHOR_SHIFT = 5;
+constexpr int ANCHOR_K = 1 << ANCHOR_SHIFT;
+
+struct Anchor {
+    int blk;       // anchor block index
+    int I[3];      // integer part
+    float r[3];    // remainder in [0, 1)
+};
+
+__device__ __forceinline__ void make_anchor(const RaySetup &ray, float step, int blk, Anchor &an) {
+    ff m = two_prod((float)(blk << ANCHOR_SHIFT), step);
+    an.blk = blk;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ff P = ff_add(ray.pin[k], ff_mul(m, ray.d[k]));
+        float I = floorf(P.hi);
+        float r = (P.hi - I) + P.lo;
+        if (r < 0.0f) {
+            r += 1.0f;
+            I -= 1.0f;
+        } else if (r >= 1.0f) {
+            r -= 1.0f;
+            I += 1.0f;
+        }
+        an.I[k] = (int)I;
+        an.r[k] = r;
+    }
+}
+
+// Segment j: length delta and midpoint relative to the start of its anchor block.
+__device__ __forceinline__ void segment_rel(const RaySetup &ray, float step, int j, int blk,
+                                            float &delta, float &mrel) {
+    if (j < ray.nseg - 1) {
+        delta = step;
+        mrel = ((float)(j - (blk << ANCHOR_SHIFT)) + 0.5f) * step;
+    } else {
+        // last (possibly short) segment: delta = L - j ds in double-float
+        ff a = two_prod((float)j, step);
+        ff dl = ff_sub(ray.L, a);
+        delta = dl.hi + dl.lo;
+        if (delta > step) delta = step;
+        mrel = (float)(j - (blk << ANCHOR_SHIFT)) * step + 0.5f * delta;
+    }
+}
+
+// floor() of a float of magnitude < 2^22 and its integer, via rounding toward -inf onto
+// the integer grid of 1.5 * 2^23 (one add with a directed rounding mode).
+__device__ __forceinline__ float floor_small(float q, int &iq) {
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    float y = __fadd_rd(q, M);
+    iq = __float_as_int(y) - 0x4B400000;
+    return y - M;
+}
+
+// Integer voxel coordinate (clamped to [-1, n-1]) and fraction of sample at m_rel.
+__device__ __forceinline__ void sample_pos(const Anchor &an, const RaySetup &ray, float mrel,
+                                           const int n[3], int ip[3], float f[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float q = fmaf(mrel, ray.d[k].hi, an.r[k]);
+        int iq;
+        float fq = floor_small(q, iq);
+        f[k] = q - fq;
+        int v = an.I[k] + iq;
+        v = max(v, -1);
+        v = min(v, n[k] - 1);
+        ip[k] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Uniform cubic B-spline weights of the taps at i-1 .. i+2 for a sample at i + f.
+__device__ __forceinline__ void bspline_w(float f, float w[4]) {
+    const float s6 = 1.0f / 6.0f;
+    float f2 = f * f;
+    float f3 = f2 * f;
+    float g = 1.0f - f;
+    w[0] = g * g * g * s6;
+    w[3] = f3 * s6;
+    w[1] = fmaf(0.5f, f3, 2.0f / 3.0f - f2);           // (3f^3 - 6f^2 + 4) / 6
+    w[2] = 1.0f - w[0] - w[1] - w[3];                   // partition of unity
+}
+
+constexpr float ALPHA_MAX = 0.99999994039535522f;  // 1 - 2^-24
+
+// Opacity of a segment of length delta for table opacity a per unit length.
+__device__ __forceinline__ float segment_alpha(float a, float delta) {
+    a = fminf(fmaxf(a, 0.0f), ALPHA_MAX);
+    return 1.0f - exp2f(delta * __log2f(1.0f - a));
+}
+
+}  // namespace vrc

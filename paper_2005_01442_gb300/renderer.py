@@ -1,0 +1,180 @@
+"""Python face of libvrc: a context object holding resident volumes, brick tables and
+transfer functions, with torch tensors for device memory and torch streams for ordering.
+
+Only marshalling happens here; every step of the method runs in the library's CUDA kernels.
+Volumes are arrays of shape (nz, ny, nx) (x fastest) of uint16, int16 or float32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import native
+
+_DT = {np.dtype(np.uint16): native.VRC_U16, np.dtype(np.int16): native.VRC_I16,
+       np.dtype(np.float32): native.VRC_F32}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+class Renderer:
+    """One libvrc context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libvrc needs a CUDA device")
+        self.lib = native.load()
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        ctx = C.c_void_p()
+        native.check(None, self.lib.vrc_create(C.byref(ctx), self.device))
+        self.ctx = ctx
+        self._vols = {}
+
+    # -- lifetime -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.vrc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _ck(self, status):
+        native.check(self.ctx, status)
+
+    # -- volumes --------------------------------------------------------------------------
+    def upload_volume(self, vol, stream=None) -> int:
+        """Makes `vol` ((nz, ny, nx) numpy array or CUDA tensor) resident; returns its id."""
+        torch = _torch()
+        vid = C.c_int()
+        if isinstance(vol, torch.Tensor) and vol.is_cuda:
+            t = vol.contiguous()
+            dt = {torch.uint16: native.VRC_U16, torch.int16: native.VRC_I16,
+                  torch.float32: native.VRC_F32}[t.dtype]
+            nz, ny, nx = t.shape
+            self._ck(self.lib.vrc_volume_upload(self.ctx, C.c_void_p(t.data_ptr()), 1, dt, nx, ny,
+                                                nz, C.byref(vid), _stream_ptr(stream)))
+            torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        else:
+            a = np.ascontiguousarray(vol)
+            nz, ny, nx = a.shape
+            self._ck(self.lib.vrc_volume_upload(self.ctx, a.ctypes.data_as(C.c_void_p), 0,
+                                                _DT[a.dtype], nx, ny, nz, C.byref(vid),
+                                                _stream_ptr(stream)))
+        self._vols[vid.value] = None
+        return vid.value
+
+    def free_volume(self, vol_id: int):
+        self._ck(self.lib.vrc_volume_free(self.ctx, int(vol_id)))
+        self._vols.pop(vol_id, None)
+
+    def volume_info(self, vol_id: int):
+        dt, nx, ny, nz = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._ck(self.lib.vrc_volume_info(self.ctx, int(vol_id), C.byref(dt), C.byref(nx),
+                                          C.byref(ny), C.byref(nz)))
+        return dt.value, (nx.value, ny.value, nz.value)
+
+    def build_bricks(self, vol_id: int, B: int, stream=None):
+        self._ck(self.lib.vrc_bricks_build(self.ctx, int(vol_id), int(B), _stream_ptr(stream)))
+
+    def bricks(self, vol_id: int, B: int, stream=None):
+        """Host copies of the (min, max) brick tables, shape (nbz, nby, nbx)."""
+        dt, (nx, ny, nz) = self.volume_info(vol_id)
+        npdt = {native.VRC_U16: np.uint16, native.VRC_I16: np.int16, native.VRC_F32: np.float32}[dt]
+        nb = tuple((n + B - 1) // B for n in (nz, ny, nx))
+        mn = np.empty(nb, npdt)
+        mx = np.empty(nb, npdt)
+        self._ck(self.lib.vrc_bricks_get(self.ctx, int(vol_id), int(B),
+                                         mn.ctypes.data_as(C.c_void_p),
+                                         mx.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return mn, mx
+
+    # -- transfer functions -----------------------------------------------------------------
+    def set_tf(self, rgba, lo: float, hi: float) -> int:
+        t = np.ascontiguousarray(rgba, np.float32).reshape(256, 4)
+        tid = C.c_int()
+        self._ck(self.lib.vrc_tf_set(self.ctx, t.ctypes.data_as(C.c_void_p), float(lo),
+                                     float(hi), C.byref(tid)))
+        return tid.value
+
+    def update_tf(self, tf_id: int, rgba, lo: float, hi: float):
+        t = np.ascontiguousarray(rgba, np.float32).reshape(256, 4)
+        self._ck(self.lib.vrc_tf_update(self.ctx, int(tf_id), t.ctypes.data_as(C.c_void_p),
+                                        float(lo), float(hi)))
+
+    def free_tf(self, tf_id: int):
+        self._ck(self.lib.vrc_tf_free(self.ctx, int(tf_id)))
+
+    def build_occupancy(self, vol_id: int, tf_id: int, B: int, stream=None):
+        self._ck(self.lib.vrc_occupancy_build(self.ctx, int(vol_id), int(tf_id), int(B),
+                                              _stream_ptr(stream)))
+
+    def occupancy(self, vol_id: int, tf_id: int, B: int, stream=None):
+        _, (nx, ny, nz) = self.volume_info(vol_id)
+        nb = tuple((n + B - 1) // B for n in (nz, ny, nx))
+        occ = np.empty(nb, np.uint8)
+        self._ck(self.lib.vrc_occupancy_get(self.ctx, int(vol_id), int(tf_id), int(B),
+                                            occ.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return occ
+
+    # -- rendering ----------------------------------------------------------------------------
+    def render(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
+               brick: int = 0, out=None, counters=None, stream=None, kernel: int = 0):
+        """Renders into a (H, W, 4) float32 CUDA tensor (allocated when `out` is None).
+        `counters`: optional int64 CUDA tensor of 2 elements incremented by (nominal,
+        executed) samples."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == cam.height * cam.width * 4
+        cptr = None
+        if counters is not None:
+            assert counters.is_cuda and counters.dtype == torch.int64 and counters.numel() == 2
+            cptr = C.c_void_p(counters.data_ptr())
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, ert, brick, 64, kernel)
+        self._ck(self.lib.vrc_render(self.ctx, int(vol_id), int(tf_id), C.byref(cs), C.byref(ps),
+                                     C.c_void_p(out.data_ptr()), cptr, _stream_ptr(stream)))
+        return out
+
+    def render_host(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
+                    brick: int = 0, out=None, stream=None, kernel: int = 0):
+        """End-to-end render into host memory (pinned torch tensor or numpy array)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32, pin_memory=True)
+        ptr = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, ert, brick, 64, kernel)
+        self._ck(self.lib.vrc_render_host(self.ctx, int(vol_id), int(tf_id), C.byref(cs),
+                                          C.byref(ps), C.c_void_p(ptr), _stream_ptr(stream)))
+        return out
+
+    def last_device_error(self, stream=None) -> int:
+        code = C.c_int()
+        self._ck(self.lib.vrc_last_device_error(self.ctx, C.byref(code), _stream_ptr(stream)))
+        return code.value

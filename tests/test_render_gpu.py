@@ -1,0 +1,265 @@
+"""GPU parity of libvrc against the FP64 oracle, through the C ABI.
+
+Tolerances: images within max |d| <= 1e-4 per RGBA channel of the oracle; brick tables and
+occupancy bytes bit-exact; empty-space leaping bit-identical to no leaping. Where early ray
+termination is on, a pixel whose opacity passes the threshold within 1e-5 of it may stop one
+sample apart in float32 and float64; such pixels (flagged by the oracle's margin) are held to
+the termination bound 1e-3 instead.
+"""
+import numpy as np
+import pytest
+
+from paper_2005_01442_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+ERT_MARGIN = 1e-5
+ERT_BOUND = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def R(torch):
+    from paper_2005_01442_gb300 import build
+    from paper_2005_01442_gb300.renderer import Renderer
+    build.build()
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def _check(img, ref, margin=None, tol=TOL):
+    img = np.asarray(img, np.float64).reshape(ref.shape)
+    d = np.abs(img - ref).max(axis=-1)
+    if margin is not None:
+        flagged = margin.reshape(d.shape) < ERT_MARGIN
+        assert d[~flagged].max(initial=0.0) <= tol, d[~flagged].max(initial=0.0)
+        assert d[flagged].max(initial=0.0) <= ERT_BOUND
+        return d, flagged
+    assert d.max() <= tol, (d.max(), np.unravel_index(d.argmax(), d.shape))
+    return d, None
+
+
+def _ct_small(seed=21, shape=(48, 64, 72)):
+    return synth.ct_volume(shape, seed=seed)
+
+
+# ------------------------------------------------------------------- a1, a2: exact tables
+
+@pytest.mark.parametrize("kind", ["u16", "i16", "f32"])
+@pytest.mark.parametrize("B", [8, 16])
+def test_brick_tables_bit_exact(R, orc, kind, B):
+    if kind == "u16":
+        vol = synth.phantom(40, seed=3)[:, :37, :]
+    elif kind == "i16":
+        vol = _ct_small(shape=(45, 50, 61))
+    else:
+        vol = np.random.default_rng(4).normal(0, 50, (33, 29, 47)).astype(np.float32)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, B)
+    mn, mx = R.bricks(vid, B)
+    rmn, rmx = orc.bricks(vol, B)
+    assert mn.dtype == rmn.dtype and np.array_equal(mn, rmn) and np.array_equal(mx, rmx)
+    R.free_volume(vid)
+
+
+@pytest.mark.parametrize("B", [8, 16])
+def test_occupancy_bit_exact(R, orc, B):
+    vol = _ct_small()
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, B)
+    for seed in (None, 1, 2):
+        tf = synth.tf_ct(seed)
+        tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+        occ = R.occupancy(vid, tid, B)
+        ref = orc.occupancy(*orc.bricks(vol, B), tf, synth.CT_LO, synth.CT_HI)
+        assert np.array_equal(occ, ref)
+        R.free_tf(tid)
+    R.free_volume(vid)
+
+
+# ------------------------------------------------------------- a3-a9: images vs the oracle
+
+def test_phantom_orthographic_parity(R, orc, torch):
+    """64^3 uint16 phantom, 128^2 orthographic along +z, step 0.5, no skipping."""
+    vol = synth.phantom()
+    tf = synth.tf_random(2)
+    cam = synth.ortho_z_camera((64, 64, 64), 128, 128)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(tf, synth.PHANTOM_LO, synth.PHANTOM_HI)
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    img = R.render(vid, tid, cam, step=0.5, counters=cnt).cpu().numpy()
+    ref = orc.render(vol, tf, synth.PHANTOM_LO, synth.PHANTOM_HI, cam, 0.5)
+    _check(img, ref)
+    assert cnt.tolist() == [2097152, 2097152]
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+@pytest.mark.parametrize("B", [0, 8, 16])
+@pytest.mark.parametrize("ert", [1.0, 0.999])
+def test_ct_perspective_parity(R, orc, torch, B, ert):
+    vol = _ct_small()
+    tf = synth.tf_ct()
+    vid = R.upload_volume(vol)
+    if B:
+        R.build_bricks(vid, B)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    for cam in synth.orbit_cameras(40, 3, synth.dims_of(vol), 96, 80):
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        img = R.render(vid, tid, cam, step=0.5, ert=ert, brick=B, counters=cnt).cpu().numpy()
+        ref, margin, rc = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=ert,
+                                     brick=B, return_margin=True, return_counts=True)
+        _check(img, ref, margin if ert < 1 else None)
+        assert cnt[0].item() == rc[0] or abs(cnt[0].item() - rc[0]) <= 8  # segment counts
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+def test_empty_space_leaping_bit_identical(R, torch):
+    vol = _ct_small(seed=5)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    R.build_bricks(vid, 16)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    for cam in synth.orbit_cameras(41, 4, synth.dims_of(vol), 120, 90):
+        for ert in (1.0, 0.999):
+            c0 = torch.zeros(2, dtype=torch.int64, device="cuda")
+            ref = R.render(vid, tid, cam, ert=ert, brick=0, counters=c0)
+            for B in (8, 16):
+                c1 = torch.zeros(2, dtype=torch.int64, device="cuda")
+                img = R.render(vid, tid, cam, ert=ert, brick=B, counters=c1)
+                assert torch.equal(img, ref)
+                assert c1[0] == c0[0] and c1[1] < c0[1]
+    R.free_volume(vid)
+
+
+def test_early_termination_bound(R, torch):
+    vol = _ct_small(seed=6)
+    tf = synth.tf_ct().copy()
+    tf[:, 3] = np.minimum(tf[:, 3] * 3.0, 0.95)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    for cam in synth.orbit_cameras(42, 2, synth.dims_of(vol), 96, 80):
+        full = R.render(vid, tid, cam, ert=1.0, brick=8).cpu().numpy().astype(np.float64)
+        ert = R.render(vid, tid, cam, ert=0.999, brick=8).cpu().numpy().astype(np.float64)
+        stopped = ert[..., 3] > 0.999
+        assert stopped.any()
+        d = np.abs(full - ert).max(-1)
+        assert np.all(d[stopped] <= (1.0 - ert[..., 3])[stopped] + 1e-6)
+    R.free_volume(vid)
+
+
+def test_float_volume_and_ragged_sizes(R, orc):
+    rng = np.random.default_rng(9)
+    vol = (rng.normal(0, 1, (13, 17, 19)).cumsum(0) * 40).astype(np.float32)
+    tf = synth.tf_random(7, 5)
+    tf[:, 3] *= 0.4
+    lo, hi = float(vol.min()), float(vol.max())
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, lo, hi)
+    dims = synth.dims_of(vol)
+    for cam in synth.orbit_cameras(43, 2, dims, 37, 23) + [synth.ortho_z_camera(dims, 29, 31)]:
+        for B in (0, 8):
+            img = R.render(vid, tid, cam, step=0.37, brick=B).cpu().numpy()
+            ref = orc.render(vol, tf, lo, hi, cam, 0.37, brick=B)
+            _check(img, ref)
+    R.free_volume(vid)
+
+
+def test_degenerate_cases(R, orc):
+    tf = synth.tf_random(3)
+    # 1x1x1 volume, 1x1 image, step longer than the box
+    vol = np.array([[[1234]]], np.uint16)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(tf, 0, 4095)
+    cam = synth.ortho_z_camera((1, 1, 1), 1, 1)
+    img = R.render(vid, tid, cam, step=3.0).cpu().numpy()
+    _check(img, orc.render(vol, tf, 0, 4095, cam, 3.0))
+    # camera looking away from the volume: every ray misses, black transparent image
+    vol = synth.phantom(16)
+    vid2 = R.upload_volume(vol)
+    away = synth.Camera(0, (7.5, 7.5, -20.0), (7.5, 7.5, -40.0), (0, 1, 0), 30.0, (0, 0), 8, 8)
+    assert np.all(R.render(vid2, tid, away).cpu().numpy() == 0.0)
+    # eye inside the volume
+    inside = synth.Camera(0, (7.3, 8.1, 6.6), (0.0, 3.0, 15.0), (0, 1, 0), 60.0, (0, 0), 16, 12)
+    img = R.render(vid2, tid, inside, step=0.25).cpu().numpy()
+    _check(img, orc.render(vol, tf, 0, 4095, inside, 0.25))
+    R.free_volume(vid)
+    R.free_volume(vid2)
+
+
+def test_invalid_arguments_are_rejected(R, torch):
+    from paper_2005_01442_gb300.native import VrcError
+    vol = synth.phantom(16)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(synth.tf_random(3), 0, 4095)
+    cam = synth.ortho_z_camera((16, 16, 16), 8, 8)
+    with pytest.raises(VrcError, match="VRC_ERR_ARG"):
+        R.render(vid + 1000, tid, cam)
+    with pytest.raises(VrcError, match="VRC_ERR_ARG"):
+        R.render(vid, tid, cam, step=0.0)
+    with pytest.raises(VrcError, match="VRC_ERR_ARG"):
+        R.render(vid, tid, cam, brick=4)
+    with pytest.raises(VrcError, match="VRC_ERR_STATE"):
+        R.render(vid, tid, cam, brick=8)  # no brick table yet
+    with pytest.raises(VrcError, match="VRC_ERR_ARG"):
+        R.set_tf(synth.tf_random(3), 5.0, 5.0)
+    bad = synth.Camera(0, (1, 2, 3), (1, 2, 3), (0, 1, 0), 30.0, (0, 0), 8, 8)
+    with pytest.raises(VrcError, match="VRC_ERR_ARG"):
+        R.render(vid, tid, bad)
+    assert R.last_device_error() == 0
+    R.free_volume(vid)
+
+
+def test_render_host_matches_device(R, torch):
+    vol = _ct_small(seed=8)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 16)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(44, 1, synth.dims_of(vol), 64, 48)[0]
+    dev = R.render(vid, tid, cam, ert=0.999, brick=16).cpu()
+    host = R.render_host(vid, tid, cam, ert=0.999, brick=16)
+    assert torch.equal(dev, host)
+    R.free_volume(vid)
+
+
+# --------------------------------------------------------- full-size CT, sampled pixels
+
+@pytest.fixture(scope="module")
+def ct_full(R):
+    vol = synth.ct_volume()  # 512 x 512 x 400 int16
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    R.build_bricks(vid, 16)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    yield vol, vid, tid
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+@pytest.mark.parametrize("B", [8, 16])
+def test_ct_full_size_sampled_parity(R, orc, torch, ct_full, B):
+    """512^2 x 400 CT, 1024^2 perspective, step 0.5, ESL, ERT 0.999: 4096 sampled pixels per
+    camera against the oracle; ESL bit-identical to no ESL on the whole image."""
+    vol, vid, tid = ct_full
+    tf = synth.tf_ct()
+    rng = np.random.default_rng(B)
+    for cam in synth.orbit_cameras(4, 2, synth.dims_of(vol), 1024, 1024):
+        img = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=B).cpu().numpy()
+        pix = np.stack([rng.integers(0, 1024, 4096), rng.integers(0, 1024, 4096)], -1)
+        ref, margin = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=0.999,
+                                 brick=B, pixels=pix, return_margin=True)
+        _check(img[pix[:, 1], pix[:, 0]], ref, margin)
+        noesl = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=0).cpu().numpy()
+        assert np.array_equal(img, noesl)
