@@ -337,7 +337,7 @@ def main():
                          "basis": f"{FLOPS_PER_SAMPLE} flop/executed sample; peak = {sms} SMs x "
                                   f"{FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
             "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * (2 + args.cameras),
+            "gpu_launches": args.steps * (6 + args.cameras),  # bricks, occupancy, 3 summed-volume passes, distance, frames
             "clocks": clocks,
         }
         if clocks.get("sm_mhz"):

@@ -71,7 +71,7 @@ def lib():
         L.orc_occupancy.argtypes = [vp, vp, ip, C.c_long, vp, C.c_float, C.c_float, vp]
         L.orc_render.argtypes = [vp, ip, ip, ip, ip, vp, C.c_double, C.c_double,
                                  C.POINTER(Camera), C.POINTER(Params), vp, C.POINTER(Ball), vp,
-                                 C.c_long, vp, vp, vp]
+                                 C.c_long, vp, vp, vp, vp]
         L.orc_render_grad.argtypes = [vp, ip, ip, ip, ip, vp, C.c_double, C.c_double,
                                       C.POINTER(Camera), C.POINTER(Params), vp, vp, C.c_long,
                                       vp, vp, vp]
@@ -176,9 +176,10 @@ def _pix(pixels):
 
 
 def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
-           return_margin=False, return_counts=False):
+           return_margin=False, return_counts=False, return_executed=False):
     """FP64 render. Returns float64 (H, W, 4) (or (npix, 4) for a pixel list), plus the ERT
-    margins and the (nominal, executed) sample counts when asked."""
+    margins, the (nominal, executed) sample counts and the per-pixel executed samples when
+    asked."""
     vol = np.ascontiguousarray(vol)
     tf = np.ascontiguousarray(tf, np.float32)
     nz, ny, nx = vol.shape
@@ -191,6 +192,7 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
     out = np.zeros((n, 4), np.float64)
     margin = np.empty(n, np.float64) if return_margin else None
     counts = np.zeros(2, np.int64)
+    expp = np.zeros(n, np.int32) if return_executed else None
     par = Params(float(step), float(ert), int(brick), 0)
     b = None
     if ball is not None:
@@ -198,7 +200,7 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
     rc = lib().orc_render(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
                           float(hi), C.byref(_cam(cam)), C.byref(par), _ptr(occ),
                           C.byref(b) if b is not None else None, _ptr(pix), npix, _ptr(out),
-                          _ptr(margin), _ptr(counts))
+                          _ptr(margin), _ptr(counts), _ptr(expp))
     if rc != 0:
         raise ValueError(f"orc_render failed ({rc})")
     img = out if pix is not None else out.reshape(cam.height, cam.width, 4)
@@ -207,6 +209,8 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
         res.append(margin if pix is not None else margin.reshape(cam.height, cam.width))
     if return_counts:
         res.append((int(counts[0]), int(counts[1])))
+    if return_executed:
+        res.append(expp if pix is not None else expp.reshape(cam.height, cam.width))
     return res[0] if len(res) == 1 else tuple(res)
 
 

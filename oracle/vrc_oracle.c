@@ -504,13 +504,14 @@ static void scene_init(scene_t *S, const orc_volume *v, const orc_ball *ball, co
 
 /* Renders the pixels listed in `pix` (pairs px, py; NULL = the whole image in row-major
  * order). out: npix x 4 doubles. margin (optional): npix doubles. counts (optional): two
- * longs, nominal and executed samples summed over the rendered pixels.
+ * longs, nominal and executed samples summed over the rendered pixels. executed_per_pixel
+ * (optional): npix ints, the executed samples of each pixel.
  * occ: per-brick occupancy for params->brick (required when brick > 0). ball: optional
  * analytic indicator field replacing the volume. */
 int orc_render(const void *data, int dtype, int nx, int ny, int nz, const float *tf, double lo,
                double hi, const orc_camera *cam, const orc_params *par, const uint8_t *occ,
                const orc_ball *ball, const int *pix, long npix, double *out, double *margin,
-               long *counts) {
+               long *counts, int *executed_per_pixel) {
     if (!cam || !par || !out || !tf || par->step <= 0.0 || !(hi > lo)) return ORC_EARG;
     if (par->brick > 0 && !occ) return ORC_EARG;
     orc_volume v = {data, dtype, {nx, ny, nz}};
@@ -527,6 +528,7 @@ int orc_render(const void *data, int dtype, int nx, int ny, int nz, const float 
         ray_stats_t st;
         render_ray(&S, cam, dims, px, py, out + 4 * i, &mg, &st);
         if (margin) margin[i] = mg;
+        if (executed_per_pixel) executed_per_pixel[i] = (int)st.executed;
         nominal += st.nominal;
         executed += st.executed;
     }

@@ -41,6 +41,54 @@ cudaError_t launch_pad_volume(const void *src, int dtype, const int n[3], void *
     return cudaGetLastError();
 }
 
+// Render layout: float4 entries replicated along x. Entry (x', y', z') holds the four voxels
+// x'-2 .. x'+1 of row (y'-2, z'-2), each index clamped to the volume (clamp-to-edge), for
+// x' in [0, nx], y' in [0, ny+3], z' in [0, nz+3]. A cubic B-spline sample with integer base
+// i reads its 16 tap rows as 16 aligned 16-byte loads of entries (i0+1, i1+1+b, i2+1+c).
+template <typename T>
+__global__ void replicate_x4_kernel(const T *__restrict__ src, int nx, int ny, int nz,
+                                    float4 *__restrict__ dst, int rnx, int rny, int rnz) {
+    long total = (long)rnx * rny * rnz;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % rnx);
+        const int y = (int)((i / rnx) % rny);
+        const int z = (int)(i / ((long)rnx * rny));
+        const int sy = min(max(y - 2, 0), ny - 1);
+        const int sz = min(max(z - 2, 0), nz - 1);
+        const T *row = src + ((long)sz * ny + sy) * nx;
+        float4 e;
+        e.x = (float)row[min(max(x - 2, 0), nx - 1)];
+        e.y = (float)row[min(max(x - 1, 0), nx - 1)];
+        e.z = (float)row[min(max(x, 0), nx - 1)];
+        e.w = (float)row[min(max(x + 1, 0), nx - 1)];
+        dst[i] = e;
+    }
+}
+
+cudaError_t launch_replicate_x4(const void *src, int dtype, const int n[3], float4 *dst,
+                                cudaStream_t st) {
+    const int rnx = n[0] + 1, rny = n[1] + 4, rnz = n[2] + 4;
+    long total = (long)rnx * rny * rnz;
+    int threads = 256;
+    long blocks = (total + threads - 1) / threads;
+    if (blocks > 152L * 64) blocks = 152L * 64;
+    switch (dtype) {
+    case DT_U16:
+        replicate_x4_kernel<uint16_t><<<(unsigned)blocks, threads, 0, st>>>(
+            (const uint16_t *)src, n[0], n[1], n[2], dst, rnx, rny, rnz);
+        break;
+    case DT_I16:
+        replicate_x4_kernel<int16_t><<<(unsigned)blocks, threads, 0, st>>>(
+            (const int16_t *)src, n[0], n[1], n[2], dst, rnx, rny, rnz);
+        break;
+    default:
+        replicate_x4_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(
+            (const float *)src, n[0], n[1], n[2], dst, rnx, rny, rnz);
+    }
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ brick min/max ------
 template <typename T>
 struct Lim;
@@ -65,63 +113,73 @@ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
-// One warp per brick: lanes sweep the apron box row by row (x fastest, coalesced within a
-// row), then a warp reduction. Exact for every dtype (min/max involve no rounding).
+// One CTA per brick row (by, bz): thread x handles brick bx (64 at a time) and sweeps the x
+// apron [bx*B-1, bx*B+B+1] of every row of the (y, z) apron, thread y interleaves those rows;
+// partial min/max are combined through shared memory. Each voxel is read from HBM about once
+// (neighbouring rows of bricks re-read the overlap through L2). Exact for every dtype.
+constexpr int BM_TX = 64, BM_TY = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(256) brick_minmax_kernel(VolView v, int B, int nbx, int nby,
-                                                           int nbz, T *__restrict__ mn,
-                                                           T *__restrict__ mx) {
-    const int lane = threadIdx.x & 31;
-    const long warp = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
-    const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
-    const long total = (long)nbx * nby * nbz;
+__global__ void __launch_bounds__(BM_TX *BM_TY) brick_minmax_kernel(VolView v, int B, int nbx,
+                                                                     int nby, int nbz,
+                                                                     T *__restrict__ mn,
+                                                                     T *__restrict__ mx) {
+    __shared__ T s_lo[BM_TY][BM_TX], s_hi[BM_TY][BM_TX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int by = blockIdx.x % nby, bz = blockIdx.x / nby;
+    if (bz >= nbz) return;
+    const int y0 = max(by * B - 1, 0), y1 = min(by * B + B + 1, v.n[1] - 1);
+    const int z0 = max(bz * B - 1, 0), z1 = min(bz * B + B + 1, v.n[2] - 1);
+    const int wy = y1 - y0 + 1, rows = wy * (z1 - z0 + 1);
     const T *base = (const T *)v.base;
-    for (long b = warp; b < total; b += nwarps) {
-        int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long)nbx * nby));
-        int x0 = max(bx * B - 1, 0), x1 = min(bx * B + B + 1, v.n[0] - 1);
-        int y0 = max(by * B - 1, 0), y1 = min(by * B + B + 1, v.n[1] - 1);
-        int z0 = max(bz * B - 1, 0), z1 = min(bz * B + B + 1, v.n[2] - 1);
-        int wx = x1 - x0 + 1, wy = y1 - y0 + 1, wz = z1 - z0 + 1;
-        int cnt = wx * wy * wz;
+    for (int bx0 = 0; bx0 < nbx; bx0 += BM_TX) {
+        const int bx = bx0 + tx;
         T lo = Lim<T>::hi(), hi = Lim<T>::lo();
-        for (int i = lane; i < cnt; i += 32) {
-            int x = i % wx, r = i / wx;
-            int y = r % wy, z = r / wy;
-            long idx = ((long)(z0 + z + PAD) * v.pny + (y0 + y + PAD)) * v.pnx + (x0 + x + PAD);
-            T val = base[idx];
-            lo = tmin(lo, val);
-            hi = tmax(hi, val);
+        if (bx < nbx) {
+            const int x0 = max(bx * B - 1, 0), x1 = min(bx * B + B + 1, v.n[0] - 1);
+            for (int r = ty; r < rows; r += BM_TY) {
+                const int y = y0 + r % wy, z = z0 + r / wy;
+                const T *row = base + ((long)(z + PAD) * v.pny + (y + PAD)) * v.pnx + PAD;
+                for (int x = x0; x <= x1; ++x) {
+                    const T val = row[x];
+                    lo = tmin(lo, val);
+                    hi = tmax(hi, val);
+                }
+            }
         }
+        s_lo[ty][tx] = lo;
+        s_hi[ty][tx] = hi;
+        __syncthreads();
+        if (ty == 0 && bx < nbx) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = tmin(lo, (T)__shfl_xor_sync(0xffffffffu, lo, o));
-            hi = tmax(hi, (T)__shfl_xor_sync(0xffffffffu, hi, o));
+            for (int k = 1; k < BM_TY; ++k) {
+                lo = tmin(lo, s_lo[k][tx]);
+                hi = tmax(hi, s_hi[k][tx]);
+            }
+            const long o = ((long)bz * nby + by) * nbx + bx;
+            mn[o] = lo;
+            mx[o] = hi;
         }
-        if (lane == 0) {
-            mn[b] = lo;
-            mx[b] = hi;
-        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_brick_minmax(const VolView &v, int B, void *mn, void *mx, cudaStream_t st) {
     int nb[3];
     for (int k = 0; k < 3; ++k) nb[k] = (v.n[k] + B - 1) / B;
-    long total = (long)nb[0] * nb[1] * nb[2];
-    int threads = 256;
-    long blocks = (total * 32 + threads - 1) / threads;
-    if (blocks > 152L * 32) blocks = 152L * 32;
+    const unsigned blocks = (unsigned)nb[1] * (unsigned)nb[2];
+    const dim3 threads(BM_TX, BM_TY);
     switch (v.dtype) {
     case DT_U16:
-        brick_minmax_kernel<uint16_t><<<(unsigned)blocks, threads, 0, st>>>(
+        brick_minmax_kernel<uint16_t><<<blocks, threads, 0, st>>>(
             v, B, nb[0], nb[1], nb[2], (uint16_t *)mn, (uint16_t *)mx);
         break;
     case DT_I16:
-        brick_minmax_kernel<int16_t><<<(unsigned)blocks, threads, 0, st>>>(
+        brick_minmax_kernel<int16_t><<<blocks, threads, 0, st>>>(
             v, B, nb[0], nb[1], nb[2], (int16_t *)mn, (int16_t *)mx);
         break;
     default:
-        brick_minmax_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(
+        brick_minmax_kernel<float><<<blocks, threads, 0, st>>>(
             v, B, nb[0], nb[1], nb[2], (float *)mn, (float *)mx);
     }
     return cudaGetLastError();
@@ -175,6 +233,112 @@ cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbr
         occupancy_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(
             (const float *)mn, (const float *)mx, nbricks, prefix_dev, lo, du, occ);
     }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- empty-box distance (leaping) ----
+// For each of the 8 direction octants s = (sx, sy, sz) in {+1, -1}^3 and each brick b:
+// dist[oct][b] = 0 for an occupied brick, else the smallest r >= 1 such that the forward box
+// of bricks {b + t : t_k between 0 and r s_k} holds an occupied brick (capped at 255). Every
+// brick of the forward box of extent r - 1 is empty, so a ray whose direction lies in that
+// octant may leap from b to the exit of that box. Computed from a summed-volume table of the
+// occupancy bytes; octant index = (sx < 0) | (sy < 0) << 1 | (sz < 0) << 2.
+
+// S has (nbz+1) x (nby+1) x (nbx+1) ints; first pass: S[z+1][y+1][x+1] = sum_{x'<=x} occ.
+__global__ void svt_x_kernel(const uint8_t *__restrict__ occ, int nbx, int nby, int nbz,
+                             int *__restrict__ S) {
+    const int sx = nbx + 1, sy = nby + 1;
+    long lines = (long)(nby + 1) * (nbz + 1);
+    for (long l = blockIdx.x * (long)blockDim.x + threadIdx.x; l < lines;
+         l += (long)gridDim.x * blockDim.x) {
+        int y = (int)(l % sy), z = (int)(l / sy);
+        int *row = S + ((long)z * sy + y) * sx;
+        int acc = 0;
+        row[0] = 0;
+        for (int x = 0; x < nbx; ++x) {
+            if (y > 0 && z > 0) acc += occ[((long)(z - 1) * nby + (y - 1)) * nbx + x];
+            row[x + 1] = acc;
+        }
+    }
+}
+
+// prefix sums along y (axis = 1) or z (axis = 2) of S in place
+__global__ void svt_yz_kernel(int nbx, int nby, int nbz, int axis, int *__restrict__ S) {
+    const long sx = nbx + 1, sy = nby + 1, sz = nbz + 1;
+    const long lines = axis == 1 ? sx * sz : sx * sy;
+    const long stride = axis == 1 ? sx : sx * sy;
+    const int len = axis == 1 ? (int)sy : (int)sz;
+    for (long l = blockIdx.x * (long)blockDim.x + threadIdx.x; l < lines;
+         l += (long)gridDim.x * blockDim.x) {
+        long base = axis == 1 ? (l % sx) + (l / sx) * sx * sy : l;
+        int acc = 0;
+        for (int i = 0; i < len; ++i) {
+            acc += S[base + i * stride];
+            S[base + i * stride] = acc;
+        }
+    }
+}
+
+__device__ __forceinline__ int svt_at(const int *S, int sx, int sy, int x, int y, int z) {
+    return S[((long)z * sy + y) * sx + x];
+}
+
+__global__ void box_dist_kernel(const uint8_t *__restrict__ occ, const int *__restrict__ S,
+                                int nbx, int nby, int nbz, uint8_t *__restrict__ dist) {
+    const int sx = nbx + 1, sy = nby + 1;
+    const long n = (long)nbx * nby * nbz;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < 8 * n;
+         q += (long)gridDim.x * blockDim.x) {
+        const int oct = (int)(q / n);
+        const long i = q % n;
+        if (occ[i]) {
+            dist[q] = 0;
+            continue;
+        }
+        const int bx = (int)(i % nbx), by = (int)((i / nbx) % nby), bz = (int)(i / ((long)nbx * nby));
+        const bool nx_ = oct & 1, ny_ = oct & 2, nz_ = oct & 4;
+        auto count = [&](int r) {
+            int x0 = nx_ ? max(bx - r, 0) : bx, x1 = (nx_ ? bx : min(bx + r, nbx - 1)) + 1;
+            int y0 = ny_ ? max(by - r, 0) : by, y1 = (ny_ ? by : min(by + r, nby - 1)) + 1;
+            int z0 = nz_ ? max(bz - r, 0) : bz, z1 = (nz_ ? bz : min(bz + r, nbz - 1)) + 1;
+            return svt_at(S, sx, sy, x1, y1, z1) - svt_at(S, sx, sy, x0, y1, z1) -
+                   svt_at(S, sx, sy, x1, y0, z1) - svt_at(S, sx, sy, x1, y1, z0) +
+                   svt_at(S, sx, sy, x0, y0, z1) + svt_at(S, sx, sy, x0, y1, z0) +
+                   svt_at(S, sx, sy, x1, y0, z0) - svt_at(S, sx, sy, x0, y0, z0);
+        };
+        int lo = 1, hi = 255;  // smallest r in [lo, hi] with count(r) > 0, else 255
+        if (count(hi) == 0) {
+            dist[q] = 255;
+            continue;
+        }
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (count(mid) > 0) hi = mid;
+            else lo = mid + 1;
+        }
+        dist[q] = (uint8_t)lo;
+    }
+}
+
+size_t box_dist_scratch_bytes(const int nb[3]) {
+    return (size_t)(nb[0] + 1) * (nb[1] + 1) * (nb[2] + 1) * sizeof(int);
+}
+
+cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,
+                             cudaStream_t st) {
+    const int threads = 256;
+    auto grid_for = [&](long n) {
+        long b = (n + threads - 1) / threads;
+        return (unsigned)(b < 1 ? 1 : (b > 152L * 16 ? 152L * 16 : b));
+    };
+    svt_x_kernel<<<grid_for((long)(nb[1] + 1) * (nb[2] + 1)), threads, 0, st>>>(occ, nb[0], nb[1],
+                                                                                 nb[2], scratch);
+    svt_yz_kernel<<<grid_for((long)(nb[0] + 1) * (nb[2] + 1)), threads, 0, st>>>(nb[0], nb[1],
+                                                                                  nb[2], 1, scratch);
+    svt_yz_kernel<<<grid_for((long)(nb[0] + 1) * (nb[1] + 1)), threads, 0, st>>>(nb[0], nb[1],
+                                                                                  nb[2], 2, scratch);
+    box_dist_kernel<<<grid_for(8L * nb[0] * nb[1] * nb[2]), threads, 0, st>>>(
+        occ, scratch, nb[0], nb[1], nb[2], dist);
     return cudaGetLastError();
 }
 

@@ -1,40 +1,51 @@
 // Per-ray render kernel: one thread casts the ray of one pixel (paper, Sec. "Methodology":
 // every pixel is processed independently; the ray moves with a fixed step and accumulates
-// colour). Steps per sample: placement (double-float anchors), 64-tap uniform cubic B-spline
-// gathered through L1 from the padded volume, post-classification through the 256-entry
-// table in shared memory, opacity correction to the segment length, front-to-back
-// compositing, early ray termination. With a brick table the ray leaps over empty bricks
-// (Sec. "Analysis", Pros (b)): a sample is skipped only when the brick holding floor(p) is
-// empty, which makes its opacity exactly zero, so the image is the same bit for bit.
+// colour; the preference is cubic interpolation with post-classification).
+//
+// Per sample: exact placement from double-float anchors, the 64-tap uniform cubic B-spline
+// read as 16 aligned float4 rows of the x-replicated volume through L1, post-classification
+// through the 256-entry table in shared memory, opacity corrected to the segment length,
+// front-to-back compositing, early ray termination. With a brick table the ray leaps over
+// boxes of empty bricks ahead of it (Sec. "Analysis", Pros (b): auxiliary structures to skip
+// empty space), using the forward-box distance field of its direction octant. A sample is
+// skipped only when it lies, by a margin of MARGIN voxels beyond any rounding of its
+// position, inside an empty brick, where its opacity is exactly zero; the image is therefore
+// identical bit for bit with and without leaping.
+//
+// Scheduling: each warp renders an 8 x 4 pixel tile; CTAs are small (RAY_WARPS warps) so the
+// hardware block scheduler balances tiles of very different cost (rays through bone take
+// hundreds of samples, rays through air none).
 #include "vrc_internal.h"
 
 namespace vrc {
 
-template <typename T>
-__device__ __forceinline__ float ld_voxel(const T *p) { return (float)__ldg(p); }
+// Leaping decisions use float positions and exit distances whose combined error stays below
+// ~1.5e-3 voxel for coordinates up to 4096; a sample is leapt over only when it sits at least
+// MARGIN inside a box of empty bricks.
+constexpr float MARGIN = 4.0e-3f;
 
-// Cubic B-spline sample at integer base ip (taps ip-1 .. ip+2) with fractions f.
-template <typename T>
-__device__ __forceinline__ float tricubic(const T *__restrict__ vol, int pnx, int pslice,
-                                          const int ip[3], const float f[3]) {
+// Cubic B-spline sample at integer base ip (taps ip-1 .. ip+2) with fractions f, from the
+// x-replicated float4 volume: entry (ip0 + 1, ip1 + 1 + b, ip2 + 1 + c) holds tap row (b, c).
+__device__ __forceinline__ float tricubic_rep(const ReplView &rp, const int ip[3],
+                                              const float f[3]) {
     float wx[4], wy[4], wz[4];
     bspline_w(f[0], wx);
     bspline_w(f[1], wy);
     bspline_w(f[2], wz);
-    // element offset of tap (ip-1, ip-1, ip-1) in the padded layout
-    const int off = (ip[2] - 1 + PAD) * pslice + (ip[1] - 1 + PAD) * pnx + (ip[0] - 1 + PAD);
-    const T *p0 = vol + off;
+    const long rslice = (long)rp.rnx * rp.rny;
+    const float4 *p0 = rp.base + ((long)(ip[2] + 1) * rp.rny + (ip[1] + 1)) * rp.rnx + (ip[0] + 1);
     float s = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
+        const float4 *pc = p0 + c * rslice;
         float plane = 0.0f;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const T *row = p0 + c * pslice + b * pnx;
-            float r = wx[0] * ld_voxel(row);
-            r = fmaf(wx[1], ld_voxel(row + 1), r);
-            r = fmaf(wx[2], ld_voxel(row + 2), r);
-            r = fmaf(wx[3], ld_voxel(row + 3), r);
+            const float4 v = __ldg(pc + b * rp.rnx);
+            float r = wx[0] * v.x;
+            r = fmaf(wx[1], v.y, r);
+            r = fmaf(wx[2], v.z, r);
+            r = fmaf(wx[3], v.w, r);
             plane = fmaf(wy[b], r, plane);
         }
         s = fmaf(wz[c], plane, s);
@@ -42,123 +53,164 @@ __device__ __forceinline__ float tricubic(const T *__restrict__ vol, int pnx, in
     return s;
 }
 
-__device__ __forceinline__ int brick_index(const BrickView &bv, const int ip[3]) {
-    int bx = max(ip[0], 0) >> bv.shift;
-    int by = max(ip[1], 0) >> bv.shift;
-    int bz = max(ip[2], 0) >> bv.shift;
+__device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by, int bz) {
     return (bz * bv.nb[1] + by) * bv.nb[0] + bx;
 }
 
-// First sample index after the run of samples that lie in the empty brick holding sample j,
-// less one sample of margin; verified by placing the last skipped sample again.
-__device__ __forceinline__ int skip_empty_brick(const RaySetup &ray, const RayGrid &g,
-                                                const BrickView &bv, const Anchor &an, int j,
-                                                const int ip[3]) {
-    const int B = bv.B;
-    float texit = INFINITY;  // relative to the start of the anchor block
+// Leap mode for sample j. Returns the next sample index to look at: > j when sample j (and
+// every sample before the returned index) lies MARGIN inside a forward box of empty bricks,
+// or j itself when sample j needs its exact position. `dist` is the field of the ray's octant.
+__device__ __forceinline__ int leap(const BrickView &bv, const uint8_t *__restrict__ dist,
+                                    const float Pf[3], const float df[3], const float inv_df[3],
+                                    float step, float inv_step, int nseg, int j, int &cache_lin,
+                                    int &cache_r) {
+    if (j == nseg - 1) return j;  // the last segment's midpoint is not (j + 1/2) ds
+    const float m = ((float)j + 0.5f) * step;
+    float pa[3];
+    int b[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float dk = ray.d[k].hi;
-        const int bk = max(ip[k], 0) >> bv.shift;
-        float plane;
-        if (dk > 0.0f) {
-            if (bk == bv.nb[k] - 1) continue;
-            plane = (float)((bk + 1) * B - an.I[k]);
-        } else if (dk < 0.0f) {
-            if (bk == 0) continue;
-            plane = (float)(bk * B - an.I[k]);
+        pa[k] = fmaf(m, df[k], Pf[k]);
+        const int fl = (int)floorf(pa[k]);
+        b[k] = min(max(fl, 0) >> bv.shift, bv.nb[k] - 1);
+    }
+    const int lin = brick_linear(bv, b[0], b[1], b[2]);
+    if (lin != cache_lin) {
+        cache_lin = lin;
+        cache_r = dist[lin];
+    }
+    const int r = cache_r;
+    if (r == 0) return j;
+    const float B = (float)bv.B;
+    float texit = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        // sample j must sit MARGIN inside its own brick (interior faces only)
+        const float lo = (float)(b[k] * bv.B), hi = lo + B;
+        if ((b[k] > 0 && pa[k] < lo + MARGIN) || (b[k] < bv.nb[k] - 1 && pa[k] > hi - MARGIN))
+            return j;
+        // exit of the empty forward box of extent r - 1 bricks, face moved inward by MARGIN
+        float face;
+        if (df[k] > 0.0f) {
+            if (b[k] + r >= bv.nb[k]) continue;
+            face = (float)((b[k] + r) * bv.B) - MARGIN;
+        } else if (df[k] < 0.0f) {
+            if (b[k] - r + 1 <= 0) continue;
+            face = (float)((b[k] - r + 1) * bv.B) + MARGIN;
         } else {
             continue;
         }
-        texit = fminf(texit, (plane - an.r[k]) / dk);
+        texit = fminf(texit, (face - Pf[k]) * inv_df[k]);
     }
-    if (!(texit < INFINITY)) return ray.nseg;
-    float jf = ceilf(texit / g.step - 0.5f) - 1.0f + (float)(an.blk << ANCHOR_SHIFT);
-    int jn = jf >= (float)ray.nseg ? ray.nseg : (int)jf;
-    if (jn <= j + 1) return j + 1;
-    // verify the last skipped sample lies in the same brick
-    const int jl = jn - 1;
-    Anchor a2;
-    make_anchor(ray, g.step, jl >> ANCHOR_SHIFT, a2);
-    float delta, mrel;
-    segment_rel(ray, g.step, jl, a2.blk, delta, mrel);
-    int ip2[3];
-    float f2[3];
-    sample_pos(a2, ray, mrel, g.n, ip2, f2);
-    if (brick_index(bv, ip2) != brick_index(bv, ip)) return j + 1;
-    return jn;
+    if (!(texit < INFINITY)) return nseg;
+    // first sample whose midpoint may reach the moved face
+    const float jf = ceilf(fmaf(texit, inv_step, -0.5f));
+    const int jn = jf >= (float)nseg ? nseg : (int)jf;
+    return max(jn, j + 1);
 }
 
-template <typename T, bool ESL>
-__global__ void __launch_bounds__(256) render_ray_kernel(RenderLaunch L) {
-    __shared__ float4 s_rgba[256];
-    __shared__ float4 s_drgba[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-        s_rgba[i] = L.tf.rgba[i];
-        s_drgba[i] = L.tf.drgba[i];
-    }
-    __syncthreads();
+constexpr int RAY_WARPS = 2;  // warps per CTA
 
-    // 16 x 16 pixel tile per CTA; each warp covers 8 x 4 pixels
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * 16 + (warp >> 1) * 4 + (lane >> 3);
+template <bool ESL>
+__global__ void __launch_bounds__(32 * RAY_WARPS, 16 / RAY_WARPS) render_ray_kernel(RenderLaunch L) {
+    // one 8 x 4 pixel tile per warp, tiles in raster order
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * RAY_WARPS + (threadIdx.x >> 5);
+    const int tiles_x = (L.cam.width + 7) >> 3;
+    const int px = (tile % tiles_x) * 8 + (lane & 7);
+    const int py = (tile / tiles_x) * 4 + (lane >> 3);
     const bool valid = px < L.cam.width && py < L.cam.height;
+    const float4 *__restrict__ tf_rgba = L.tf.rgba;
+    const float4 *__restrict__ tf_drgba = L.tf.drgba;
 
     RaySetup ray;
     ray.nseg = 0;
     if (valid) ray_setup(L.cam, L.grid, px, py, ray);
 
-    const T *vol = (const T *)L.vol.base;
-    const int pnx = L.vol.pnx, pslice = L.vol.pnx * L.vol.pny;
     const float step = L.grid.step, thr = L.grid.ert;
+    const float inv_step = 1.0f / step;
+    float Pf[3], df[3], inv_df[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Pf[k] = ray.pin[k].hi + ray.pin[k].lo;
+        df[k] = ray.d[k].hi;
+        inv_df[k] = 1.0f / df[k];
+    }
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Tr = 1.0f;
     int executed = 0;
+    const uint8_t *dist = nullptr;
+    if (ESL) {
+        const int oct = (df[0] < 0.0f) | ((df[1] < 0.0f) << 1) | ((df[2] < 0.0f) << 2);
+        dist = L.dist + (long)oct * L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
+    }
 
     Anchor an;
     an.blk = -1;
-    int cur_brick = -1;
-    bool cur_empty = false;
+    int leap_lin = -1, leap_r = 0;      // dist cache of the leap path
+    int run_lin = -1, run_empty = 0;    // dist cache of the exact path
+    bool in_run = !ESL;                 // exact placement mode (vs leap mode)
+    bool done = ray.nseg == 0;
     int j = 0;
-    while (j < ray.nseg) {
-        const int blk = j >> ANCHOR_SHIFT;
-        if (blk != an.blk) make_anchor(ray, step, blk, an);
-        float delta, mrel;
-        segment_rel(ray, step, j, blk, delta, mrel);
+    while (true) {
+        // advance this lane to its next sample to composite
         int ip[3];
-        float f[3];
-        sample_pos(an, ray, mrel, L.grid.n, ip, f);
-        if (ESL) {
-            const int b = brick_index(L.bricks, ip);
-            if (b != cur_brick) {
-                cur_brick = b;
-                cur_empty = L.occ[b] == 0;
+        float f[3], delta = 0.0f;
+        while (!done) {
+            if (j >= ray.nseg) {
+                done = true;
+                break;
             }
-            if (cur_empty) {
-                j = skip_empty_brick(ray, L.grid, L.bricks, an, j, ip);
-                continue;
+            if (ESL && !in_run) {
+                const int jn = leap(L.bricks, dist, Pf, df, inv_df, step, inv_step, ray.nseg, j,
+                                    leap_lin, leap_r);
+                if (jn != j) {
+                    j = jn;
+                    continue;
+                }
+                in_run = true;
             }
+            const int blk = j >> ANCHOR_SHIFT;
+            if (blk != an.blk) make_anchor(ray, step, blk, an);
+            float mrel;
+            segment_rel(ray, step, j, blk, delta, mrel);
+            sample_pos(an, ray, mrel, L.grid.n, ip, f);
+            if (ESL) {
+                const int lin = brick_linear(L.bricks, max(ip[0], 0) >> L.bricks.shift,
+                                             max(ip[1], 0) >> L.bricks.shift,
+                                             max(ip[2], 0) >> L.bricks.shift);
+                if (lin != run_lin) {
+                    run_lin = lin;
+                    run_empty = dist[lin] != 0;
+                }
+                if (run_empty) {  // in an empty brick: opacity zero, back to leaping
+                    ++j;
+                    in_run = false;
+                    continue;
+                }
+            }
+            break;
         }
-        const float s = tricubic<T>(vol, pnx, pslice, ip, f);
-        // post-classification: u = (s - lo) * du on [0, 255], linear between entries
-        float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
-        int i0;
-        const float fl = floor_small(u, i0);
-        i0 = min(i0, 254);
-        const float fu = u - (float)i0;
-        (void)fl;
-        const float4 c0 = s_rgba[i0], dc = s_drgba[i0];
-        const float r = fmaf(fu, dc.x, c0.x), gcol = fmaf(fu, dc.y, c0.y);
-        const float bcol = fmaf(fu, dc.z, c0.z), a = fmaf(fu, dc.w, c0.w);
-        const float alpha = segment_alpha(a, delta);
-        const float w = Tr * alpha;
-        C0 = fmaf(w, r, C0);
-        C1 = fmaf(w, gcol, C1);
-        C2 = fmaf(w, bcol, C2);
-        Tr = Tr - w;
-        ++executed;
-        if (1.0f - Tr > thr) break;
-        ++j;
+        if (__all_sync(0xffffffffu, done)) break;
+        if (!done) {
+            const float s = tricubic_rep(L.rep, ip, f);
+            // post-classification: u = (s - lo) * du on [0, 255], linear between entries
+            const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
+            int i0;
+            floor_small(u, i0);
+            i0 = min(i0, 254);
+            const float fu = u - (float)i0;
+            const float4 c0 = __ldg(tf_rgba + i0), dc = __ldg(tf_drgba + i0);
+            const float a = fmaf(fu, dc.w, c0.w);
+            const float alpha = segment_alpha(a, delta);
+            const float w = Tr * alpha;
+            C0 = fmaf(w, fmaf(fu, dc.x, c0.x), C0);
+            C1 = fmaf(w, fmaf(fu, dc.y, c0.y), C1);
+            C2 = fmaf(w, fmaf(fu, dc.z, c0.z), C2);
+            Tr = Tr - w;
+            ++executed;
+            if (1.0f - Tr > thr) done = true;
+            ++j;
+        }
     }
     if (valid) L.out[(long)py * L.cam.width + px] = make_float4(C0, C1, C2, 1.0f - Tr);
 
@@ -174,21 +226,10 @@ __global__ void __launch_bounds__(256) render_ray_kernel(RenderLaunch L) {
 }
 
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st) {
-    dim3 grid((L.cam.width + 15) / 16, (L.cam.height + 15) / 16);
-    const bool esl = L.occ != nullptr;
-    switch (L.vol.dtype) {
-    case DT_U16:
-        if (esl) render_ray_kernel<uint16_t, true><<<grid, 256, 0, st>>>(L);
-        else render_ray_kernel<uint16_t, false><<<grid, 256, 0, st>>>(L);
-        break;
-    case DT_I16:
-        if (esl) render_ray_kernel<int16_t, true><<<grid, 256, 0, st>>>(L);
-        else render_ray_kernel<int16_t, false><<<grid, 256, 0, st>>>(L);
-        break;
-    default:
-        if (esl) render_ray_kernel<float, true><<<grid, 256, 0, st>>>(L);
-        else render_ray_kernel<float, false><<<grid, 256, 0, st>>>(L);
-    }
+    const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
+    const unsigned grid = (unsigned)((tiles + RAY_WARPS - 1) / RAY_WARPS);
+    if (L.dist) render_ray_kernel<true><<<grid, 32 * RAY_WARPS, 0, st>>>(L);
+    else render_ray_kernel<false><<<grid, 32 * RAY_WARPS, 0, st>>>(L);
     return cudaGetLastError();
 }
 

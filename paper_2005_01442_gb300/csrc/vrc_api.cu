@@ -28,7 +28,9 @@ struct Bricks {
 };
 
 struct Occ {
-    uint8_t *dev = nullptr;
+    uint8_t *dev = nullptr;   // occupancy bytes
+    uint8_t *dist = nullptr;  // 8 forward-box distance fields (0 = occupied)
+    int *scratch = nullptr;   // summed-volume table used while building dist
     long n = 0;
     unsigned brick_version = 0, tf_version = 0;
 };
@@ -37,7 +39,8 @@ struct Volume {
     int dtype = 0;
     int n[3] = {0, 0, 0};
     int pnx = 0, pny = 0, pnz = 0;
-    void *dpad = nullptr;
+    void *dpad = nullptr;          // compact padded copy (brick tables)
+    float4 *drep = nullptr;        // x-replicated float4 copy (rendering)
     Bricks bricks[2];               // B = 8, B = 16
     std::map<long, Occ> occ;        // key: tf_id * 2 + (B == 16)
 };
@@ -105,11 +108,16 @@ struct DeviceGuard {
 
 void free_volume(Volume &v) {
     cudaFree(v.dpad);
+    cudaFree(v.drep);
     for (auto &b : v.bricks) {
         cudaFree(b.mn);
         cudaFree(b.mx);
     }
-    for (auto &kv : v.occ) cudaFree(kv.second.dev);
+    for (auto &kv : v.occ) {
+        cudaFree(kv.second.dev);
+        cudaFree(kv.second.dist);
+        cudaFree(kv.second.scratch);
+    }
     v.occ.clear();
 }
 
@@ -244,25 +252,33 @@ vrc_status upload_tf(vrc_ctx *ctx, Tf &t, const float *rgba, float lo, float hi)
 
 // Occupancy of (volume, B, tf), rebuilt when the bricks or the table changed.
 vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStream_t st,
-                      const uint8_t **out) {
+                      const uint8_t **out, const uint8_t **dist_out = nullptr) {
     Bricks &b = v.bricks[slot_of(B)];
     if (!b.mn || b.B != B) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
     long key = (long)tf_id * 2 + slot_of(B);
     Occ &o = v.occ[key];
     if (!o.dev || o.n != b.count()) {
         cudaFree(o.dev);
-        o.dev = nullptr;
+        cudaFree(o.dist);
+        cudaFree(o.scratch);
+        o.dev = o.dist = nullptr;
+        o.scratch = nullptr;
+        o.n = 0;
         CK(cudaMalloc(&o.dev, (size_t)b.count()), "cudaMalloc(occupancy)");
+        CK(cudaMalloc(&o.dist, 8 * (size_t)b.count()), "cudaMalloc(occupancy)");
+        CK(cudaMalloc(&o.scratch, box_dist_scratch_bytes(b.nb)), "cudaMalloc(occupancy)");
         o.n = b.count();
         o.brick_version = o.tf_version = 0;
     }
     if (o.brick_version != b.version || o.tf_version != t.version) {
         CK(launch_occupancy(b.mn, b.mx, v.dtype, b.count(), t.prefix, t.lo, t.du, o.dev, st),
            "occupancy launch");
+        CK(launch_box_dist(o.dev, b.nb, o.scratch, o.dist, st), "distance launch");
         o.brick_version = b.version;
         o.tf_version = t.version;
     }
     *out = o.dev;
+    if (dist_out) *dist_out = o.dist;
     return VRC_OK;
 }
 
@@ -293,17 +309,21 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     vrc_status s = build_camera(ctx, cam, L.cam);
     if (s != VRC_OK) return s;
     L.vol = view_of(*v);
+    L.rep.base = v->drep;
+    L.rep.rnx = v->n[0] + 1;
+    L.rep.rny = v->n[1] + 4;
+    L.rep.rnz = v->n[2] + 4;
     L.tf = tf_view(*t);
     for (int k = 0; k < 3; ++k) L.grid.n[k] = v->n[k];
     L.grid.step = p->step;
     L.grid.ert = p->ert_threshold;
     L.err = ctx->err_word;
     if (p->brick) {
-        const uint8_t *occ = nullptr;
-        s = ensure_occ(ctx, *v, tf_id, *t, p->brick, st, &occ);
+        const uint8_t *occ = nullptr, *dist = nullptr;
+        s = ensure_occ(ctx, *v, tf_id, *t, p->brick, st, &occ, &dist);
         if (s != VRC_OK) return s;
         Bricks &b = v->bricks[slot_of(p->brick)];
-        L.occ = occ;
+        L.dist = dist;
         L.bricks.B = b.B;
         L.bricks.shift = b.B == 16 ? 4 : 3;
         for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b.nb[k];
@@ -387,7 +407,8 @@ vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_
     const size_t es = dtype_size(dtype);
     const size_t padded = (size_t)v.pnx * v.pny * v.pnz * es;
     const size_t raw = (size_t)nx * ny * nz * es;
-    if ((size_t)v.pnx * v.pny * v.pnz >= (size_t)1 << 31)
+    if ((size_t)v.pnx * v.pny * v.pnz >= (size_t)1 << 31 ||
+        (size_t)(nx + 1) * (ny + 4) * (nz + 4) >= (size_t)1 << 31)
         return fail(ctx, VRC_ERR_ARG, "volume too large (padded elements must stay below 2^31)");
     cudaError_t e = cudaMalloc(&v.dpad, padded);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(volume)");
@@ -398,7 +419,10 @@ vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_
         if (e == cudaSuccess) e = cudaMemcpyAsync(staging, data, raw, cudaMemcpyHostToDevice, st);
         src = staging;
     }
+    const size_t rep = (size_t)(nx + 1) * (ny + 4) * (nz + 4) * sizeof(float4);
+    if (e == cudaSuccess) e = cudaMalloc(&v.drep, rep);
     if (e == cudaSuccess) e = launch_pad_volume(src, dtype, v.n, v.dpad, v.pnx, v.pny, v.pnz, st);
+    if (e == cudaSuccess) e = launch_replicate_x4(src, dtype, v.n, v.drep, st);
     if (staging) {
         cudaError_t e2 = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = e2;
@@ -406,6 +430,7 @@ vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_
     }
     if (e != cudaSuccess) {
         cudaFree(v.dpad);
+        cudaFree(v.drep);
         return cuda_fail(ctx, e, "volume upload");
     }
     int id = ctx->next_id++;
@@ -516,6 +541,8 @@ vrc_status vrc_tf_free(vrc_ctx *ctx, int tf_id) {
             auto it = kv.second.occ.find((long)tf_id * 2 + s);
             if (it != kv.second.occ.end()) {
                 cudaFree(it->second.dev);
+                cudaFree(it->second.dist);
+                cudaFree(it->second.scratch);
                 kv.second.occ.erase(it);
             }
         }

@@ -67,15 +67,13 @@ VRC_HD ff ff_mul_f(ff a, float b) {
     return quick_two_sum(p.hi, p.lo);
 }
 
-// a / b: one float quotient, then a correction from the exact remainder (long division).
-VRC_HD ff ff_div(ff a, ff b) {
-    float q1 = a.hi / b.hi;
+// a / b given rb = 1/b.hi in float: quotient estimate, then one correction from the exact
+// remainder; about 2^-44 relative error, enough for ray parameters.
+VRC_HD ff ff_div_rcp(ff a, ff b, float rb) {
+    float q1 = a.hi * rb;
     ff r = ff_sub(a, ff_mul_f(b, q1));
-    float q2 = r.hi / b.hi;
-    ff q = quick_two_sum(q1, q2);
-    r = ff_sub(a, ff_mul(b, q));
-    float q3 = r.hi / b.hi;
-    return ff_add(q, ff_make(q3));
+    float q2 = r.hi * rb;
+    return quick_two_sum(q1, q2);
 }
 
 // 1/sqrt(a) for a > 0: float estimate refined by Newton's iteration y += y (1 - a y^2) / 2
@@ -149,8 +147,9 @@ __device__ __forceinline__ void ray_setup(const CamDev &cam, const RayGrid &g, i
     for (int k = 0; k < 3; ++k) {
         const float lo = -0.5f, hi = (float)g.n[k] - 0.5f;
         if (d[k].hi != 0.0f) {
-            ff ta = ff_div(ff_sub(ff_make(lo), o[k]), d[k]);
-            ff tb = ff_div(ff_sub(ff_make(hi), o[k]), d[k]);
+            const float rb = 1.0f / d[k].hi;
+            ff ta = ff_div_rcp(ff_sub(ff_make(lo), o[k]), d[k], rb);
+            ff tb = ff_div_rcp(ff_sub(ff_make(hi), o[k]), d[k], rb);
             if (ff_lt(tb, ta)) {
                 ff tmp = ta;
                 ta = tb;

@@ -27,6 +27,13 @@ struct VolView {
     int pnx, pny, pnz;
 };
 
+// The render layout of a resident volume (float4 entries replicated along x, see
+// replicate_x4_kernel): rnx = nx + 1, rny = ny + 4, rnz = nz + 4.
+struct ReplView {
+    const float4 *base;
+    int rnx, rny, rnz;
+};
+
 // Brick table of size B (min/max arrays of the voxel dtype, ceil(n/B) per axis).
 struct BrickView {
     int B, shift;
@@ -43,10 +50,11 @@ struct TfView {
 
 struct RenderLaunch {
     VolView vol;
+    ReplView rep;
     TfView tf;
     CamDev cam;
     RayGrid grid;
-    const uint8_t *occ;  // NULL: no empty-space leaping
+    const uint8_t *dist;  // NULL: no leaping; else 8 x nbricks forward-box distances
     BrickView bricks;
     float4 *out;
     unsigned long long *counters;  // NULL or [nominal, executed]
@@ -56,9 +64,15 @@ struct RenderLaunch {
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_pad_volume(const void *src, int dtype, const int n[3], void *dst, int pnx,
                               int pny, int pnz, cudaStream_t st);
+cudaError_t launch_replicate_x4(const void *src, int dtype, const int n[3], float4 *dst,
+                                cudaStream_t st);
 cudaError_t launch_brick_minmax(const VolView &v, int B, void *mn, void *mx, cudaStream_t st);
 cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbricks,
                              const int *prefix_dev, float lo, float du, uint8_t *occ,
+                             cudaStream_t st);
+size_t box_dist_scratch_bytes(const int nb[3]);
+// dist: 8 x nbricks bytes (one forward-box distance field per direction octant)
+cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,
                              cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
 
