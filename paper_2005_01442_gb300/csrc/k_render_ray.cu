@@ -2,7 +2,7 @@
 // every pixel is processed independently; the ray moves with a fixed step and accumulates
 // colour; the preference is cubic interpolation with post-classification).
 //
-// Per sample: exact placement from double-float anchors, the 64-tap uniform cubic B-spline
+// Per sample: exact placement from the double-float ray record, the 64-tap uniform cubic B-spline
 // read as 16 aligned float4 rows of the x-replicated volume through L1, post-classification
 // through the 256-entry table in shared memory, opacity corrected to the segment length,
 // front-to-back compositing, early ray termination. With a brick table the ray leaps over
@@ -129,13 +129,10 @@ __global__ void __launch_bounds__(32 * RAY_WARPS, 16 / RAY_WARPS) render_ray_ker
 
     const float step = L.grid.step, thr = L.grid.ert;
     const float inv_step = 1.0f / step;
+    RayPos rp;
+    ray_pos_init(ray, step, rp);
     float Pf[3], df[3], inv_df[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        Pf[k] = ray.pin[k].hi + ray.pin[k].lo;
-        df[k] = ray.d[k].hi;
-        inv_df[k] = 1.0f / df[k];
-    }
+    ray_float(rp, Pf, df, inv_df);
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Tr = 1.0f;
     int executed = 0;
     const uint8_t *dist = nullptr;
@@ -144,8 +141,6 @@ __global__ void __launch_bounds__(32 * RAY_WARPS, 16 / RAY_WARPS) render_ray_ker
         dist = L.dist + (long)oct * L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
     }
 
-    Anchor an;
-    an.blk = -1;
     int leap_lin = -1, leap_r = 0;      // dist cache of the leap path
     int run_lin = -1, run_empty = 0;    // dist cache of the exact path
     bool in_run = !ESL;                 // exact placement mode (vs leap mode)
@@ -169,11 +164,7 @@ __global__ void __launch_bounds__(32 * RAY_WARPS, 16 / RAY_WARPS) render_ray_ker
                 }
                 in_run = true;
             }
-            const int blk = j >> ANCHOR_SHIFT;
-            if (blk != an.blk) make_anchor(ray, step, blk, an);
-            float mrel;
-            segment_rel(ray, step, j, blk, delta, mrel);
-            sample_pos(an, ray, mrel, L.grid.n, ip, f);
+            place(rp, step, L.grid.n, j, ip, f, delta);
             if (ESL) {
                 const int lin = brick_linear(L.bricks, max(ip[0], 0) >> L.bricks.shift,
                                              max(ip[1], 0) >> L.bricks.shift,

@@ -37,7 +37,11 @@ VRC_HD ff quick_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
 }
 
 VRC_HD ff two_prod(float a, float b) {
+#ifdef __CUDA_ARCH__
+    float p = __fmul_rn(a, b);  // never fused with a later add: p must be the rounded product
+#else
     float p = a * b;
+#endif
     float e = fmaf(a, b, -p);
     return {p, e};
 }
@@ -178,55 +182,43 @@ __device__ __forceinline__ void ray_setup(const CamDev &cam, const RayGrid &g, i
 }
 
 // ----------------------------------------------------------------------------------------
-// Sample placement. Samples are grouped in blocks of ANCHOR_K; each block has an anchor
-// point P_a = pin + (a * K * ds) d evaluated in double-float and split into an integer part
-// I (per axis) and a float remainder r in [0, 1). A sample j of block a then sits at
-// I + r + m_rel d, m_rel = (midpoint of j) - a K ds, a float of magnitude <= K ds, so its
-// fractional coordinate carries ~1e-6 voxel error at any volume size. Positions depend on
-// j only (never accumulated), identically with or without empty-space leaping.
-constexpr int ANCHOR_SHIFT = 5;
-constexpr int ANCHOR_K = 1 << ANCHOR_SHIFT;
-
-struct Anchor {
-    int blk;       // anchor block index
-    int I[3];      // integer part
-    float r[3];    // remainder in [0, 1)
+// Sample placement. Sample j of a ray sits at p_j = p_in + m_j d, with m_j = (j + 1/2) ds for
+// every segment but the last, whose midpoint and length come from L = t_out - t_in. The entry
+// point is split once per ray into an integer part I0 and a double-float remainder r0; then
+// per axis p_j - I0 = r0 + m_j d is formed with an error-free product (m_j d_hi exactly as
+// hi + lo) whose large part hi is split into its integer and fractional parts exactly, so the
+// fractional coordinate of every sample carries ~3e-7 voxel error at any volume size.
+// Positions are a function of j alone (never accumulated), identical with or without
+// empty-space leaping.
+struct RayPos {
+    int I0[3];    // integer part of the entry point
+    ff r0[3];     // entry point minus I0
+    ff d[3];      // unit direction
+    ff mlast;     // midpoint of the last segment, measured from the entry point
+    float dlast;  // length of the last segment
+    int nseg;
 };
 
-__device__ __forceinline__ void make_anchor(const RaySetup &ray, float step, int blk, Anchor &an) {
-    ff m = two_prod((float)(blk << ANCHOR_SHIFT), step);
-    an.blk = blk;
+__device__ __forceinline__ void ray_pos_init(const RaySetup &ray, float step, RayPos &rp) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        ff P = ff_add(ray.pin[k], ff_mul(m, ray.d[k]));
-        float I = floorf(P.hi);
-        float r = (P.hi - I) + P.lo;
-        if (r < 0.0f) {
-            r += 1.0f;
+        float I = floorf(ray.pin[k].hi);
+        ff r = ff_sub(ray.pin[k], ff_make(I));
+        if (r.hi < 0.0f) {  // hi was an integer and lo < 0
             I -= 1.0f;
-        } else if (r >= 1.0f) {
-            r -= 1.0f;
-            I += 1.0f;
+            r = ff_add(r, ff_make(1.0f));
         }
-        an.I[k] = (int)I;
-        an.r[k] = r;
+        rp.I0[k] = (int)I;
+        rp.r0[k] = r;
+        rp.d[k] = ray.d[k];
     }
-}
-
-// Segment j: length delta and midpoint relative to the start of its anchor block.
-__device__ __forceinline__ void segment_rel(const RaySetup &ray, float step, int j, int blk,
-                                            float &delta, float &mrel) {
-    if (j < ray.nseg - 1) {
-        delta = step;
-        mrel = ((float)(j - (blk << ANCHOR_SHIFT)) + 0.5f) * step;
-    } else {
-        // last (possibly short) segment: delta = L - j ds in double-float
-        ff a = two_prod((float)j, step);
-        ff dl = ff_sub(ray.L, a);
-        delta = dl.hi + dl.lo;
-        if (delta > step) delta = step;
-        mrel = (float)(j - (blk << ANCHOR_SHIFT)) * step + 0.5f * delta;
-    }
+    rp.nseg = ray.nseg;
+    const ff a = two_prod((float)(ray.nseg > 0 ? ray.nseg - 1 : 0), step);
+    const ff dl = ff_sub(ray.L, a);
+    float delta = dl.hi + dl.lo;
+    if (delta > step) delta = step;
+    rp.dlast = delta;
+    rp.mlast = ff_add(a, ff_make(0.5f * delta));
 }
 
 // floor() of a float of magnitude < 2^22 and its integer, via rounding toward -inf onto
@@ -238,19 +230,43 @@ __device__ __forceinline__ float floor_small(float q, int &iq) {
     return y - M;
 }
 
-// Integer voxel coordinate (clamped to [-1, n-1]) and fraction of sample at m_rel.
-__device__ __forceinline__ void sample_pos(const Anchor &an, const RaySetup &ray, float mrel,
-                                           const int n[3], int ip[3], float f[3]) {
+// Sample j: integer voxel coordinate (clamped to [-1, n-1]), fraction and segment length.
+__device__ __forceinline__ void place(const RayPos &rp, float step, const int n[3], int j,
+                                      int ip[3], float f[3], float &delta) {
+    ff m;
+    if (j < rp.nseg - 1) {
+        m = two_prod((float)j + 0.5f, step);
+        delta = step;
+    } else {
+        m = rp.mlast;
+        delta = rp.dlast;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float q = fmaf(mrel, ray.d[k].hi, an.r[k]);
-        int iq;
-        float fq = floor_small(q, iq);
-        f[k] = q - fq;
-        int v = an.I[k] + iq;
+        const float hi = __fmul_rn(m.hi, rp.d[k].hi);
+        const float lo = fmaf(m.hi, rp.d[k].hi, -hi);
+        const float small = fmaf(m.hi, rp.d[k].lo, fmaf(m.lo, rp.d[k].hi, lo)) + rp.r0[k].lo;
+        int ih;
+        const float fh = floor_small(hi, ih);
+        const float t = ((hi - fh) + rp.r0[k].hi) + small;
+        int it;
+        const float ft = floor_small(t, it);
+        f[k] = t - ft;
+        int v = rp.I0[k] + ih + it;
         v = max(v, -1);
         v = min(v, n[k] - 1);
         ip[k] = v;
+    }
+}
+
+// Float entry point and direction for leaping decisions.
+__device__ __forceinline__ void ray_float(const RayPos &rp, float Pf[3], float df[3],
+                                          float inv_df[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Pf[k] = (float)rp.I0[k] + rp.r0[k].hi;
+        df[k] = rp.d[k].hi;
+        inv_df[k] = 1.0f / df[k];
     }
 }
 

@@ -75,5 +75,6 @@ size_t box_dist_scratch_bytes(const int nb[3]);
 cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,
                              cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
+cudaError_t launch_render_warp(const RenderLaunch &L, cudaStream_t st);
 
 }  // namespace vrc
