@@ -156,6 +156,29 @@ vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam
 vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                            const vrc_params *params, float *out_rgba_host, void *stream);
 
+/* Size of the device array that vrc_render_noalloc works in (8 MiB). */
+#define VRC_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* vrc_render for callers that must not allocate device memory while rendering: a render loop
+ * under a fixed, pre-reserved GPU memory budget, or one that cannot take the device-wide
+ * synchronisation cudaMalloc/cudaFree imply while other streams run. vrc_render caches the
+ * occupancy and leaping fields of each (volume, transfer function, brick size) in memory the
+ * context allocates on first use; this call instead rebuilds them on every call inside one
+ * fixed device array of VRC_NOALLOC_SCRATCH_BYTES, a file-scope static of the library that
+ * every GPU loading the library holds until the process exits. It calls no cudaMalloc or
+ * cudaFree; the volume, its brick table for params->brick (vrc_bricks_build) and the
+ * transfer function must already exist. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Arguments, outputs and the image are those of vrc_render (same pixels, bit for bit).
+ * Returns VRC_ERR_ARG, with a message naming the sizes, when the brick grid needs more than
+ * the array holds (about 9 bytes per brick plus a 4-byte summed-volume table entry per
+ * brick). All calls share the one array: calls that can overlap on the GPU (other streams,
+ * other contexts of the process) race and must be serialised by the caller.
+ * The paper has no counterpart to this call. */
+vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                              const vrc_params *params, float *out_rgba_dev,
+                              unsigned long long *counters_dev, void *stream);
+
 /* Reads and clears the device error word shared by the context's kernels: 0 when no kernel
  * check has fired, else a VRC_ERR_* code. Synchronises `stream`. */
 vrc_status vrc_last_device_error(vrc_ctx *ctx, int *code, void *stream);

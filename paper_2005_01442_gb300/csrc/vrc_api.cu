@@ -648,3 +648,103 @@ vrc_status vrc_last_device_error(vrc_ctx *ctx, int *code, void *stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free rendering. vrc_render builds and caches the occupancy and leaping fields of
+// a (volume, transfer function, brick size) in memory the context allocates on first use.
+// Callers that must not allocate device memory while rendering -- a render loop running under
+// a fixed, pre-reserved GPU memory budget, or one that cannot afford the implicit device-wide
+// synchronisation of cudaMalloc/cudaFree while other streams are busy -- use
+// vrc_render_noalloc instead: it rebuilds those fields on every call inside one file-scope
+// device array that exists from library load until process exit, then renders.
+namespace {
+
+__device__ __align__(256) static unsigned char g_noalloc_scratch[VRC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of the scratch array on the current device (looked up once per device).
+vrc_status noalloc_scratch(vrc_ctx *ctx, unsigned char **out) {
+    if (ctx->device < 0 || ctx->device >= kMaxDevices)
+        return fail(ctx, VRC_ERR_ARG, "device index %d beyond %d", ctx->device, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[ctx->device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[ctx->device] = (unsigned char *)ptr;
+    }
+    *out = g_noalloc_ptr[ctx->device];
+    return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
+                                         const vrc_camera *cam, const vrc_params *params,
+                                         float *out_rgba_dev, unsigned long long *counters_dev,
+                                         void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!params) return fail(ctx, VRC_ERR_ARG, "params is NULL");
+    if (!out_rgba_dev) return fail(ctx, VRC_ERR_ARG, "out_rgba_dev is NULL");
+    if (((uintptr_t)out_rgba_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be 16-byte aligned");
+    if (counters_dev && ((uintptr_t)counters_dev & 7) != 0)
+        return fail(ctx, VRC_ERR_ARG, "counters_dev must be 8-byte aligned");
+    const int B = params->brick;
+    if (B != 0 && B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick must be 0, 8 or 16");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    Bricks *b = nullptr;
+    size_t occ_off = 0, dist_off = 0, svt_off = 0;
+    if (B) {
+        b = &v->bricks[slot_of(B)];
+        if (!b->mn || b->B != B) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
+        const size_t n = (size_t)b->count();
+        occ_off = 0;
+        dist_off = align256(n);
+        svt_off = dist_off + align256(8 * n);
+        const size_t need = svt_off + align256(box_dist_scratch_bytes(b->nb));
+        if (need > (size_t)VRC_NOALLOC_SCRATCH_BYTES)
+            return fail(ctx, VRC_ERR_ARG,
+                        "vrc_render_noalloc: %ld bricks of size %d need %zu scratch bytes, above "
+                        "the fixed maximum of %zu (use a larger brick size or vrc_render)",
+                        b->count(), B, need, (size_t)VRC_NOALLOC_SCRATCH_BYTES);
+    }
+    // validation and camera set-up without the context's occupancy cache
+    vrc_params p0 = *params;
+    p0.brick = 0;
+    RenderLaunch L;
+    vrc_status s = prepare_render(ctx, vol_id, tf_id, cam, &p0, st, L);
+    if (s != VRC_OK) return s;
+    if (B) {
+        unsigned char *scratch = nullptr;
+        s = noalloc_scratch(ctx, &scratch);
+        if (s != VRC_OK) return s;
+        uint8_t *occ = scratch + occ_off;
+        uint8_t *dist = scratch + dist_off;
+        int *svt = (int *)(scratch + svt_off);
+        // every byte these kernels read is written first by this call: nothing to clear
+        CK(launch_occupancy(b->mn, b->mx, v->dtype, b->count(), t->prefix, t->lo, t->du, occ, st),
+           "occupancy launch");
+        CK(launch_box_dist(occ, b->nb, svt, dist, st), "distance launch");
+        L.dist = dist;
+        L.bricks.B = b->B;
+        L.bricks.shift = b->B == 16 ? 4 : 3;
+        for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b->nb[k];
+        L.bricks.mn = b->mn;
+        L.bricks.mx = b->mx;
+    }
+    L.out = (float4 *)out_rgba_dev;
+    L.counters = counters_dev;
+    CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
+    return VRC_OK;
+}

@@ -22,7 +22,8 @@ STATUS = {0: "VRC_OK", -1: "VRC_ERR_ARG", -2: "VRC_ERR_OOM", -3: "VRC_ERR_CUDA",
 EXPORTS = [
     "vrc_create", "vrc_destroy", "vrc_volume_upload", "vrc_volume_free", "vrc_volume_info",
     "vrc_bricks_build", "vrc_bricks_get", "vrc_tf_set", "vrc_tf_update", "vrc_tf_free",
-    "vrc_occupancy_build", "vrc_occupancy_get", "vrc_render", "vrc_render_host", "vrc_last_device_error",
+    "vrc_occupancy_build", "vrc_occupancy_get", "vrc_render", "vrc_render_host",
+    "vrc_render_noalloc", "vrc_last_device_error",
     "vrc_last_error_message", "vrc_status_str", "vrc_version",
 ]
 
@@ -80,6 +81,8 @@ def load(build_if_missing: bool = False):
     L.vrc_occupancy_get.argtypes = [vp, ip, ip, ip, vp, vp]
     L.vrc_render.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp, vp]
     L.vrc_render_host.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp]
+    L.vrc_render_noalloc.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
+                                     vp, vp]
     L.vrc_last_device_error.argtypes = [vp, pint, vp]
     L.vrc_last_error_message.argtypes = [vp]
     L.vrc_last_error_message.restype = C.c_char_p
