@@ -80,7 +80,7 @@ typedef struct {
  *                  size (requires vrc_bricks_build for that size; the image is identical
  *                  to brick = 0).
  *   seg_len        adjoint checkpoint interval in samples (0 = default 64).
- *   kernel         0 = automatic (warp-cooperative), 1 = one ray per thread,
+ *   kernel         0 = automatic (one ray per thread), 1 = one ray per thread,
  *                  2 = warp-cooperative (one ray per warp, 32 samples per step). Both
  *                  kernels compute the same method; images agree within float rounding. */
 typedef struct {

@@ -36,7 +36,9 @@
  *              inside an empty brick are jumped over. Skipped samples have alpha == 0, so the
  *              image equals the no-skip image bit for bit.
  *   gradient   reverse mode through compositing, opacity, classification and resampling,
- *              w.r.t. the TF entries and the voxel values (see orc_render_grad).
+ *              w.r.t. the TF entries and the voxel values (see orc_render_grad). At the kinks
+ *              of the opacity clamp (a = 0, a = 1-2^-24) and of the index clamp (u = 0, 255)
+ *              the derivative is taken on the clamped side (0).
  */
 #include <math.h>
 #include <stdint.h>
@@ -641,7 +643,10 @@ int orc_render_grad(const void *data, int dtype, int nx, int ny, int nz, const f
                 dalpha *= r->T;
                 double a = r->a;
                 double raw = r->c.rgba[3];
-                double da = (raw >= 0.0 && raw <= ALPHA_MAX)
+                /* The clamp of the opacity to [0, 1-2^-24] has kinks at both ends; there the
+                 * derivative is the one-sided value on the clamped side (0). At a = 0 this makes
+                 * a sample in an empty brick contribute nothing, with or without leaping. */
+                double da = (raw > 0.0 && raw <= ALPHA_MAX)
                                 ? r->delta * pow(1.0 - a, r->delta - 1.0) : 0.0;
                 drgba[3] = dalpha * da;
                 for (int c = 0; c < 4; ++c) {

@@ -8,7 +8,7 @@
 // front-to-back compositing, early ray termination. With a brick table the ray leaps over
 // boxes of empty bricks ahead of it (Sec. "Analysis", Pros (b): auxiliary structures to skip
 // empty space), using the forward-box distance field of its direction octant. A sample is
-// skipped only when it lies, by a margin of MARGIN voxels beyond any rounding of its
+// skipped only when it lies, by a margin of LEAP_MARGIN voxels beyond any rounding of its
 // position, inside an empty brick, where its opacity is exactly zero; the image is therefore
 // identical bit for bit with and without leaping.
 //
@@ -18,11 +18,6 @@
 #include "vrc_internal.h"
 
 namespace vrc {
-
-// Leaping decisions use float positions and exit distances whose combined error stays below
-// ~1.5e-3 voxel for coordinates up to 4096; a sample is leapt over only when it sits at least
-// MARGIN inside a box of empty bricks.
-constexpr float MARGIN = 4.0e-3f;
 
 // Cubic B-spline sample at integer base ip (taps ip-1 .. ip+2) with fractions f, from the
 // x-replicated float4 volume: entry (ip0 + 1, ip1 + 1 + b, ip2 + 1 + c) holds tap row (b, c).
@@ -55,58 +50,6 @@ __device__ __forceinline__ float tricubic_rep(const ReplView &rp, const int ip[3
 
 __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by, int bz) {
     return (bz * bv.nb[1] + by) * bv.nb[0] + bx;
-}
-
-// Leap mode for sample j. Returns the next sample index to look at: > j when sample j (and
-// every sample before the returned index) lies MARGIN inside a forward box of empty bricks,
-// or j itself when sample j needs its exact position. `dist` is the field of the ray's octant.
-__device__ __forceinline__ int leap(const BrickView &bv, const uint8_t *__restrict__ dist,
-                                    const float Pf[3], const float df[3], const float inv_df[3],
-                                    float step, float inv_step, int nseg, int j, int &cache_lin,
-                                    int &cache_r) {
-    if (j == nseg - 1) return j;  // the last segment's midpoint is not (j + 1/2) ds
-    const float m = ((float)j + 0.5f) * step;
-    float pa[3];
-    int b[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        pa[k] = fmaf(m, df[k], Pf[k]);
-        const int fl = (int)floorf(pa[k]);
-        b[k] = min(max(fl, 0) >> bv.shift, bv.nb[k] - 1);
-    }
-    const int lin = brick_linear(bv, b[0], b[1], b[2]);
-    if (lin != cache_lin) {
-        cache_lin = lin;
-        cache_r = dist[lin];
-    }
-    const int r = cache_r;
-    if (r == 0) return j;
-    const float B = (float)bv.B;
-    float texit = INFINITY;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        // sample j must sit MARGIN inside its own brick (interior faces only)
-        const float lo = (float)(b[k] * bv.B), hi = lo + B;
-        if ((b[k] > 0 && pa[k] < lo + MARGIN) || (b[k] < bv.nb[k] - 1 && pa[k] > hi - MARGIN))
-            return j;
-        // exit of the empty forward box of extent r - 1 bricks, face moved inward by MARGIN
-        float face;
-        if (df[k] > 0.0f) {
-            if (b[k] + r >= bv.nb[k]) continue;
-            face = (float)((b[k] + r) * bv.B) - MARGIN;
-        } else if (df[k] < 0.0f) {
-            if (b[k] - r + 1 <= 0) continue;
-            face = (float)((b[k] - r + 1) * bv.B) + MARGIN;
-        } else {
-            continue;
-        }
-        texit = fminf(texit, (face - Pf[k]) * inv_df[k]);
-    }
-    if (!(texit < INFINITY)) return nseg;
-    // first sample whose midpoint may reach the moved face
-    const float jf = ceilf(fmaf(texit, inv_step, -0.5f));
-    const int jn = jf >= (float)nseg ? nseg : (int)jf;
-    return max(jn, j + 1);
 }
 
 constexpr int RAY_WARPS = 2;  // warps per CTA
@@ -156,8 +99,8 @@ __global__ void __launch_bounds__(32 * RAY_WARPS, 16 / RAY_WARPS) render_ray_ker
                 break;
             }
             if (ESL && !in_run) {
-                const int jn = leap(L.bricks, dist, Pf, df, inv_df, step, inv_step, ray.nseg, j,
-                                    leap_lin, leap_r);
+                const int jn = leap_float(L.bricks, dist, Pf, df, inv_df, step, inv_step,
+                                          ray.nseg, j, leap_lin, leap_r);
                 if (jn != j) {
                     j = jn;
                     continue;

@@ -24,7 +24,6 @@ namespace vrc {
 
 constexpr int WC_WARPS = 8;         // warps per CTA; the CTA renders a 16 x 16 pixel tile
 constexpr int WC_RAYS = 32 * WC_WARPS;
-constexpr float WC_MARGIN = 4.0e-3f;  // same leaping margin as the per-ray kernel
 
 struct RayRec {
     RayPos rp;
@@ -59,52 +58,6 @@ __device__ __forceinline__ float tricubic_rep4(const ReplView &rp, const int ip[
     return s;
 }
 
-__device__ __forceinline__ int wc_brick_of(const BrickView &bv, const int ip[3]) {
-    return ((max(ip[2], 0) >> bv.shift) * bv.nb[1] + (max(ip[1], 0) >> bv.shift)) * bv.nb[0] +
-           (max(ip[0], 0) >> bv.shift);
-}
-
-// Float leap for sample j (see the per-ray kernel): returns > j when samples j .. result-1
-// lie WC_MARGIN inside a forward box of empty bricks, else j.
-__device__ __forceinline__ int wc_leap(const BrickView &bv, const uint8_t *__restrict__ dist,
-                                       const float Pf[3], const float df[3],
-                                       const float inv_df[3], float step, float inv_step,
-                                       int nseg, int j) {
-    if (j >= nseg - 1) return j;
-    const float m = ((float)j + 0.5f) * step;
-    float pa[3];
-    int b[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        pa[k] = fmaf(m, df[k], Pf[k]);
-        b[k] = min(max((int)floorf(pa[k]), 0) >> bv.shift, bv.nb[k] - 1);
-    }
-    const int r = dist[(b[2] * bv.nb[1] + b[1]) * bv.nb[0] + b[0]];
-    if (r == 0) return j;
-    float texit = INFINITY;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float lo = (float)(b[k] * bv.B), hi = lo + (float)bv.B;
-        if ((b[k] > 0 && pa[k] < lo + WC_MARGIN) || (b[k] < bv.nb[k] - 1 && pa[k] > hi - WC_MARGIN))
-            return j;
-        float face;
-        if (df[k] > 0.0f) {
-            if (b[k] + r >= bv.nb[k]) continue;
-            face = (float)((b[k] + r) * bv.B) - WC_MARGIN;
-        } else if (df[k] < 0.0f) {
-            if (b[k] - r + 1 <= 0) continue;
-            face = (float)((b[k] - r + 1) * bv.B) + WC_MARGIN;
-        } else {
-            continue;
-        }
-        texit = fminf(texit, (face - Pf[k]) * inv_df[k]);
-    }
-    if (!(texit < INFINITY)) return nseg;
-    const float jf = ceilf(fmaf(texit, inv_step, -0.5f));
-    const int jn = jf >= (float)nseg ? nseg : (int)jf;
-    return max(jn, j + 1);
-}
-
 // From sample j, the first sample whose exact position lies in an occupied brick (or nseg).
 // Deterministic in its inputs, so every lane of a warp gets the same answer.
 __device__ __forceinline__ int wc_advance(const RayPos &rp, const RenderLaunch &L,
@@ -112,8 +65,10 @@ __device__ __forceinline__ int wc_advance(const RayPos &rp, const RenderLaunch &
                                           const float df[3], const float inv_df[3],
                                           float inv_step, int j) {
     const float step = L.grid.step;
+    int cache_lin = -1, cache_r = 0;
     while (j < rp.nseg) {
-        const int jn = wc_leap(L.bricks, dist, Pf, df, inv_df, step, inv_step, rp.nseg, j);
+        const int jn = leap_float(L.bricks, dist, Pf, df, inv_df, step, inv_step, rp.nseg, j,
+                                  cache_lin, cache_r);
         if (jn != j) {
             j = jn;
             continue;
@@ -122,7 +77,7 @@ __device__ __forceinline__ int wc_advance(const RayPos &rp, const RenderLaunch &
         int ip[3];
         float f[3];
         place(rp, step, L.grid.n, j, ip, f, delta);
-        if (dist[wc_brick_of(L.bricks, ip)] == 0) return j;
+        if (dist[brick_of(L.bricks, ip)] == 0) return j;
         ++j;
     }
     return rp.nseg;
@@ -202,7 +157,7 @@ __global__ void __launch_bounds__(WC_RAYS, 2) render_warp_kernel(RenderLaunch L)
                 int ip[3];
                 float f[3];
                 place(rp, step, L.grid.n, j, ip, f, delta);
-                if (ESL && dist[wc_brick_of(L.bricks, ip)] != 0) live = false;
+                if (ESL && dist[brick_of(L.bricks, ip)] != 0) live = false;
                 if (live) {
                     const float s = tricubic_rep4(L.rep, ip, f);
                     const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);

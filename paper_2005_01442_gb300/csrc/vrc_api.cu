@@ -600,7 +600,7 @@ vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam
     if (s != VRC_OK) return s;
     L.out = (float4 *)out_rgba_dev;
     L.counters = counters_dev;
-    CK(params->kernel == 1 ? launch_render_ray(L, st) : launch_render_warp(L, st), "render launch");
+    CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
     return VRC_OK;
 }
 
@@ -627,7 +627,7 @@ vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera
     if (s != VRC_OK) return s;
     L.out = ctx->host_img;
     L.counters = nullptr;
-    CK(params->kernel == 1 ? launch_render_ray(L, st) : launch_render_warp(L, st), "render launch");
+    CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
     CK(cudaMemcpyAsync(out_rgba_host, ctx->host_img, bytes, cudaMemcpyDeviceToHost, st),
        "image copy");
     CK(cudaStreamSynchronize(st), "image copy sync");
