@@ -104,6 +104,12 @@ vrc_status vrc_destroy(vrc_ctx *ctx);
  * Sizes must be 1..32768 per axis. Returns the new volume id in *vol_id. */
 vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_dtype dtype,
                              int nx, int ny, int nz, int *vol_id, void *stream);
+/* Overwrites the values of a resident volume (same dtype and sizes as uploaded) from host
+ * (on_device = 0) or device memory, e.g. between optimisation steps. Brick tables built
+ * before are stale afterwards: rebuild them before rendering with empty-space leaping.
+ * Allocates nothing for device data; host data goes through a temporary device copy. */
+vrc_status vrc_volume_update(vrc_ctx *ctx, int vol_id, const void *data, int on_device,
+                             void *stream);
 /* Frees a resident volume and its brick tables. */
 vrc_status vrc_volume_free(vrc_ctx *ctx, int vol_id);
 /* Reports a resident volume's dtype and sizes. Any output pointer may be NULL. */
@@ -155,6 +161,22 @@ vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam
  * pinned memory gives an asynchronous copy). Returns after the copy has completed. */
 vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                            const vrc_params *params, float *out_rgba_host, void *stream);
+
+/* Reverse mode of vrc_render (same volume, transfer function, camera and parameters):
+ * given grad_out_dev = dL/d(image) (height x width x 4 floats, 16-byte aligned), ADDS
+ * dL/d(table) to grad_tf_dev (256 x 4 floats) and, when grad_vol_dev is not NULL,
+ * dL/d(voxel values) to grad_vol_dev (nx*ny*nz floats, x fastest; any voxel dtype, values
+ * treated as reals). The forward model is the paper's (Sec. "Methodology": cubic-spline
+ * resampling, post-classification, front-to-back accumulation, early termination); its
+ * reverse is not in the paper. Each ray replays its forward pass exactly, keeps the
+ * transmittance at the start of every params->seg_len samples (1..128, 0 = 64) in
+ * per-thread memory, and walks the segments back to front, recomputing each from its
+ * checkpoint. Early termination is treated as a fixed decision; the opacity clamp has zero
+ * derivative at its ends. Rays may hold at most 256 * seg_len samples (VRC_ERR_ARG
+ * otherwise). Gradients are summed with float atomics: the last bits vary between runs. */
+vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                               const vrc_params *params, const float *grad_out_dev,
+                               float *grad_tf_dev, float *grad_vol_dev, void *stream);
 
 /* Size of the device array that vrc_render_noalloc works in (8 MiB). */
 #define VRC_NOALLOC_SCRATCH_BYTES (8u << 20)

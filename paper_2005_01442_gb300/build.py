@@ -19,8 +19,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libvrc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-              "-I", CSRC, "--expt-relaxed-constexpr"]
+# -fmad=false: no implicit multiply-add contraction, so the same source expression rounds
+# the same way in every kernel (the adjoint replays the forward's transmittances bit for bit);
+# every fused multiply-add in the kernels is written out with fmaf.
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I",
+              INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

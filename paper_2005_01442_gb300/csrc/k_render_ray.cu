@@ -19,35 +19,6 @@
 
 namespace vrc {
 
-// Cubic B-spline sample at integer base ip (taps ip-1 .. ip+2) with fractions f, from the
-// x-replicated float4 volume: entry (ip0 + 1, ip1 + 1 + b, ip2 + 1 + c) holds tap row (b, c).
-__device__ __forceinline__ float tricubic_rep(const ReplView &rp, const int ip[3],
-                                              const float f[3]) {
-    float wx[4], wy[4], wz[4];
-    bspline_w(f[0], wx);
-    bspline_w(f[1], wy);
-    bspline_w(f[2], wz);
-    const long rslice = (long)rp.rnx * rp.rny;
-    const float4 *p0 = rp.base + ((long)(ip[2] + 1) * rp.rny + (ip[1] + 1)) * rp.rnx + (ip[0] + 1);
-    float s = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float4 *pc = p0 + c * rslice;
-        float plane = 0.0f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const float4 v = __ldg(pc + b * rp.rnx);
-            float r = wx[0] * v.x;
-            r = fmaf(wx[1], v.y, r);
-            r = fmaf(wx[2], v.z, r);
-            r = fmaf(wx[3], v.w, r);
-            plane = fmaf(wy[b], r, plane);
-        }
-        s = fmaf(wz[c], plane, s);
-    }
-    return s;
-}
-
 __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by, int bz) {
     return (bz * bv.nb[1] + by) * bv.nb[0] + bx;
 }

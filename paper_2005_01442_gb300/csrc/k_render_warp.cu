@@ -31,33 +31,6 @@ struct RayRec {
     int pix;  // linear pixel index
 };
 
-__device__ __forceinline__ float tricubic_rep4(const ReplView &rp, const int ip[3],
-                                               const float f[3]) {
-    float wx[4], wy[4], wz[4];
-    bspline_w(f[0], wx);
-    bspline_w(f[1], wy);
-    bspline_w(f[2], wz);
-    const long rslice = (long)rp.rnx * rp.rny;
-    const float4 *p0 = rp.base + ((long)(ip[2] + 1) * rp.rny + (ip[1] + 1)) * rp.rnx + (ip[0] + 1);
-    float s = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float4 *pc = p0 + c * rslice;
-        float plane = 0.0f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const float4 v = __ldg(pc + b * rp.rnx);
-            float r = wx[0] * v.x;
-            r = fmaf(wx[1], v.y, r);
-            r = fmaf(wx[2], v.z, r);
-            r = fmaf(wx[3], v.w, r);
-            plane = fmaf(wy[b], r, plane);
-        }
-        s = fmaf(wz[c], plane, s);
-    }
-    return s;
-}
-
 // From sample j, the first sample whose exact position lies in an occupied brick (or nseg).
 // Deterministic in its inputs, so every lane of a warp gets the same answer.
 __device__ __forceinline__ int wc_advance(const RayPos &rp, const RenderLaunch &L,
@@ -159,7 +132,7 @@ __global__ void __launch_bounds__(WC_RAYS, 2) render_warp_kernel(RenderLaunch L)
                 place(rp, step, L.grid.n, j, ip, f, delta);
                 if (ESL && dist[brick_of(L.bricks, ip)] != 0) live = false;
                 if (live) {
-                    const float s = tricubic_rep4(L.rep, ip, f);
+                    const float s = tricubic_rep(L.rep, ip, f);
                     const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
                     int i0;
                     floor_small(u, i0);

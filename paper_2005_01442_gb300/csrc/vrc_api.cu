@@ -439,6 +439,34 @@ vrc_status vrc_volume_upload(vrc_ctx *ctx, const void *data, int on_device, vrc_
     return VRC_OK;
 }
 
+vrc_status vrc_volume_update(vrc_ctx *ctx, int vol_id, const void *data, int on_device,
+                             void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    if (!data) return fail(ctx, VRC_ERR_ARG, "data is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t raw = (size_t)v->n[0] * v->n[1] * v->n[2] * dtype_size(v->dtype);
+    const void *src = data;
+    void *staging = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        e = cudaMalloc(&staging, raw);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(staging, data, raw, cudaMemcpyHostToDevice, st);
+        src = staging;
+    }
+    if (e == cudaSuccess) e = launch_pad_volume(src, v->dtype, v->n, v->dpad, v->pnx, v->pny, v->pnz, st);
+    if (e == cudaSuccess) e = launch_replicate_x4(src, v->dtype, v->n, v->drep, st);
+    if (staging) {
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+        cudaFree(staging);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "volume update");
+    return VRC_OK;
+}
+
 vrc_status vrc_volume_free(vrc_ctx *ctx, int vol_id) {
     if (!ctx) return VRC_ERR_ARG;
     Volume *v = get_vol(ctx, vol_id);
@@ -631,6 +659,43 @@ vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera
     CK(cudaMemcpyAsync(out_rgba_host, ctx->host_img, bytes, cudaMemcpyDeviceToHost, st),
        "image copy");
     CK(cudaStreamSynchronize(st), "image copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
+                               const vrc_params *params, const float *grad_out_dev,
+                               float *grad_tf_dev, float *grad_vol_dev, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!params) return fail(ctx, VRC_ERR_ARG, "params is NULL");
+    if (!grad_out_dev || !grad_tf_dev)
+        return fail(ctx, VRC_ERR_ARG, "grad_out_dev and grad_tf_dev must be non-NULL");
+    if (((uintptr_t)grad_out_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "grad_out_dev must be 16-byte aligned");
+    if (((uintptr_t)grad_tf_dev & 3) != 0 || ((uintptr_t)grad_vol_dev & 3) != 0)
+        return fail(ctx, VRC_ERR_ARG, "gradient buffers must be 4-byte aligned");
+    const int seg = params->seg_len == 0 ? 64 : params->seg_len;
+    if (seg < 1 || seg > ADJ_MAX_SEG) return fail(ctx, VRC_ERR_ARG, "seg_len must be 0..128");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    AdjointLaunch A;
+    vrc_status s = prepare_render(ctx, vol_id, tf_id, cam, params, st, A.L);
+    if (s != VRC_OK) return s;
+    // longest possible ray: the box diagonal
+    const double diag = sqrt((double)A.L.grid.n[0] * A.L.grid.n[0] +
+                             (double)A.L.grid.n[1] * A.L.grid.n[1] +
+                             (double)A.L.grid.n[2] * A.L.grid.n[2]);
+    const double max_samples = ceil(diag / (double)params->step) + 2.0;
+    if (max_samples > (double)ADJ_MAX_CKPT * seg)
+        return fail(ctx, VRC_ERR_ARG,
+                    "rays may hold %.0f samples, above %d checkpoints x seg_len %d; raise "
+                    "seg_len or the step", max_samples, ADJ_MAX_CKPT, seg);
+    A.grad_out = (const float4 *)grad_out_dev;
+    A.grad_tf = grad_tf_dev;
+    A.grad_vol = grad_vol_dev;
+    A.seg = seg;
+    A.L.out = nullptr;
+    A.L.counters = nullptr;
+    CK(launch_adjoint(A, st), "adjoint launch");
     return VRC_OK;
 }
 

@@ -107,6 +107,35 @@ __device__ __forceinline__ int leap_float(const BrickView &bv, const uint8_t *__
     return max(jn, j + 1);
 }
 
+// Cubic B-spline sample at integer base ip (taps ip-1 .. ip+2) with fractions f, from the
+// x-replicated float4 volume: entry (ip0 + 1, ip1 + 1 + b, ip2 + 1 + c) holds tap row (b, c).
+__device__ __forceinline__ float tricubic_rep(const ReplView &rp, const int ip[3],
+                                              const float f[3]) {
+    float wx[4], wy[4], wz[4];
+    bspline_w(f[0], wx);
+    bspline_w(f[1], wy);
+    bspline_w(f[2], wz);
+    const long rslice = (long)rp.rnx * rp.rny;
+    const float4 *p0 = rp.base + ((long)(ip[2] + 1) * rp.rny + (ip[1] + 1)) * rp.rnx + (ip[0] + 1);
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 *pc = p0 + c * rslice;
+        float plane = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float4 v = __ldg(pc + b * rp.rnx);
+            float r = wx[0] * v.x;
+            r = fmaf(wx[1], v.y, r);
+            r = fmaf(wx[2], v.z, r);
+            r = fmaf(wx[3], v.w, r);
+            plane = fmaf(wy[b], r, plane);
+        }
+        s = fmaf(wz[c], plane, s);
+    }
+    return s;
+}
+
 __device__ __forceinline__ int brick_of(const BrickView &bv, const int ip[3]) {
     return ((max(ip[2], 0) >> bv.shift) * bv.nb[1] + (max(ip[1], 0) >> bv.shift)) * bv.nb[0] +
            (max(ip[0], 0) >> bv.shift);
@@ -144,5 +173,18 @@ cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, u
                              cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
 cudaError_t launch_render_warp(const RenderLaunch &L, cudaStream_t st);
+
+// Reverse mode of one render: grad_out is the loss gradient per pixel (H x W x RGBA);
+// grad_tf (256 x 4) and grad_vol (nx*ny*nz, x fastest, may be NULL) are accumulated.
+constexpr int ADJ_MAX_SEG = 128;   // largest checkpoint interval (samples)
+constexpr int ADJ_MAX_CKPT = 256;  // checkpoints per ray: rays up to 256 * seg samples
+struct AdjointLaunch {
+    RenderLaunch L;
+    const float4 *grad_out;
+    float *grad_tf;
+    float *grad_vol;
+    int seg;
+};
+cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st);
 
 }  // namespace vrc

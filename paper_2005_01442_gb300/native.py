@@ -20,10 +20,11 @@ STATUS = {0: "VRC_OK", -1: "VRC_ERR_ARG", -2: "VRC_ERR_OOM", -3: "VRC_ERR_CUDA",
 
 # Every symbol include/vrc.h declares (checked by the CPU test suite).
 EXPORTS = [
-    "vrc_create", "vrc_destroy", "vrc_volume_upload", "vrc_volume_free", "vrc_volume_info",
+    "vrc_create", "vrc_destroy", "vrc_volume_upload", "vrc_volume_update", "vrc_volume_free",
+    "vrc_volume_info",
     "vrc_bricks_build", "vrc_bricks_get", "vrc_tf_set", "vrc_tf_update", "vrc_tf_free",
     "vrc_occupancy_build", "vrc_occupancy_get", "vrc_render", "vrc_render_host",
-    "vrc_render_noalloc", "vrc_last_device_error",
+    "vrc_render_noalloc", "vrc_render_backward", "vrc_last_device_error",
     "vrc_last_error_message", "vrc_status_str", "vrc_version",
 ]
 
@@ -70,6 +71,7 @@ def load(build_if_missing: bool = False):
     L.vrc_create.argtypes = [C.POINTER(vp), ip]
     L.vrc_destroy.argtypes = [vp]
     L.vrc_volume_upload.argtypes = [vp, vp, ip, ip, ip, ip, ip, pint, vp]
+    L.vrc_volume_update.argtypes = [vp, ip, vp, ip, vp]
     L.vrc_volume_free.argtypes = [vp, ip]
     L.vrc_volume_info.argtypes = [vp, ip, pint, pint, pint, pint]
     L.vrc_bricks_build.argtypes = [vp, ip, ip, vp]
@@ -83,6 +85,8 @@ def load(build_if_missing: bool = False):
     L.vrc_render_host.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp]
     L.vrc_render_noalloc.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                      vp, vp]
+    L.vrc_render_backward.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params),
+                                      vp, vp, vp, vp]
     L.vrc_last_device_error.argtypes = [vp, pint, vp]
     L.vrc_last_error_message.argtypes = [vp]
     L.vrc_last_error_message.restype = C.c_char_p

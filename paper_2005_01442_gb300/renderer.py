@@ -86,6 +86,19 @@ class Renderer:
         self._vols[vid.value] = None
         return vid.value
 
+    def update_volume(self, vol_id: int, vol, stream=None):
+        """Overwrites a resident volume's values (same dtype and shape)."""
+        torch = _torch()
+        if isinstance(vol, torch.Tensor) and vol.is_cuda:
+            t = vol.contiguous()
+            self._ck(self.lib.vrc_volume_update(self.ctx, int(vol_id), C.c_void_p(t.data_ptr()), 1,
+                                                _stream_ptr(stream)))
+        else:
+            a = np.ascontiguousarray(vol)
+            self._ck(self.lib.vrc_volume_update(self.ctx, int(vol_id),
+                                                a.ctypes.data_as(C.c_void_p), 0,
+                                                _stream_ptr(stream)))
+
     def free_volume(self, vol_id: int):
         self._ck(self.lib.vrc_volume_free(self.ctx, int(vol_id)))
         self._vols.pop(vol_id, None)
@@ -173,6 +186,20 @@ class Renderer:
         self._ck(self.lib.vrc_render_host(self.ctx, int(vol_id), int(tf_id), C.byref(cs),
                                           C.byref(ps), C.c_void_p(ptr), _stream_ptr(stream)))
         return out
+
+    def render_backward(self, vol_id: int, tf_id: int, cam, grad_out, grad_tf, grad_vol=None,
+                        step: float = 0.5, ert: float = 1.0, brick: int = 0, seg_len: int = 64,
+                        stream=None):
+        """Adds dL/dTF to grad_tf (256x4 CUDA float32) and dL/dvoxel to grad_vol ((nz, ny, nx)
+        CUDA float32, optional) for dL/dimage = grad_out ((H, W, 4) CUDA float32)."""
+        g = grad_out.contiguous()
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, ert, brick, seg_len, 0)
+        self._ck(self.lib.vrc_render_backward(
+            self.ctx, int(vol_id), int(tf_id), C.byref(cs), C.byref(ps), C.c_void_p(g.data_ptr()),
+            C.c_void_p(grad_tf.data_ptr()),
+            C.c_void_p(grad_vol.data_ptr()) if grad_vol is not None else None,
+            _stream_ptr(stream)))
 
     def last_device_error(self, stream=None) -> int:
         code = C.c_int()
