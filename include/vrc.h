@@ -178,6 +178,33 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
                                const vrc_params *params, const float *grad_out_dev,
                                float *grad_tf_dev, float *grad_vol_dev, void *stream);
 
+/* ---- Batched serving. The paper's cloud server lets multiple clients use one application
+ * (Sec. "Cloud architecture"); here render requests of any resident volume, transfer
+ * function, camera and image size share one persistent launch. Requests are appended to a
+ * device FIFO while the kernel runs (a copy stream publishes them); its warps claim 8 x 4
+ * pixel tiles of the oldest unfinished request and render them with the same per-ray code
+ * as vrc_render, so every image equals the vrc_render image of the same request bit for
+ * bit. Tiles of successive requests overlap on the device. Every device wait is bounded:
+ * the kernel leaves after budget_ns, after idle_ns without work, or on vrc_server_destroy;
+ * vrc_server_pump relaunches it while requests are pending. */
+typedef struct vrc_server vrc_server;
+/* Creates a server on ctx with max_slots requests in flight at most (1..65536). */
+vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **server_out);
+/* Queues one render into out_rgba_dev (caller-owned, height x width x 4 floats, 16-byte
+ * aligned, untouched by the caller until completion). Returns a ticket for vrc_server_poll.
+ * Brick tables for params->brick must exist; the first request of a (volume, transfer
+ * function, brick size) builds its occupancy. VRC_ERR_BUSY when max_slots are in flight.
+ * params->kernel 2 is not served (the per-ray body is used). */
+vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id, const vrc_camera *cam,
+                             const vrc_params *params, float *out_rgba_dev, long long *ticket);
+/* Launches the persistent kernel if it is not running and requests are pending; *running
+ * (may be NULL) tells whether a launch is on the device after the call. */
+vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long long idle_ns, int *running);
+/* *done = 1 once every pixel of the ticket's image is written (the slot is then free). */
+vrc_status vrc_server_poll(vrc_server *s, long long ticket, int *done);
+/* Stops the kernel (between tiles), waits for it and frees the server. */
+vrc_status vrc_server_destroy(vrc_server *s);
+
 /* Size of the device array that vrc_render_noalloc works in (8 MiB). */
 #define VRC_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -1,0 +1,130 @@
+// The per-ray render body shared by the one-launch-per-image kernel and the persistent
+// serving kernel: one thread casts the ray of one pixel (paper, Sec. "Methodology": every
+// pixel is processed independently; the ray moves with a fixed step and accumulates colour;
+// cubic interpolation with post-classification is preferred).
+//
+// Per sample: exact placement from the double-float ray record, the 64-tap uniform cubic
+// B-spline read as 16 aligned float4 rows of the x-replicated volume through L1,
+// post-classification through the 256-entry table, opacity corrected to the segment length,
+// front-to-back compositing, early ray termination. With a brick table the ray leaps over
+// boxes of empty bricks ahead of it (Sec. "Analysis", Pros (b): auxiliary structures to skip
+// empty space), using the forward-box distance field of its direction octant. A sample is
+// skipped only when it lies, by a margin of LEAP_MARGIN voxels beyond any rounding of its
+// position, inside an empty brick, where its opacity is exactly zero; the image is therefore
+// identical bit for bit with and without leaping.
+#pragma once
+
+#include "vrc_internal.h"
+
+namespace vrc {
+
+__device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by, int bz) {
+    return (bz * bv.nb[1] + by) * bv.nb[0] + bx;
+}
+
+// Renders the 8 x 4 pixel tile `tile` (raster order over the image) of launch L with the
+// calling warp (all 32 lanes must call it together).
+template <bool ESL>
+__device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile) {
+    const int lane = threadIdx.x & 31;
+    const int tiles_x = (L.cam.width + 7) >> 3;
+    const int px = (tile % tiles_x) * 8 + (lane & 7);
+    const int py = (tile / tiles_x) * 4 + (lane >> 3);
+    const bool valid = px < L.cam.width && py < L.cam.height;
+    const float4 *__restrict__ tf_rgba = L.tf.rgba;
+    const float4 *__restrict__ tf_drgba = L.tf.drgba;
+
+    RaySetup ray;
+    ray.nseg = 0;
+    if (valid) ray_setup(L.cam, L.grid, px, py, ray);
+
+    const float step = L.grid.step, thr = L.grid.ert;
+    const float inv_step = 1.0f / step;
+    RayPos rp;
+    ray_pos_init(ray, step, rp);
+    float Pf[3], df[3], inv_df[3];
+    ray_float(rp, Pf, df, inv_df);
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Tr = 1.0f;
+    int executed = 0;
+    const uint8_t *dist = nullptr;
+    if (ESL) {
+        const int oct = (df[0] < 0.0f) | ((df[1] < 0.0f) << 1) | ((df[2] < 0.0f) << 2);
+        dist = L.dist + (long)oct * L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
+    }
+
+    int leap_lin = -1, leap_r = 0;      // dist cache of the leap path
+    int run_lin = -1, run_empty = 0;    // dist cache of the exact path
+    bool in_run = !ESL;                 // exact placement mode (vs leap mode)
+    bool done = ray.nseg == 0;
+    int j = 0;
+    while (true) {
+        // advance this lane to its next sample to composite
+        int ip[3];
+        float f[3], delta = 0.0f;
+        while (!done) {
+            if (j >= ray.nseg) {
+                done = true;
+                break;
+            }
+            if (ESL && !in_run) {
+                const int jn = leap_float(L.bricks, dist, Pf, df, inv_df, step, inv_step,
+                                          ray.nseg, j, leap_lin, leap_r);
+                if (jn != j) {
+                    j = jn;
+                    continue;
+                }
+                in_run = true;
+            }
+            place(rp, step, L.grid.n, j, ip, f, delta);
+            if (ESL) {
+                const int lin = brick_linear(L.bricks, max(ip[0], 0) >> L.bricks.shift,
+                                             max(ip[1], 0) >> L.bricks.shift,
+                                             max(ip[2], 0) >> L.bricks.shift);
+                if (lin != run_lin) {
+                    run_lin = lin;
+                    run_empty = dist[lin] != 0;
+                }
+                if (run_empty) {  // in an empty brick: opacity zero, back to leaping
+                    ++j;
+                    in_run = false;
+                    continue;
+                }
+            }
+            break;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        if (!done) {
+            const float s = tricubic_rep(L.rep, ip, f);
+            // post-classification: u = (s - lo) * du on [0, 255], linear between entries
+            const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
+            int i0;
+            floor_small(u, i0);
+            i0 = min(i0, 254);
+            const float fu = u - (float)i0;
+            const float4 c0 = __ldg(tf_rgba + i0), dc = __ldg(tf_drgba + i0);
+            const float a = fmaf(fu, dc.w, c0.w);
+            const float alpha = segment_alpha(a, delta);
+            const float w = Tr * alpha;
+            C0 = fmaf(w, fmaf(fu, dc.x, c0.x), C0);
+            C1 = fmaf(w, fmaf(fu, dc.y, c0.y), C1);
+            C2 = fmaf(w, fmaf(fu, dc.z, c0.z), C2);
+            Tr = Tr - w;
+            ++executed;
+            if (1.0f - Tr > thr) done = true;
+            ++j;
+        }
+    }
+    if (valid) L.out[(long)py * L.cam.width + px] = make_float4(C0, C1, C2, 1.0f - Tr);
+
+    if (L.counters) {
+        unsigned int nom = (unsigned)ray.nseg, ex = (unsigned)executed;
+        nom = __reduce_add_sync(0xffffffffu, nom);
+        ex = __reduce_add_sync(0xffffffffu, ex);
+        if (lane == 0) {
+            atomicAdd(&L.counters[0], (unsigned long long)nom);
+            atomicAdd(&L.counters[1], (unsigned long long)ex);
+        }
+    }
+}
+
+}  // namespace vrc

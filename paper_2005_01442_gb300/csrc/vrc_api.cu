@@ -813,3 +813,189 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
     return VRC_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+// Persistent batched serving (kernel in k_serve.cu). The host side publishes requests into
+// device memory through a copy stream while the persistent kernel runs on its own stream.
+struct vrc_server {
+    vrc_ctx *ctx = nullptr;
+    int max_slots = 0, cap = 0, ctas = 0;
+    ServeSlot *d_slots = nullptr;
+    ServeEntry *d_queue = nullptr;
+    ServeCtl *d_ctl = nullptr;
+    int *h_done = nullptr, *d_done = nullptr;        // host-mapped completion flags
+    ServeSlot *h_slot_stage = nullptr;               // pinned staging, one record per slot
+    ServeEntry *h_entry_stage = nullptr;             // pinned staging ring (cap)
+    unsigned long long *h_tail_stage = nullptr;      // pinned staging ring (cap)
+    int *h_stop_stage = nullptr;
+    cudaStream_t s_ctl = nullptr, s_run = nullptr;
+    cudaEvent_t ev_run = nullptr;
+    bool launched = false;
+    unsigned long long tail = 0;
+    long long next_seq = 0;
+    std::vector<long long> slot_seq;  // request in each slot, -1 when free
+};
+
+namespace {
+
+void server_free(vrc_server *s) {
+    if (!s) return;
+    if (s->s_run) cudaStreamSynchronize(s->s_run);
+    if (s->s_ctl) cudaStreamSynchronize(s->s_ctl);
+    cudaFree(s->d_slots);
+    cudaFree(s->d_queue);
+    cudaFree(s->d_ctl);
+    cudaFreeHost(s->h_done);
+    cudaFreeHost(s->h_slot_stage);
+    cudaFreeHost(s->h_entry_stage);
+    cudaFreeHost(s->h_tail_stage);
+    cudaFreeHost(s->h_stop_stage);
+    if (s->ev_run) cudaEventDestroy(s->ev_run);
+    if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
+    if (s->s_run) cudaStreamDestroy(s->s_run);
+    delete s;
+}
+
+bool server_slot_free(vrc_server *s, int slot) {
+    const long long q = s->slot_seq[slot];
+    return q < 0 || *(volatile int *)&s->h_done[slot] == (int)q;
+}
+
+}  // namespace
+
+extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **out) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!out) return fail(ctx, VRC_ERR_ARG, "out is NULL");
+    if (max_slots < 1 || max_slots > 65536) return fail(ctx, VRC_ERR_ARG, "max_slots must be 1..65536");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    vrc_server *s = new (std::nothrow) vrc_server();
+    if (!s) return fail(ctx, VRC_ERR_OOM, "server allocation failed");
+    s->ctx = ctx;
+    s->max_slots = max_slots;
+    s->cap = 4 * max_slots;
+    s->slot_seq.assign(max_slots, -1);
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    ck(cudaMalloc(&s->d_slots, sizeof(ServeSlot) * max_slots));
+    ck(cudaMalloc(&s->d_queue, sizeof(ServeEntry) * s->cap));
+    ck(cudaMalloc(&s->d_ctl, sizeof(ServeCtl)));
+    ck(cudaHostAlloc(&s->h_done, sizeof(int) * max_slots, cudaHostAllocMapped));
+    ck(cudaHostAlloc(&s->h_slot_stage, sizeof(ServeSlot) * max_slots, cudaHostAllocDefault));
+    ck(cudaHostAlloc(&s->h_entry_stage, sizeof(ServeEntry) * s->cap, cudaHostAllocDefault));
+    ck(cudaHostAlloc(&s->h_tail_stage, sizeof(unsigned long long) * s->cap, cudaHostAllocDefault));
+    ck(cudaHostAlloc(&s->h_stop_stage, sizeof(int), cudaHostAllocDefault));
+    if (e == cudaSuccess) ck(cudaHostGetDevicePointer((void **)&s->d_done, s->h_done, 0));
+    ck(cudaStreamCreateWithFlags(&s->s_ctl, cudaStreamNonBlocking));
+    ck(cudaStreamCreateWithFlags(&s->s_run, cudaStreamNonBlocking));
+    ck(cudaEventCreateWithFlags(&s->ev_run, cudaEventDisableTiming));
+    if (e == cudaSuccess) {
+        for (int i = 0; i < max_slots; ++i) s->h_done[i] = -1;
+        ck(cudaMemset(s->d_ctl, 0, sizeof(ServeCtl)));
+        ck(cudaMemset(s->d_slots, 0, sizeof(ServeSlot) * max_slots));
+        int per_sm = 0, sms = 0;
+        ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(), 32 * SERVE_WARPS, 0));
+        s->ctas = sms * (per_sm > 0 ? per_sm : 1);
+        ck(cudaDeviceSynchronize());
+    }
+    if (e != cudaSuccess) {
+        vrc_status st = cuda_fail(ctx, e, "server create");
+        server_free(s);
+        return st;
+    }
+    *out = s;
+    return VRC_OK;
+}
+
+extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
+                                        const vrc_camera *cam, const vrc_params *params,
+                                        float *out_rgba_dev, long long *ticket) {
+    if (!s) return VRC_ERR_ARG;
+    vrc_ctx *ctx = s->ctx;
+    if (!ticket) return fail(ctx, VRC_ERR_ARG, "ticket is NULL");
+    if (!out_rgba_dev || ((uintptr_t)out_rgba_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be a 16-byte aligned device pointer");
+    if (params && params->kernel == 2)
+        return fail(ctx, VRC_ERR_ARG, "the server renders with the per-ray kernel (kernel 0 or 1)");
+    DeviceGuard g(ctx->device);
+    const int slot = (int)(s->next_seq % s->max_slots);
+    if (!server_slot_free(s, slot)) return fail(ctx, VRC_ERR_BUSY, "all %d slots in flight", s->max_slots);
+    ServeSlot &rec = s->h_slot_stage[slot];
+    vrc_status st = prepare_render(ctx, vol_id, tf_id, cam, params, s->s_ctl, rec.L);
+    if (st != VRC_OK) return st;
+    rec.L.out = (float4 *)out_rgba_dev;
+    rec.L.counters = nullptr;
+    rec.ntiles = ((cam->width + 7) / 8) * ((cam->height + 3) / 4);
+    rec.next_tile = 0;
+    rec.done_tiles = 0;
+    const long long seq = s->next_seq++;
+    rec.seq = (int)(seq & 0x7fffffff);
+    s->slot_seq[slot] = rec.seq;
+    s->h_done[slot] = -1;
+    const int qi = (int)(s->tail % (unsigned long long)s->cap);
+    s->h_entry_stage[qi].slot = slot;
+    s->h_entry_stage[qi].seq = rec.seq;
+    s->tail += 1;
+    s->h_tail_stage[qi] = s->tail;
+    // record, then queue entry, then tail: stream order makes each visible before the next
+    CK(cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(ServeSlot), cudaMemcpyHostToDevice, s->s_ctl),
+       "server submit");
+    CK(cudaMemcpyAsync(s->d_queue + qi, &s->h_entry_stage[qi], sizeof(ServeEntry),
+                       cudaMemcpyHostToDevice, s->s_ctl), "server submit");
+    CK(cudaMemcpyAsync(&s->d_ctl->tail, &s->h_tail_stage[qi], sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, s->s_ctl), "server submit");
+    *ticket = rec.seq;
+    return VRC_OK;
+}
+
+extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long long idle_ns,
+                                      int *running) {
+    if (!s) return VRC_ERR_ARG;
+    vrc_ctx *ctx = s->ctx;
+    if (budget_ns <= 0 || idle_ns <= 0) return fail(ctx, VRC_ERR_ARG, "budget and idle must be > 0");
+    DeviceGuard g(ctx->device);
+    bool busy = false;
+    if (s->launched) {
+        cudaError_t q = cudaEventQuery(s->ev_run);
+        if (q == cudaErrorNotReady) busy = true;
+        else if (q != cudaSuccess) return cuda_fail(ctx, q, "serve kernel");
+    }
+    if (!busy) {
+        bool pending = false;
+        for (int i = 0; i < s->max_slots && !pending; ++i)
+            if (!server_slot_free(s, i)) pending = true;
+        if (pending) {
+            // the published tail must reach the device before the kernel could idle out
+            CK(cudaStreamSynchronize(s->s_ctl), "server publish");
+            CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done,
+                            (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
+                            s->s_run), "serve launch");
+            CK(cudaEventRecord(s->ev_run, s->s_run), "serve launch");
+            s->launched = true;
+            busy = true;
+        }
+    }
+    if (running) *running = busy ? 1 : 0;
+    return VRC_OK;
+}
+
+extern "C" vrc_status vrc_server_poll(vrc_server *s, long long ticket, int *done) {
+    if (!s) return VRC_ERR_ARG;
+    if (!done) return fail(s->ctx, VRC_ERR_ARG, "done is NULL");
+    const int slot = (int)(ticket % s->max_slots);
+    if (ticket < 0 || s->slot_seq[slot] != ticket)
+        return fail(s->ctx, VRC_ERR_ARG, "ticket %lld is not in flight", ticket);
+    *done = *(volatile int *)&s->h_done[slot] == (int)ticket ? 1 : 0;
+    if (*done) s->slot_seq[slot] = -1;
+    return VRC_OK;
+}
+
+extern "C" vrc_status vrc_server_destroy(vrc_server *s) {
+    if (!s) return VRC_OK;
+    DeviceGuard g(s->ctx->device);
+    *s->h_stop_stage = 1;
+    cudaMemcpyAsync(&s->d_ctl->stop, s->h_stop_stage, sizeof(int), cudaMemcpyHostToDevice, s->s_ctl);
+    server_free(s);
+    return VRC_OK;
+}

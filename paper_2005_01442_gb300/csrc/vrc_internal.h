@@ -187,4 +187,29 @@ struct AdjointLaunch {
 };
 cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st);
 
+// Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
+// entries in arrival order; ctl holds the device-side front and the host-published tail.
+constexpr int SERVE_WARPS = 2;  // warps per CTA of the persistent kernel
+struct ServeSlot {
+    RenderLaunch L;  // the request's render
+    int ntiles;      // 8 x 4 pixel tiles of its image
+    int next_tile;   // tiles claimed (device atomics)
+    int done_tiles;  // tiles finished (device atomics)
+    int seq;         // request sequence number (published on completion)
+};
+struct ServeEntry {
+    int slot;
+    int seq;
+};
+struct ServeCtl {
+    unsigned long long front;  // oldest queue entry that may still have unclaimed tiles
+    unsigned long long tail;   // entries published by the host
+    int stop;                  // host request to leave
+    int pad;
+};
+const void *serve_kernel_ptr();
+cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
+                         int *done_flags, unsigned long long budget_ns,
+                         unsigned long long idle_ns, int ctas, cudaStream_t st);
+
 }  // namespace vrc

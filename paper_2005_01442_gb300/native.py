@@ -24,7 +24,8 @@ EXPORTS = [
     "vrc_volume_info",
     "vrc_bricks_build", "vrc_bricks_get", "vrc_tf_set", "vrc_tf_update", "vrc_tf_free",
     "vrc_occupancy_build", "vrc_occupancy_get", "vrc_render", "vrc_render_host",
-    "vrc_render_noalloc", "vrc_render_backward", "vrc_last_device_error",
+    "vrc_render_noalloc", "vrc_render_backward", "vrc_server_create", "vrc_server_submit",
+    "vrc_server_pump", "vrc_server_poll", "vrc_server_destroy", "vrc_last_device_error",
     "vrc_last_error_message", "vrc_status_str", "vrc_version",
 ]
 
@@ -87,6 +88,12 @@ def load(build_if_missing: bool = False):
                                      vp, vp]
     L.vrc_render_backward.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params),
                                       vp, vp, vp, vp]
+    L.vrc_server_create.argtypes = [vp, ip, C.POINTER(vp)]
+    L.vrc_server_submit.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
+                                    C.POINTER(C.c_longlong)]
+    L.vrc_server_pump.argtypes = [vp, C.c_longlong, C.c_longlong, pint]
+    L.vrc_server_poll.argtypes = [vp, C.c_longlong, pint]
+    L.vrc_server_destroy.argtypes = [vp]
     L.vrc_last_device_error.argtypes = [vp, pint, vp]
     L.vrc_last_error_message.argtypes = [vp]
     L.vrc_last_error_message.restype = C.c_char_p

@@ -1,0 +1,110 @@
+"""Persistent batched serving on the GPU: every request's image in a mixed batch equals its
+image rendered alone by vrc_render (bit for bit: rays never interact and run the same code),
+requests overlap, the kernel leaves by itself when idle, and the open-loop driver works
+against both servers."""
+import numpy as np
+import pytest
+
+from paper_2005_01442_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_01442_gb300 import build
+    from paper_2005_01442_gb300.renderer import Renderer
+    build.build()
+    R = Renderer(0)
+    vols = [synth.ct_volume(s, seed=60 + k)
+            for k, s in enumerate([(48, 64, 64), (64, 64, 64), (40, 56, 72)])]
+    vids = []
+    for v in vols:
+        vid = R.upload_volume(v)
+        R.build_bricks(vid, 8)
+        vids.append(vid)
+    tids = [R.set_tf(synth.tf_ct(seed), synth.CT_LO, synth.CT_HI) for seed in (None, 1, 2, 3)]
+    dims = {vid: synth.dims_of(v) for vid, v in zip(vids, vols)}
+    yield torch, R, vids, tids, dims
+    R.close()
+
+
+def _requests(vids, tids, dims, n, seed):
+    from paper_2005_01442_gb300 import serve
+    rng = np.random.default_rng(seed)
+    sizes = [(64, 48), (128, 96), (32, 32), (96, 128)]
+    out = []
+    for k in range(n):
+        v = vids[int(rng.integers(len(vids)))]
+        w, h = sizes[int(rng.integers(len(sizes)))]
+        cam = synth.orbit_camera(int(rng.integers(1 << 30)), dims[v], w, h)
+        out.append(serve.Request(0.0, v, tids[int(rng.integers(len(tids)))], cam,
+                                 ert=[1.0, 0.999][k % 2], brick=[0, 8][(k // 2) % 2]))
+    return out
+
+
+def test_batched_images_equal_alone(env):
+    torch, R, vids, tids, dims = env
+    from paper_2005_01442_gb300 import serve
+    srv = serve.BatchedServer(R, max_slots=64, budget_ms=200.0, idle_ms=5.0)
+    reqs = _requests(vids, tids, dims, 48, 1)
+    outs, handles = [], []
+    for r in reqs:  # all submitted back to back: they share the persistent launch
+        o = torch.full((r.cam.height, r.cam.width, 4), float("nan"), device="cuda")
+        outs.append(o)
+        handles.append(srv.submit(r, o))
+    pending = set(range(len(reqs)))
+    import time
+    t0 = time.time()
+    while pending:
+        srv.pump()
+        pending = {k for k in pending if not srv.done(handles[k])}
+        assert time.time() - t0 < 60.0
+    torch.cuda.synchronize()
+    for r, o in zip(reqs, outs):
+        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick)
+        assert torch.equal(o, alone)
+    srv.close()
+
+
+def test_kernel_leaves_when_idle_and_relaunches(env):
+    torch, R, vids, tids, dims = env
+    from paper_2005_01442_gb300 import serve
+    import time
+    srv = serve.BatchedServer(R, max_slots=8, budget_ms=1000.0, idle_ms=2.0)
+    assert srv.pump() is False  # nothing pending: no launch
+    for round_ in range(3):
+        r = _requests(vids, tids, dims, 1, 10 + round_)[0]
+        o = torch.empty((r.cam.height, r.cam.width, 4), device="cuda")
+        h = srv.submit(r, o)
+        t0 = time.time()
+        while not srv.done(h):
+            srv.pump()
+            assert time.time() - t0 < 30.0
+        time.sleep(0.05)  # > idle limit: the kernel must have left by itself
+        torch.cuda.synchronize()
+        assert srv.pump() is False
+        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick)
+        assert torch.equal(o, alone)
+    srv.close()
+
+
+@pytest.mark.parametrize("kind", ["batched", "plain"])
+def test_open_loop_run(env, kind):
+    torch, R, vids, tids, dims = env
+    from paper_2005_01442_gb300 import serve
+    reqs = _requests(vids, tids, dims, 60, 2)
+    rng = np.random.default_rng(3)
+    t = np.cumsum(rng.exponential(1 / 300.0, len(reqs)))
+    for r, a in zip(reqs, t):
+        r.arrival = float(a)
+    srv = serve.BatchedServer(R, max_slots=32) if kind == "batched" else serve.PlainServer(R)
+    budget = serve.ImageBudget(1 << 20, lambda h, w: torch.empty((h, w, 4), device="cuda"))
+    res = serve.run_open_loop(srv, reqs, budget, warmup=0.02)
+    srv.close()
+    assert res["requests"] > 0 and len(res["latencies_s"]) == res["requests"]
+    assert res["p50_ms"] > 0 and res["p99_ms"] >= res["p50_ms"]
+    assert budget.used == 0
