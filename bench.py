@@ -41,7 +41,7 @@ METRIC = ("Gsamples/s & Mrays/s (512²×400 CT, 1024² img) vs roofline; "
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="vrc", choices=["vrc", "reference"])
     p.add_argument("--brick", type=int, default=8)
@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--kernel", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--mode", default="render", choices=["render", "serve", "adjoint", "large"])
+    p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
 
@@ -63,7 +66,7 @@ def workload_config(args):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,7 +83,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -188,6 +191,43 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+SERVE_SIZES = [(512, 512), (1024, 1024), (2048, 2048)]
+
+
+def serve_bench(R, torch, vols, tids, runs, warmup, brick, seed):
+    """Open-loop Poisson load (seeded) of mixed volumes, transfer functions, orbit cameras and
+    image sizes, replayed against the one-launch-per-request server and the persistent
+    batched server for each (offered rate, seconds) run; admission by a 2 GiB image budget.
+    A rate above capacity measures the sustained images/s of each server."""
+    from paper_2005_01442_gb300 import serve, synth
+
+    def cam_fn(rng, v, w, h):
+        return synth.orbit_camera(rng, vols[v], w, h)
+
+    for v in vols:
+        for t in tids:
+            R.build_occupancy(v, t, brick)
+    torch.cuda.synchronize()
+    out = {"volumes": [list(d) for d in vols.values()], "transfer_functions": len(tids),
+           "images": [f"{w}x{h}" for w, h in SERVE_SIZES],
+           "warmup_s": warmup, "hbm_image_budget_bytes": 2 << 30, "runs": []}
+    for rate, seconds in runs:
+        reqs = serve.poisson_requests(seed, rate, seconds + warmup, list(vols), tids,
+                                      SERVE_SIZES, cam_fn, brick=brick)
+        for kind in ("plain", "batched"):
+            srv = serve.BatchedServer(R, max_slots=1024) if kind == "batched" else \
+                serve.PlainServer(R)
+            budget = serve.ImageBudget(2 << 30, lambda h, w: torch.empty(
+                (h, w, 4), dtype=torch.float32, device="cuda"))
+            res = serve.run_open_loop(srv, reqs, budget, warmup=warmup)
+            srv.close()
+            res.pop("latencies_s")
+            res.pop("records")
+            res["offered_rate"] = rate
+            out["runs"].append(res)
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -212,6 +252,11 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
     gpu_id = f"GPU-{uuid}" if uuid is not None else str(local)
+    if args.mode != "render":
+        R = Renderer(local)
+        run_mode(args, torch, R, synth)
+        R.close()
+        return
 
     vol = synth.ct_volume()
     tf = synth.tf_ct()
@@ -343,10 +388,128 @@ def main():
         if clocks.get("sm_mhz"):
             line["roofline"]["frac_at_measured_clock"] = achieved / (
                 sms * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+        if not args.no_serve:
+            small = synth.ct_volume((256, 256, 256), seed=5)
+            sid = R.upload_volume(small)
+            R.build_bricks(sid, B)
+            tids = [tid] + [R.set_tf(synth.tf_ct(k), synth.CT_LO, synth.CT_HI) for k in (1, 2, 3)]
+            vols = {vid: dims, sid: synth.dims_of(small)}
+            line["serving"] = serve_bench(R, torch, vols, tids,
+                                          [(200.0, args.serve_seconds), (900.0, 4.0),
+                                           (1200.0, 4.0)], 1.0, B, seed=5)
         print(json.dumps(line), flush=True)
     R.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _timed(torch, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_mode(args, torch, R, synth):
+    """--mode serve | adjoint | large: the serving, differentiation and large workloads; one
+    JSON line each (not the headline metric)."""
+    dev = torch.device("cuda", 0)
+    if args.mode == "serve":
+        specs = [((256, 256, 256), 5), ((400, 512, 512), 3), ((1200, 512, 512), 6)]
+        vols, tids = {}, []
+        for shape, seed in specs:
+            v = synth.ct_volume(shape, seed=seed)
+            vid = R.upload_volume(v)
+            R.build_bricks(vid, args.brick)
+            vols[vid] = synth.dims_of(v)
+            del v
+        tids = [R.set_tf(synth.tf_ct(k), synth.CT_LO, synth.CT_HI) for k in (None, 1, 2, 3)]
+        res = serve_bench(R, torch, vols, tids,
+                          [(200.0, 60.0), (600.0, 20.0), (900.0, 20.0), (1200.0, 10.0),
+                           (3000.0, 3.0)], 5.0, args.brick, seed=5)
+        print(json.dumps({"mode": "serve", "metric": "p50/p99 request latency (ms) and images/s",
+                          "data": "synthetic", "serving": res}), flush=True)
+        return
+    if args.mode == "adjoint":
+        vol = synth.ct_float_downsampled(7)
+        dims = synth.dims_of(vol)
+        cams = synth.orbit_cameras(7, 8, dims, 512, 512)
+        vid = R.upload_volume(vol)
+        R.build_bricks(vid, args.brick)
+        tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+        tgt_tf = R.set_tf(synth.tf_ct(8), synth.CT_LO, synth.CT_HI)
+        targets = [R.render(vid, tgt_tf, c, brick=args.brick).clone() for c in cams]
+        imgs = [torch.empty((512, 512, 4), device=dev) for _ in cams]
+        gtf = torch.zeros((256, 4), device=dev)
+        gvol = torch.zeros(vol.shape, device=dev)
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        for c, im in zip(cams, imgs):
+            R.render(vid, tid, c, brick=args.brick, out=im, counters=cnt)
+        torch.cuda.synchronize()
+        executed = int(cnt[1])
+
+        def fwd():
+            for c, im in zip(cams, imgs):
+                R.render(vid, tid, c, brick=args.brick, out=im)
+
+        def bwd():
+            for c, im, t in zip(cams, imgs, targets):
+                R.render_backward(vid, tid, c, 2.0 * (im - t), gtf, gvol, brick=args.brick)
+
+        for _ in range(args.warmup):
+            fwd()
+            bwd()
+        f_ms = _timed(torch, fwd, args.steps)
+        b_ms = _timed(torch, bwd, args.steps)
+        loss = float(sum(((im - t) ** 2).sum() for im, t in zip(imgs, targets)))
+        print(json.dumps({
+            "mode": "adjoint", "metric": "forward+adjoint Gsamples/s", "data": "synthetic",
+            "config": {"volume": [256, 256, 256], "volume_dtype": "float32",
+                       "cameras": 8, "image": [512, 512], "step": 0.5, "brick": args.brick,
+                       "loss": "L2 vs targets rendered with transfer function seed 8"},
+            "forward_ms_per_step": f_ms, "backward_ms_per_step": b_ms,
+            "executed_samples_per_step": executed, "loss": loss,
+            "value": executed / ((f_ms + b_ms) / 1e3) / 1e9, "unit": "Gsamples/s",
+            "gpu_launches": 8 * args.steps * 3}), flush=True)
+        return
+    if args.mode == "large":
+        vol = synth.ct_volume((2000, 512, 512), seed=9)
+        dims = synth.dims_of(vol)
+        vid = R.upload_volume(vol)
+        del vol
+        B = 16
+        R.build_bricks(vid, B)
+        tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+        cam = synth.orbit_cameras(9, 1, dims, 4096, 4096)[0]
+        img = torch.empty((4096, 4096, 4), device=dev)
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        R.render(vid, tid, cam, step=0.25, ert=0.999, brick=B, out=img, counters=cnt)
+        torch.cuda.synchronize()
+        nominal, executed = (int(x) for x in cnt.tolist())
+        g = torch.rand((4096, 4096, 4), device=dev) - 0.5
+        gtf = torch.zeros((256, 4), device=dev)
+        gvol = torch.zeros((dims[2], dims[1], dims[0]), device=dev)
+        fwd = lambda: R.render(vid, tid, cam, step=0.25, ert=0.999, brick=B, out=img)  # noqa
+        bwd = lambda: R.render_backward(vid, tid, cam, g, gtf, gvol, step=0.25,  # noqa
+                                        ert=0.999, brick=B, seg_len=64)
+        fwd()
+        bwd()
+        reps = max(1, min(args.steps, 3))
+        f_ms = _timed(torch, fwd, reps)
+        b_ms = _timed(torch, bwd, reps)
+        print(json.dumps({
+            "mode": "large", "metric": "forward and adjoint time, Gsamples/s", "data": "synthetic",
+            "config": {"volume": [512, 512, 2000], "volume_dtype": "int16", "image": [4096, 4096],
+                       "step": 0.25, "brick": B, "ert": 0.999, "seg_len": 64},
+            "nominal_samples": nominal, "executed_samples": executed,
+            "forward_ms": f_ms, "backward_ms": b_ms,
+            "forward_gsamples_per_s": executed / (f_ms / 1e3) / 1e9,
+            "mrays_per_s": 4096 * 4096 / (f_ms / 1e3) / 1e6}), flush=True)
+        return
 
 
 if __name__ == "__main__":

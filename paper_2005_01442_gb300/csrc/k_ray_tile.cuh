@@ -33,6 +33,12 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     const bool valid = px < L.cam.width && py < L.cam.height;
     const float4 *__restrict__ tf_rgba = L.tf.rgba;
     const float4 *__restrict__ tf_drgba = L.tf.drgba;
+    // launch fields read in the sample loop, copied once (free for a kernel parameter, one
+    // load per tile when the launch record sits in shared memory)
+    const BrickView bricks = L.bricks;
+    const ReplView rep = L.rep;
+    const int gn[3] = {L.grid.n[0], L.grid.n[1], L.grid.n[2]};
+    const float tf_lo = L.tf.lo, tf_du = L.tf.du;
 
     RaySetup ray;
     ray.nseg = 0;
@@ -67,7 +73,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                 break;
             }
             if (ESL && !in_run) {
-                const int jn = leap_float(L.bricks, dist, Pf, df, inv_df, step, inv_step,
+                const int jn = leap_float(bricks, dist, Pf, df, inv_df, step, inv_step,
                                           ray.nseg, j, leap_lin, leap_r);
                 if (jn != j) {
                     j = jn;
@@ -75,11 +81,11 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                 }
                 in_run = true;
             }
-            place(rp, step, L.grid.n, j, ip, f, delta);
+            place(rp, step, gn, j, ip, f, delta);
             if (ESL) {
-                const int lin = brick_linear(L.bricks, max(ip[0], 0) >> L.bricks.shift,
-                                             max(ip[1], 0) >> L.bricks.shift,
-                                             max(ip[2], 0) >> L.bricks.shift);
+                const int lin = brick_linear(bricks, max(ip[0], 0) >> bricks.shift,
+                                             max(ip[1], 0) >> bricks.shift,
+                                             max(ip[2], 0) >> bricks.shift);
                 if (lin != run_lin) {
                     run_lin = lin;
                     run_empty = dist[lin] != 0;
@@ -94,9 +100,9 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
         }
         if (__all_sync(0xffffffffu, done)) break;
         if (!done) {
-            const float s = tricubic_rep(L.rep, ip, f);
+            const float s = tricubic_rep(rep, ip, f);
             // post-classification: u = (s - lo) * du on [0, 255], linear between entries
-            const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
+            const float u = fminf(fmaxf((s - tf_lo) * tf_du, 0.0f), 255.0f);
             int i0;
             floor_small(u, i0);
             i0 = min(i0, 254);

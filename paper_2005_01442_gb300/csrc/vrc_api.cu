@@ -927,6 +927,14 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     rec.L.out = (float4 *)out_rgba_dev;
     rec.L.counters = nullptr;
     rec.ntiles = ((cam->width + 7) / 8) * ((cam->height + 3) / 4);
+    {
+        // a stride near ntiles / golden ratio, made coprime to ntiles
+        auto gcd = [](long a, long b) { while (b) { long t = a % b; a = b; b = t; } return a; };
+        long st = (long)(rec.ntiles * 0.6180339887) | 1;
+        while (rec.ntiles > 1 && gcd(st, rec.ntiles) != 1) ++st;
+        rec.stride = rec.ntiles > 1 ? (int)(st % rec.ntiles) : 1;
+        if (rec.stride == 0) rec.stride = 1;
+    }
     rec.next_tile = 0;
     rec.done_tiles = 0;
     const long long seq = s->next_seq++;
@@ -968,6 +976,7 @@ extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long l
         if (pending) {
             // the published tail must reach the device before the kernel could idle out
             CK(cudaStreamSynchronize(s->s_ctl), "server publish");
+            CK(cudaMemsetAsync(&s->d_ctl->leaving, 0, sizeof(int), s->s_run), "serve launch");
             CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done,
                             (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
                             s->s_run), "serve launch");

@@ -196,6 +196,8 @@ struct ServeSlot {
     int next_tile;   // tiles claimed (device atomics)
     int done_tiles;  // tiles finished (device atomics)
     int seq;         // request sequence number (published on completion)
+    int stride;      // tile order: k -> k * stride mod ntiles (stride coprime to ntiles)
+    int pad[3];
 };
 struct ServeEntry {
     int slot;
@@ -205,7 +207,7 @@ struct ServeCtl {
     unsigned long long front;  // oldest queue entry that may still have unclaimed tiles
     unsigned long long tail;   // entries published by the host
     int stop;                  // host request to leave
-    int pad;
+    int leaving;               // set by the first warp that times out; no new claims after it
 };
 const void *serve_kernel_ptr();
 cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,

@@ -174,7 +174,7 @@ def run_open_loop(server, requests, budget: ImageBudget, warmup: float = 0.0,
     images/s over the measured window and the offered rate."""
     waiting = collections.deque()   # arrived, not yet admitted (FIFO)
     inflight = []                   # (request, buffer, handle)
-    lat, done_times = [], []
+    lat, done_times, records = [], [], []
     i, n = 0, len(requests)
     t0 = clock()
     end_arrivals = requests[-1].arrival if requests else 0.0
@@ -202,6 +202,7 @@ def run_open_loop(server, requests, budget: ImageBudget, warmup: float = 0.0,
                 if r.arrival >= warmup:
                     lat.append(t - r.arrival)
                     done_times.append(t)
+                    records.append((r.arrival, r.cam.width, r.cam.height, t - r.arrival))
             else:
                 still.append((r, buf, hnd))
         inflight = still
@@ -216,4 +217,4 @@ def run_open_loop(server, requests, budget: ImageBudget, warmup: float = 0.0,
             "offered_per_s": len(measured) / window,
             "images_per_s": len(lat) / span if done_times else 0.0,
             "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
-            "latencies_s": lat}
+            "latencies_s": lat, "records": records}
