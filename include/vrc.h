@@ -4,7 +4,7 @@
  * The library renders a scalar CT volume by direct volume ray casting as described in the
  * paper's "Methodology" section: one ray per pixel from the observer, fixed-step sampling
  * along the ray, cubic-spline (uniform cubic B-spline) resampling, post-classification through
- * an RGBA transfer function ("palette", opacity 0 = transparent, 1 = opaque), front-to-back
+ * an RGBA transfer function (a palette; opacity 0 = transparent, 1 = opaque), front-to-back
  * accumulation, early ray termination, and empty-space leaping over block ("brick") min/max
  * auxiliary structures (Sec. "Analysis", Pros (a)-(b)). The calls follow that problem
  * statement: upload a volume, build its brick structure, set a transfer function and a
@@ -74,7 +74,7 @@ typedef struct {
  *                  last may be shorter); one sample sits at each segment midpoint and its
  *                  opacity is corrected to the segment length.
  *   ert_threshold  early ray termination: a ray stops after the sample where its
- *                  accumulated opacity exceeds this value (paper: "early beam completion");
+ *                  accumulated opacity exceeds this value (the paper's early termination);
  *                  >= 1 disables it.
  *   brick          0 = no empty-space leaping; 8 or 16 = leap over empty bricks of that
  *                  size (requires vrc_bricks_build for that size; the image is identical
@@ -178,7 +178,7 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
                                const vrc_params *params, const float *grad_out_dev,
                                float *grad_tf_dev, float *grad_vol_dev, void *stream);
 
-/* ---- Batched serving. The paper's cloud server lets multiple clients use one application
+/* ---- Batched serving. The paper's cloud server serves several clients from one application
  * (Sec. "Cloud architecture"); here render requests of any resident volume, transfer
  * function, camera and image size share one persistent launch. Requests are appended to a
  * device FIFO while the kernel runs (a copy stream publishes them); its warps claim 8 x 4

@@ -6,9 +6,9 @@
  * no source, header, helper or table.
  *
  * It restates, plainly and slowly, what the paper's renderer computes (Sec. "Methodology":
- * ray casting with one ray per pixel from the observer that "accumulates" colour while moving
+ * ray casting with one ray per pixel from the observer that gathers colour while moving
  * with a fixed step; cubic-spline resampling instead of trilinear; post-classification through
- * a transfer function T(V); blocks with an overlap, "auxiliary structures" for empty space
+ * a transfer function T(V); blocks with an overlap, auxiliary structures for empty space
  * leaping; front-to-back block order with early ray termination, Sec. "Analysis", Pros (b)).
  * The paper prints no formulas for these steps; the readings taken are:
  *

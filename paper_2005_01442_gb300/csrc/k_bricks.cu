@@ -1,6 +1,6 @@
 // Volume padding, brick min/max tables and transfer-function occupancy.
 //
-// Brick tables are the "auxiliary structures" of the paper's block decomposition
+// Brick tables are the auxiliary structures of the paper's block decomposition
 // (Sec. "Methodology", Fig. 3; Sec. "Analysis", Pros (b)): brick b covers voxels [bB, bB+B)
 // per axis and stores min/max over its apron box [bB-1, bB+B+1] clamped to the volume, the
 // overlap a cubic kernel reads. The occupancy of a brick under a transfer function is the

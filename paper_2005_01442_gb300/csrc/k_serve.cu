@@ -1,5 +1,5 @@
-// Persistent batched serving kernel. The paper's server lets "multiple clients use one
-// application" (Sec. "Cloud architecture", SaaS model); here many render requests of mixed
+// Persistent batched serving kernel. The paper's SaaS server (Sec. "Cloud architecture")
+// serves several clients from one application instance; here many render requests of mixed
 // volumes, transfer functions, cameras and image sizes share one persistent launch.
 //
 // The host appends requests to a FIFO in device memory (a slot record holding the request's

@@ -1,8 +1,8 @@
 """Serving render requests: continuous batching on one persistent launch, against one plain
 launch per request, under an open-loop Poisson arrival process.
 
-The paper's server lets "multiple clients use one application" (Sec. "Cloud architecture",
-SaaS model). Here a request names a resident volume, a transfer function, a camera and an
+The paper's SaaS server (Sec. "Cloud architecture") serves several clients from one
+application instance. Here a request names a resident volume, a transfer function, a camera and an
 image size. Admission is by an HBM budget for output images (volumes, brick tables and
 occupancy stay resident); admitted requests go to
 
