@@ -134,6 +134,18 @@ def dist_init(args):
     return rank, world, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest `value` over all ranks of the default process group (the value itself
+    without one): the timed region of a replicated run ends when its slowest rank ends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_sample(vol, tf, cams, rows_every: int, brick: int):
     """Times the oracle on rows 0, k, 2k, ... of the first camera; returns (seconds,
     executed samples, rays, threads)."""
@@ -317,11 +329,7 @@ def main():
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     frame_ms = [a.elapsed_time(b) for fr in frame_ev for a, b in fr]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     secs = total_ms / 1e3
     value = world * executed * args.steps / secs / 1e9
 
@@ -342,11 +350,7 @@ def main():
             for i, cam in enumerate(cams):
                 R.render_host(vid, tid, cam, ert=0.999, brick=B, out=host[i], kernel=args.kernel)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": world * executed * args.steps / e2e_s / 1e9, "unit": "Gsamples/s",
                "h2d_bytes_per_step": args.cameras * 60,  # vrc_camera records passed by value
                "d2h_bytes_per_step": args.cameras * 1024 * 1024 * 16,
