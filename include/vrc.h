@@ -81,8 +81,10 @@ typedef struct {
  *                  to brick = 0).
  *   seg_len        adjoint checkpoint interval in samples (0 = default 64).
  *   kernel         0 = automatic (one ray per thread), 1 = one ray per thread,
- *                  2 = warp-cooperative (one ray per warp, 32 samples per step). Both
- *                  kernels compute the same method; images agree within float rounding. */
+ *                  2..5 = lane groups: one ray per 32 (2), 4 (3), 8 (4) or 16 (5) lanes,
+ *                  each group taking that many consecutive samples per step. All kernels
+ *                  compute the same method; images agree within float rounding of the
+ *                  compositing order. Other values: VRC_ERR_ARG. */
 typedef struct {
     float step;
     float ert_threshold;
@@ -194,7 +196,7 @@ vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **server_ou
  * aligned, untouched by the caller until completion). Returns a ticket for vrc_server_poll.
  * Brick tables for params->brick must exist; the first request of a (volume, transfer
  * function, brick size) builds its occupancy. VRC_ERR_BUSY when max_slots are in flight.
- * params->kernel 2 is not served (the per-ray body is used). */
+ * params->kernel 2..5 is rejected (VRC_ERR_ARG): the server renders with the per-ray body. */
 vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id, const vrc_camera *cam,
                              const vrc_params *params, float *out_rgba_dev, long long *ticket);
 /* Launches the persistent kernel if it is not running and requests are pending; *running

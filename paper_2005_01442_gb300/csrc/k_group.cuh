@@ -1,0 +1,126 @@
+// Marching one ray with a group of G lanes (G = 4, 8, 16 or 32), shared by the lane-group
+// kernels (k_render_warp.cu) and the second phase of the split render (k_render_split.cu).
+//
+// The ray is walked in blocks of G consecutive sample indices, lane q of the group taking
+// sample G k + q. Every lane places its sample exactly from the double-float ray record,
+// resamples the uniform cubic B-spline from the x-replicated float4 volume, classifies it
+// through the transfer function and corrects its opacity to the segment length (paper, Sec.
+// "Methodology": cubic interpolation, post-classification). The block is composited front to
+// back by a group-wide inclusive scan of the "over" operator
+// (C_a, T_a) o (C_b, T_b) = (C_a + T_a C_b, T_a T_b) on (alpha rgb, 1 - alpha) and prepended by
+// what the ray has accumulated so far; early ray termination picks the first lane whose
+// accumulated opacity exceeds the threshold (ballot). Samples known to lie in empty bricks
+// enter the scan as the identity (0, 1), which is exactly what computing them gives (their
+// opacity is exactly zero), so the result is bit-identical with and without leaping. Between
+// blocks the group leaps over empty space (Sec. "Analysis", Pros (b)).
+#pragma once
+
+#include "vrc_internal.h"
+
+namespace vrc {
+
+// From sample j, the first sample whose exact position lies in an occupied brick (or nseg).
+// Deterministic in its inputs, so every lane of a group gets the same answer.
+__device__ __forceinline__ int advance_to_occupied(const RayPos &rp, const RenderLaunch &L,
+                                                   const uint8_t *__restrict__ dist,
+                                                   const float Pf[3], const float df[3],
+                                                   const float inv_df[3], float inv_step, int j) {
+    const float step = L.grid.step;
+    int cache_lin = -1, cache_r = 0;
+    while (j < rp.nseg) {
+        const int jn = leap_float(L.bricks, dist, Pf, df, inv_df, step, inv_step, rp.nseg, j,
+                                  cache_lin, cache_r);
+        if (jn != j) {
+            j = jn;
+            continue;
+        }
+        float delta;
+        int ip[3];
+        float f[3];
+        place(rp, step, L.grid.n, j, ip, f, delta);
+        if (dist[brick_of(L.bricks, ip)] == 0) return j;
+        ++j;
+    }
+    return rp.nseg;
+}
+
+// Lane q of a group of G lanes (mask gmask, first lane gbase) marches the ray from sample jlo
+// on, compositing onto (RC, RT); on return RC and RT are the ray's colour and transmittance,
+// equal in every lane of the group. `executed` grows by the samples composited (counted in
+// every lane; callers count it once per group).
+template <bool ESL, int G>
+__device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos &rp,
+                                            const uint8_t *__restrict__ dist, const float Pf[3],
+                                            const float df[3], const float inv_df[3],
+                                            float inv_step, int jlo, unsigned gmask, int q,
+                                            int gbase, float &RC0, float &RC1, float &RC2,
+                                            float &RT, unsigned long long &executed) {
+    constexpr int SH = G == 32 ? 5 : G == 16 ? 4 : G == 8 ? 3 : 2;
+    constexpr unsigned low = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    const float step = L.grid.step, thr = L.grid.ert;
+    int blk = jlo >> SH;
+    while (blk * G < rp.nseg) {
+        const int j = blk * G + q;
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, eT = 1.0f;  // identity of "over"
+        bool live = j >= jlo && j < rp.nseg;
+        if (live) {
+            float delta;
+            int ip[3];
+            float f[3];
+            place(rp, step, L.grid.n, j, ip, f, delta);
+            if (ESL && dist[brick_of(L.bricks, ip)] != 0) live = false;
+            if (live) {
+                const float s = tricubic_rep(L.rep, ip, f);
+                const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
+                int i0;
+                floor_small(u, i0);
+                i0 = min(i0, 254);
+                const float fu = u - (float)i0;
+                const float4 c0 = __ldg(L.tf.rgba + i0), dc = __ldg(L.tf.drgba + i0);
+                const float alpha = segment_alpha(fmaf(fu, dc.w, c0.w), delta);
+                e0 = alpha * fmaf(fu, dc.x, c0.x);
+                e1 = alpha * fmaf(fu, dc.y, c0.y);
+                e2 = alpha * fmaf(fu, dc.z, c0.z);
+                eT = 1.0f - alpha;
+            }
+        }
+        // inclusive scan of "over" across the group's block
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const float p0 = __shfl_up_sync(gmask, e0, o, G);
+            const float p1 = __shfl_up_sync(gmask, e1, o, G);
+            const float p2 = __shfl_up_sync(gmask, e2, o, G);
+            const float pT = __shfl_up_sync(gmask, eT, o, G);
+            if (q >= o) {
+                e0 = fmaf(pT, e0, p0);
+                e1 = fmaf(pT, e1, p1);
+                e2 = fmaf(pT, e2, p2);
+                eT = pT * eT;
+            }
+        }
+        // prepend what the ray has accumulated before this block
+        const float t0 = fmaf(RT, e0, RC0), t1 = fmaf(RT, e1, RC1), t2 = fmaf(RT, e2, RC2);
+        const float tT = RT * eT;
+        const unsigned live_bits = (__ballot_sync(gmask, live) >> gbase) & low;
+        const unsigned stop_bits = (__ballot_sync(gmask, live && (1.0f - tT > thr)) >> gbase) & low;
+        const int last = stop_bits ? __ffs(stop_bits) - 1 : G - 1;
+        executed += __popc(live_bits & (0xffffffffu >> (31 - last)));
+        RC0 = __shfl_sync(gmask, t0, last, G);
+        RC1 = __shfl_sync(gmask, t1, last, G);
+        RC2 = __shfl_sync(gmask, t2, last, G);
+        RT = __shfl_sync(gmask, tT, last, G);
+        if (stop_bits) break;
+        ++blk;
+        // leap from the next block's first sample (uniform across the group) unless the block
+        // ended inside an occupied brick
+        const bool tail_live = (live_bits >> (G - 1)) & 1u;
+        if (ESL && !tail_live && blk * G < rp.nseg) {
+            jlo = advance_to_occupied(rp, L, dist, Pf, df, inv_df, inv_step, blk * G);
+            blk = jlo >> SH;
+        } else {
+            jlo = blk * G;
+        }
+    }
+}
+
+}  // namespace vrc

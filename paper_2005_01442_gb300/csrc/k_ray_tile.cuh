@@ -24,7 +24,14 @@ __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by,
 
 // Renders the 8 x 4 pixel tile `tile` (raster order over the image) of launch L with the
 // calling warp (all 32 lanes must call it together).
-template <bool ESL>
+//
+// SPLIT (first phase of the split render, k_render_split.cu): a ray that has composited
+// SPLIT_K0 samples of non-zero opacity and is still running stops at the first sample index
+// that is a multiple of SPLIT_G after that point and is queued in L.split with its colour and
+// transmittance so far; the second phase finishes it with SPLIT_G lanes. The hand-over index
+// depends only on the ray's own non-zero samples, which are the same with and without leaping,
+// so the split image is also identical with and without leaping.
+template <bool ESL, bool SPLIT = false>
 __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile) {
     const int lane = threadIdx.x & 31;
     const int tiles_x = (L.cam.width + 7) >> 3;
@@ -62,7 +69,10 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     int run_lin = -1, run_empty = 0;    // dist cache of the exact path
     bool in_run = !ESL;                 // exact placement mode (vs leap mode)
     bool done = ray.nseg == 0;
+    bool queued = false;
     int j = 0;
+    int npos = 0;           // samples of non-zero opacity composited (SPLIT)
+    int jsw = 0x7fffffff;   // hand-over index once npos reaches SPLIT_K0 (SPLIT)
     while (true) {
         // advance this lane to its next sample to composite
         int ip[3];
@@ -98,6 +108,28 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             }
             break;
         }
+        if (SPLIT) {
+            // hand long rays over to the second phase (warp-aggregated queue append)
+            const bool push = !done && j >= jsw;
+            const unsigned pm = __ballot_sync(0xffffffffu, push);
+            if (pm) {
+                const int leader = __ffs(pm) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(&L.split.head[0], (unsigned)__popc(pm));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (push) {
+                    const unsigned idx = base + __popc(pm & ((1u << lane) - 1u));
+                    if (idx < L.split.cap) {  // at most one record per pixel: always true
+                        L.split.rec_pj[idx] = make_int2(py * L.cam.width + px, j);
+                        L.split.rec_ct[idx] = make_float4(C0, C1, C2, Tr);
+                        done = true;
+                        queued = true;
+                    } else {
+                        atomicExch(L.err, VRC_ERR_DEVICE);
+                    }
+                }
+            }
+        }
         if (__all_sync(0xffffffffu, done)) break;
         if (!done) {
             const float s = tricubic_rep(rep, ip, f);
@@ -110,6 +142,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             const float4 c0 = __ldg(tf_rgba + i0), dc = __ldg(tf_drgba + i0);
             const float a = fmaf(fu, dc.w, c0.w);
             const float alpha = segment_alpha(a, delta);
+            if (SPLIT && alpha > 0.0f && ++npos == SPLIT_K0) jsw = (j / SPLIT_G + 1) * SPLIT_G;
             const float w = Tr * alpha;
             C0 = fmaf(w, fmaf(fu, dc.x, c0.x), C0);
             C1 = fmaf(w, fmaf(fu, dc.y, c0.y), C1);
@@ -120,7 +153,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             ++j;
         }
     }
-    if (valid) L.out[(long)py * L.cam.width + px] = make_float4(C0, C1, C2, 1.0f - Tr);
+    if (valid && !queued) L.out[(long)py * L.cam.width + px] = make_float4(C0, C1, C2, 1.0f - Tr);
 
     if (L.counters) {
         unsigned int nom = (unsigned)ray.nseg, ex = (unsigned)executed;

@@ -1,0 +1,109 @@
+// Split render (params.kernel 0 and 6): two launches that bound the cost any one warp carries.
+//
+// One warp per 8 x 4 pixel tile is the cheapest way to march the many short rays of a CT view
+// (air, rays that stop at a bone surface), but the rays through low-opacity tissue run for
+// hundreds of samples; a tile full of them keeps its warp busy for the whole frame while the
+// rest of the device idles. So:
+//
+// 1. the per-ray body (k_ray_tile.cuh, SPLIT) renders every ray with one lane and finishes
+//    the short ones; a ray still running after SPLIT_K0 samples of non-zero opacity stops at
+//    the next sample index that is a multiple of SPLIT_G and is appended to a queue with its
+//    colour and transmittance so far;
+// 2. a grid sized to fill the device drains the queue, each group of SPLIT_G lanes claiming
+//    one ray at a time and finishing it with group_march (k_group.cuh): blocks of SPLIT_G
+//    consecutive samples composited by a scan of the "over" operator.
+//
+// Each ray is composited in the same order whatever the other rays do, and with the same
+// result with and without leaping (the hand-over point depends only on the ray's own
+// non-zero samples; skipped samples are exact identities in both phases).
+#include "k_group.cuh"
+#include "k_ray_tile.cuh"
+
+namespace vrc {
+
+constexpr int SPLIT_RAY_WARPS = 2;  // warps per CTA of the first phase
+constexpr int SPLIT_WARPS = 8;      // warps per CTA of the second phase
+
+template <bool ESL>
+__global__ void __launch_bounds__(32 * SPLIT_RAY_WARPS, 16 / SPLIT_RAY_WARPS)
+    split_head_kernel(RenderLaunch L) {
+    render_ray_tile<ESL, true>(L, blockIdx.x * SPLIT_RAY_WARPS + (threadIdx.x >> 5));
+}
+
+template <bool ESL>
+__global__ void __launch_bounds__(32 * SPLIT_WARPS, 2) split_tail_kernel(RenderLaunch L) {
+    constexpr int G = SPLIT_G;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (G - 1);       // lane within the group
+    const int gbase = lane & ~(G - 1);  // first lane of the group
+    const unsigned gmask = ((1u << G) - 1u) << gbase;
+    const float step = L.grid.step;
+    const float inv_step = 1.0f / step;
+    const long nbricks = ESL ? (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2] : 0;
+    const unsigned total = min(__ldcg(&L.split.head[0]), L.split.cap);  // final: first phase done
+    unsigned long long executed = 0;
+    while (true) {
+        unsigned qi = 0;
+        if (q == 0) qi = atomicAdd(&L.split.head[1], 1u);
+        qi = __shfl_sync(gmask, qi, 0, G);
+        if (qi >= total) break;
+        const int2 pj = __ldcg(&L.split.rec_pj[qi]);
+        const float4 ct = __ldcg(&L.split.rec_ct[qi]);
+        const int pix = pj.x;
+        // the same ray record as the first phase (same code, same inputs)
+        RaySetup ray;
+        ray_setup(L.cam, L.grid, pix % L.cam.width, pix / L.cam.width, ray);
+        RayPos rp;
+        ray_pos_init(ray, step, rp);
+        float Pf[3], df[3], inv_df[3];
+        ray_float(rp, Pf, df, inv_df);
+        const uint8_t *dist = nullptr;
+        if (ESL) dist = L.dist + octant_of(df) * nbricks;
+        float RC0 = ct.x, RC1 = ct.y, RC2 = ct.z, RT = ct.w;
+        group_march<ESL, G>(L, rp, dist, Pf, df, inv_df, inv_step, pj.y, gmask, q, gbase, RC0,
+                            RC1, RC2, RT, executed);
+        if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
+    }
+    if (L.counters) {
+        unsigned ex = q == 0 ? (unsigned)executed : 0u;
+        ex = __reduce_add_sync(0xffffffffu, ex);
+        if (lane == 0 && ex) atomicAdd(&L.counters[1], (unsigned long long)ex);
+    }
+}
+
+namespace {
+int tail_ctas(cudaError_t &e) {
+    static int cached[64] = {0};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_tail_kernel<true>,
+                                                      32 * SPLIT_WARPS, 0);
+    if (e != cudaSuccess) return 0;
+    const int n = sms * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < 64) cached[dev] = n;
+    return n;
+}
+}  // namespace
+
+cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    const int ctas = tail_ctas(e);
+    if (e != cudaSuccess) return e;
+    const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
+    const unsigned grid = (unsigned)((tiles + SPLIT_RAY_WARPS - 1) / SPLIT_RAY_WARPS);
+    if (L.dist) {
+        split_head_kernel<true><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+        split_tail_kernel<true><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+    } else {
+        split_head_kernel<false><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+        split_tail_kernel<false><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vrc

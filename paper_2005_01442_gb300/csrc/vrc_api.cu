@@ -55,6 +55,17 @@ struct Tf {
 
 int slot_of(int B) { return B == 16 ? 1 : 0; }
 
+// lanes per ray of the group kernel for params.kernel 2..5
+int lanes_of(int kernel) { return kernel == 3 ? 4 : kernel == 4 ? 8 : kernel == 5 ? 16 : 32; }
+
+// Queue of the split render, one per stream that renders with it (renders on one stream run
+// in order, so they can share it): a 256-byte header (pushed, claimed counts), then `cap`
+// (pixel, sample) records and `cap` (colour, transmittance) records.
+struct SplitBuf {
+    unsigned char *base = nullptr;
+    size_t cap = 0;
+};
+
 }  // namespace
 
 struct vrc_ctx {
@@ -66,6 +77,7 @@ struct vrc_ctx {
     int *err_word = nullptr;   // device error word shared by kernels
     float4 *host_img = nullptr;  // device image for vrc_render_host
     size_t host_img_bytes = 0;
+    std::map<cudaStream_t, SplitBuf> split;  // split-render queues by stream
     unsigned tf_version_counter = 0;
 };
 
@@ -304,7 +316,7 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     if (isnan(p->ert_threshold)) return fail(ctx, VRC_ERR_ARG, "ert_threshold is NaN");
     if (p->brick != 0 && p->brick != 8 && p->brick != 16)
         return fail(ctx, VRC_ERR_ARG, "brick must be 0, 8 or 16");
-    if (p->kernel < 0 || p->kernel > 2) return fail(ctx, VRC_ERR_ARG, "kernel must be 0, 1 or 2");
+    if (p->kernel < 0 || p->kernel > 6) return fail(ctx, VRC_ERR_ARG, "kernel must be 0..6");
     memset(&L, 0, sizeof(L));
     vrc_status s = build_camera(ctx, cam, L.cam);
     if (s != VRC_OK) return s;
@@ -329,6 +341,43 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
         for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b.nb[k];
         L.bricks.mn = b.mn;
         L.bricks.mx = b.mx;
+    }
+    return VRC_OK;
+}
+
+// The queue of the split render on stream st, grown to hold `need` records.
+vrc_status split_queue(vrc_ctx *ctx, cudaStream_t st, size_t need, RaySplit &q) {
+    SplitBuf &b = ctx->split[st];
+    if (b.cap < need) {
+        CK(cudaStreamSynchronize(st), "sync before queue realloc");
+        cudaFree(b.base);
+        b.base = nullptr;
+        b.cap = 0;
+        const size_t bytes = 256 + ((need * sizeof(int2) + 255) & ~(size_t)255) + need * sizeof(float4);
+        CK(cudaMalloc(&b.base, bytes), "cudaMalloc(split queue)");
+        b.cap = need;
+    }
+    q.head = (unsigned *)b.base;
+    q.rec_pj = (int2 *)(b.base + 256);
+    q.rec_ct = (float4 *)(b.base + 256 + ((b.cap * sizeof(int2) + 255) & ~(size_t)255));
+    q.cap = (unsigned)b.cap;
+    return VRC_OK;
+}
+
+// Launches the render kernel params->kernel selects (0 and 6: split render; 1: per-ray;
+// 2..5: lane groups). allow_split = false renders kernel 0 with the per-ray kernel.
+vrc_status launch_render(vrc_ctx *ctx, const vrc_params *params, RenderLaunch &L,
+                         cudaStream_t st, bool allow_split = true) {
+    const int k = params->kernel;
+    if ((k == 0 && allow_split) || k == 6) {
+        vrc_status s = split_queue(ctx, st, (size_t)L.cam.width * L.cam.height, L.split);
+        if (s != VRC_OK) return s;
+        CK(cudaMemsetAsync(L.split.head, 0, 2 * sizeof(unsigned), st), "split queue reset");
+        CK(launch_render_split(L, st), "render launch");
+    } else if (k >= 2 && k <= 5) {
+        CK(launch_render_warp(L, lanes_of(k), st), "render launch");
+    } else {
+        CK(launch_render_ray(L, st), "render launch");
     }
     return VRC_OK;
 }
@@ -382,6 +431,7 @@ vrc_status vrc_destroy(vrc_ctx *ctx) {
     for (auto &kv : ctx->tfs) free_tf(kv.second);
     cudaFree(ctx->err_word);
     cudaFree(ctx->host_img);
+    for (auto &kv : ctx->split) cudaFree(kv.second.base);
     delete ctx;
     return VRC_OK;
 }
@@ -628,8 +678,7 @@ vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam
     if (s != VRC_OK) return s;
     L.out = (float4 *)out_rgba_dev;
     L.counters = counters_dev;
-    CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
-    return VRC_OK;
+    return launch_render(ctx, params, L, st);
 }
 
 vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
@@ -655,7 +704,8 @@ vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera
     if (s != VRC_OK) return s;
     L.out = ctx->host_img;
     L.counters = nullptr;
-    CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
+    s = launch_render(ctx, params, L, st);
+    if (s != VRC_OK) return s;
     CK(cudaMemcpyAsync(out_rgba_host, ctx->host_img, bytes, cudaMemcpyDeviceToHost, st),
        "image copy");
     CK(cudaStreamSynchronize(st), "image copy sync");
@@ -810,8 +860,10 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     }
     L.out = (float4 *)out_rgba_dev;
     L.counters = counters_dev;
-    CK(params->kernel == 2 ? launch_render_warp(L, st) : launch_render_ray(L, st), "render launch");
-    return VRC_OK;
+    // no queue here (it would need device memory): kernel 0 renders with the per-ray kernel
+    if (params->kernel == 6)
+        return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not run the split render (kernel 6)");
+    return launch_render(ctx, params, L, st, false);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -916,7 +968,7 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     if (!ticket) return fail(ctx, VRC_ERR_ARG, "ticket is NULL");
     if (!out_rgba_dev || ((uintptr_t)out_rgba_dev & 15) != 0)
         return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be a 16-byte aligned device pointer");
-    if (params && params->kernel == 2)
+    if (params && params->kernel >= 2)
         return fail(ctx, VRC_ERR_ARG, "the server renders with the per-ray kernel (kernel 0 or 1)");
     DeviceGuard g(ctx->device);
     const int slot = (int)(s->next_seq % s->max_slots);

@@ -6,6 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "vrc.h"
 #include "vrc_device.cuh"
 
 namespace vrc {
@@ -145,6 +146,19 @@ __device__ __forceinline__ int octant_of(const float df[3]) {
     return (df[0] < 0.0f) | ((df[1] < 0.0f) << 1) | ((df[2] < 0.0f) << 2);
 }
 
+// Split render (k_render_split.cu): the first phase renders every ray with one lane and hands
+// rays that are still running after SPLIT_K0 samples of non-zero opacity to a queue; the second
+// phase finishes each queued ray with SPLIT_G lanes (blocks of SPLIT_G consecutive samples
+// composited by a scan), so no ray's cost rests on one lane.
+constexpr int SPLIT_K0 = 32;
+constexpr int SPLIT_G = 8;
+struct RaySplit {
+    unsigned *head;  // NULL: no split; else [records pushed, records claimed by the second phase]
+    int2 *rec_pj;    // (linear pixel, first sample index left)
+    float4 *rec_ct;  // (colour so far, transmittance so far)
+    unsigned cap;    // records the queue holds (>= the image's pixels)
+};
+
 struct RenderLaunch {
     VolView vol;
     ReplView rep;
@@ -156,6 +170,7 @@ struct RenderLaunch {
     float4 *out;
     unsigned long long *counters;  // NULL or [nominal, executed]
     int *err;                      // device error word
+    RaySplit split;                // used by the split render only
 };
 
 // Launchers (return cudaSuccess or the launch error).
@@ -172,7 +187,9 @@ size_t box_dist_scratch_bytes(const int nb[3]);
 cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,
                              cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
-cudaError_t launch_render_warp(const RenderLaunch &L, cudaStream_t st);
+cudaError_t launch_render_warp(const RenderLaunch &L, int lanes_per_ray, cudaStream_t st);
+// Both phases of the split render; L.split.head must be zero (it is left nonzero).
+cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st);
 
 // Reverse mode of one render: grad_out is the loss gradient per pixel (H x W x RGBA);
 // grad_tf (256 x 4) and grad_vol (nx*ny*nz, x fastest, may be NULL) are accumulated.

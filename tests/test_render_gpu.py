@@ -88,7 +88,7 @@ def test_occupancy_bit_exact(R, orc, B):
 
 # ------------------------------------------------------------- a3-a9: images vs the oracle
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_phantom_orthographic_parity(R, orc, torch, kernel):
     """64^3 uint16 phantom, 128^2 orthographic along +z, step 0.5, no skipping."""
     vol = synth.phantom()
@@ -105,7 +105,7 @@ def test_phantom_orthographic_parity(R, orc, torch, kernel):
     R.free_tf(tid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("B", [0, 8, 16])
 @pytest.mark.parametrize("ert", [1.0, 0.999])
 def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
@@ -127,7 +127,7 @@ def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
     R.free_tf(tid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_empty_space_leaping_bit_identical(R, torch, kernel):
     vol = _ct_small(seed=5)
     vid = R.upload_volume(vol)
@@ -163,7 +163,7 @@ def test_early_termination_bound(R, torch):
     R.free_volume(vid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_float_volume_and_ragged_sizes(R, orc, kernel):
     rng = np.random.default_rng(9)
     vol = (rng.normal(0, 1, (13, 17, 19)).cumsum(0) * 40).astype(np.float32)
@@ -182,7 +182,7 @@ def test_float_volume_and_ragged_sizes(R, orc, kernel):
     R.free_volume(vid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_degenerate_cases(R, orc, kernel):
     tf = synth.tf_random(3)
     # 1x1x1 volume, 1x1 image, step longer than the box
@@ -254,7 +254,7 @@ def ct_full(R):
     R.free_tf(tid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("B", [8, 16])
 def test_ct_full_size_sampled_parity(R, orc, torch, ct_full, B, kernel):
     """512^2 x 400 CT, 1024^2 perspective, step 0.5, ESL, ERT 0.999: 4096 sampled pixels per
@@ -273,13 +273,77 @@ def test_ct_full_size_sampled_parity(R, orc, torch, ct_full, B, kernel):
 
 
 def test_kernels_agree(R, torch, ct_full):
-    """The per-ray and the warp-cooperative kernels compute the same image up to float
-    rounding of the compositing order."""
+    """The per-ray and the lane-group kernels compute the same image up to float rounding of
+    the compositing order."""
     vol, vid, tid = ct_full
     for cam in synth.orbit_cameras(7, 2, synth.dims_of(vol), 512, 512):
         a = R.render(vid, tid, cam, ert=0.999, brick=8, kernel=1)
-        b = R.render(vid, tid, cam, ert=0.999, brick=8, kernel=2)
-        d = (a - b).abs()
-        # pixels whose termination is decided within float rounding may differ by <= 1e-3
-        assert float(d.max()) <= 1e-3
-        assert float((d > 1e-5).float().mean()) < 1e-3
+        for k in (2, 3, 4, 5, 6):
+            b = R.render(vid, tid, cam, ert=0.999, brick=8, kernel=k)
+            d = (a - b).abs()
+            # pixels whose termination is decided within float rounding may differ by <= 1e-3
+            assert float(d.max()) <= 1e-3, k
+            assert float((d > 1e-5).float().mean()) < 1e-3, k
+
+
+# ------------------------------------------- split render: the second phase and its queue
+
+def _glass_tf(alpha):
+    """Every value has the same small opacity: rays never terminate early and every sample
+    has non-zero opacity, so every ray longer than the hand-over point is queued."""
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, 0] = np.linspace(0.2, 1.0, 256)
+    tf[:, 1] = np.linspace(1.0, 0.3, 256)
+    tf[:, 2] = 0.5
+    tf[:, 3] = alpha
+    return tf
+
+
+@pytest.mark.parametrize("B", [0, 8])
+def test_split_long_rays_parity_and_sample_count(R, orc, torch, B):
+    """All rays long: phase two renders nearly every pixel. Images match the oracle and the
+    sample counter shows every sample composited exactly once across the two phases."""
+    vol = _ct_small(seed=5, shape=(40, 44, 36))
+    tf = _glass_tf(0.02)
+    vid = R.upload_volume(vol)
+    if B:
+        R.build_bricks(vid, B)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    for cam in (synth.ortho_z_camera(synth.dims_of(vol), 37, 29),
+                synth.orbit_cameras(9, 1, synth.dims_of(vol), 45, 38)[0]):
+        ref, (onom, _) = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=1.0,
+                                    return_counts=True)
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        img = R.render(vid, tid, cam, step=0.5, ert=1.0, brick=B, counters=cnt, kernel=6)
+        _check(img.cpu().numpy(), ref)
+        nominal, executed = cnt.tolist()
+        assert nominal == onom
+        if B == 0:
+            assert executed == nominal
+        one = R.render(vid, tid, cam, step=0.5, ert=1.0, brick=B, kernel=1)
+        assert float((img - one).abs().max()) <= 1e-5
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+def test_split_queue_grows_and_streams_are_independent(R, torch):
+    """A larger image grows the queue; renders on two streams use separate queues and give
+    the same images as on the default stream."""
+    vol = _ct_small(seed=6)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(_glass_tf(0.01), synth.CT_LO, synth.CT_HI)
+    cams = [synth.orbit_cameras(11, 1, synth.dims_of(vol), w, h)[0]
+            for w, h in ((24, 16), (96, 80), (130, 70))]
+    ref = [R.render(vid, tid, c, ert=0.999, brick=8, kernel=6).clone() for c in cams]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for k in range(3):
+        for i, c in enumerate(cams):
+            outs.append((i, R.render(vid, tid, c, ert=0.999, brick=8, kernel=6,
+                                     stream=s1 if (i + k) % 2 else s2)))
+    torch.cuda.synchronize()
+    for i, img in outs:
+        assert torch.equal(img, ref[i])
+    R.free_tf(tid)
+    R.free_volume(vid)
