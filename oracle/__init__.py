@@ -69,6 +69,7 @@ def lib():
         L.orc_ray.restype = C.c_int
         L.orc_bricks.argtypes = [vp, ip, ip, ip, ip, ip, vp, vp]
         L.orc_occupancy.argtypes = [vp, vp, ip, C.c_long, vp, C.c_float, C.c_float, vp]
+        L.orc_cellmask.argtypes = [vp, ip, ip, ip, ip, vp, C.c_float, C.c_float, vp]
         L.orc_render.argtypes = [vp, ip, ip, ip, ip, vp, C.c_double, C.c_double,
                                  C.POINTER(Camera), C.POINTER(Params), vp, C.POINTER(Ball), vp,
                                  C.c_long, vp, vp, vp, vp]
@@ -166,6 +167,20 @@ def occupancy(mn: np.ndarray, mx: np.ndarray, tf: np.ndarray, lo: float, hi: flo
     if rc != 0:
         raise ValueError(f"orc_occupancy failed ({rc})")
     return occ
+
+
+def cellmask(vol: np.ndarray, tf: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    """Cell transparency bytes, shape (nz+1, ny+1, nx+1): entry [c2+1, c1+1, c0+1] is 0 when
+    every sample with floor(p) = (c0, c1, c2) has alpha == 0 (see orc_cellmask)."""
+    vol = np.ascontiguousarray(vol)
+    tf = np.ascontiguousarray(tf, np.float32)
+    nz, ny, nx = vol.shape
+    out = np.empty((nz + 1, ny + 1, nx + 1), np.uint8)
+    rc = lib().orc_cellmask(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
+                            float(hi), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_cellmask failed ({rc})")
+    return out
 
 
 def _pix(pixels):

@@ -352,6 +352,42 @@ int orc_occupancy(const void *mn, const void *mx, int dtype, long nbricks, const
     return ORC_OK;
 }
 
+/* Cell transparency mask. Cell c (per axis c = -1 .. n-1, stored at index c + 1, x fastest)
+ * holds the sample points p with floor(p) = c; their cubic taps are the voxels c-1 .. c+2,
+ * clamped to the volume. The B-spline weights are non-negative and sum to one, so every such
+ * sample lies between the minimum and maximum of those 64 taps; the cell's byte is the brick
+ * occupancy rule applied to that range (1 when any TF alpha > 0 on
+ * [floor(u(min))-1, ceil(u(max))+1]). A sample in a cell of byte 0 has alpha == 0 exactly. */
+int orc_cellmask(const void *data, int dtype, int nx, int ny, int nz, const float *tf,
+                 float lo, float hi, uint8_t *out) {
+    if (!(hi > lo) || nx <= 0 || ny <= 0 || nz <= 0) return ORC_EARG;
+    orc_volume v = {data, dtype, {nx, ny, nz}};
+    volatile float range = hi - lo;
+    float du = 255.0f / range;
+    long cx = (long)nx + 1, cy = (long)ny + 1, cz = (long)nz + 1;
+#pragma omp parallel for schedule(static)
+    for (long idx = 0; idx < cx * cy * cz; ++idx) {
+        long c0 = idx % cx - 1, c1 = (idx / cx) % cy - 1, c2 = idx / (cx * cy) - 1;
+        double mn = INFINITY, mx = -INFINITY;
+        for (long dz = -1; dz <= 2; ++dz)
+            for (long dy = -1; dy <= 2; ++dy)
+                for (long dx = -1; dx <= 2; ++dx) {
+                    double val = voxel(&v, c0 + dx, c1 + dy, c2 + dz);
+                    if (val < mn) mn = val;
+                    if (val > mx) mx = val;
+                }
+        float ulo = u_f32((float)mn, lo, du), uhi = u_f32((float)mx, lo, du);
+        int k0 = (int)floorf(ulo) - 1, k1 = (int)ceilf(uhi) + 1;
+        if (k0 < 0) k0 = 0;
+        if (k1 > 255) k1 = 255;
+        uint8_t o = 0;
+        for (int k = k0; k <= k1; ++k)
+            if (tf[4 * k + 3] > 0.0f) { o = 1; break; }
+        out[idx] = o;
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ render (a3-a9) ---- */
 
 typedef struct {

@@ -297,6 +297,66 @@ def test_empty_brick_decision_is_conservative_per_value(orc):
             assert mini.tf_lookup(s, tf, 0.0, 4095.0)[3] == 0.0, (v, du)
 
 
+def test_cell_mask_brute_force_and_sampled_alpha(orc):
+    # Cell mask: brute force of the support min/max (taps c-1 .. c+2 clamped, written here
+    # with NumPy edge padding) and the float32 index rule; then sample points in every
+    # transparent cell (and its faces) resampled by the independent NumPy caster have alpha 0.
+    rng = np.random.default_rng(12)
+    vol = np.full((9, 11, 13), -1000, np.int16)                  # air
+    vol[2:8, 1:9, 3:12] = rng.normal(40, 10, (6, 8, 9))           # soft tissue
+    vol[5, 4, 6] = 1200                                           # bone voxel
+    vol[3, 7, 10] = 180                                           # faint, near the 150 HU edge
+    tf = synth.tf_ct()
+    lo, hi = synth.CT_LO, synth.CT_HI
+    m = orc.cellmask(vol, tf, lo, hi)
+    nz, ny, nx = vol.shape
+    assert m.shape == (nz + 1, ny + 1, nx + 1)
+    padded = np.pad(vol.astype(np.float64), 2, mode="edge")  # voxel v at padded index v + 2
+    du = np.float32(255.0) / (np.float32(hi) - np.float32(lo))
+    ref = np.zeros_like(m)
+    for cz in range(-1, nz):
+        for cy in range(-1, ny):
+            for cx in range(-1, nx):
+                box = padded[cz + 1:cz + 5, cy + 1:cy + 5, cx + 1:cx + 5]
+                u0 = np.clip((np.float32(box.min()) - np.float32(lo)) * du, 0, 255)
+                u1 = np.clip((np.float32(box.max()) - np.float32(lo)) * du, 0, 255)
+                k0, k1 = max(int(np.floor(u0)) - 1, 0), min(int(np.ceil(u1)) + 1, 255)
+                ref[cz + 1, cy + 1, cx + 1] = (tf[k0:k1 + 1, 3] > 0).any()
+    assert np.array_equal(m, ref)
+    assert 0 < m.sum() < m.size
+    field = mini.Field(vol)
+    zeros = np.argwhere(m == 0)
+    for cz, cy, cx in zeros[rng.choice(len(zeros), min(len(zeros), 150), replace=False)]:
+        for f in rng.uniform(0, 1, (4, 3)).tolist() + [[0.0, 0.0, 0.0], [0.999, 0.999, 0.999]]:
+            p = (cx - 1 + f[0], cy - 1 + f[1], cz - 1 + f[2])
+            assert mini.tf_lookup(field(p), tf, lo, hi)[3] == 0.0, (cx, cy, cz, f)
+
+
+def test_cell_mask_refines_brick_occupancy(orc):
+    # A cell's taps lie in the apron of the brick holding the cell, so an empty brick holds
+    # only transparent cells; and an isolated opaque voxel marks exactly the 4^3 cells whose
+    # support contains it.
+    vol = synth.ct_volume((24, 20, 28), seed=13)
+    tf = synth.tf_ct()
+    lo, hi = synth.CT_LO, synth.CT_HI
+    m = orc.cellmask(vol, tf, lo, hi)
+    for B in (4, 8):
+        occ = orc.occupancy(*orc.bricks(vol, B), tf, lo, hi)
+        nz, ny, nx = vol.shape
+        for cz in range(-1, nz):
+            for cy in range(-1, ny):
+                for cx in range(-1, nx):
+                    b = (max(cz, 0) // B, max(cy, 0) // B, max(cx, 0) // B)
+                    if occ[b] == 0:
+                        assert m[cz + 1, cy + 1, cx + 1] == 0
+    flat = np.full((10, 10, 10), -1000, np.int16)
+    flat[4, 5, 6] = 1200
+    mf = orc.cellmask(flat, tf, lo, hi)
+    expect = np.zeros_like(mf)
+    expect[4 - 2 + 1:4 + 1 + 1 + 1, 5 - 2 + 1:5 + 1 + 1 + 1, 6 - 2 + 1:6 + 1 + 1 + 1] = 1
+    assert np.array_equal(mf, expect)
+
+
 # --------------------------------------------------------- ESL and ERT invariants (a4, a8)
 
 def _ct_small():
