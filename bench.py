@@ -383,10 +383,14 @@ def main():
             "render_kernel_ms": kernel_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
+                         "kernel": ("one render call: split_head_kernel + split_tail_kernel"
+                                    if args.kernel in (0, 6) else f"render kernel {args.kernel}"),
                          "basis": f"{FLOPS_PER_SAMPLE} flop/executed sample; peak = {sms} SMs x "
                                   f"{FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
             "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * (6 + args.cameras),  # bricks, occupancy, 3 summed-volume passes, distance, frames
+            # bricks, occupancy, 3 summed-volume passes, distance, cell mask; per frame the
+            # split render's two kernels (one for the per-ray kernel)
+            "gpu_launches": args.steps * (7 + args.cameras * (2 if args.kernel in (0, 6) else 1)),
             "clocks": clocks,
         }
         if clocks.get("sm_mhz"):

@@ -80,11 +80,17 @@ typedef struct {
  *                  size (requires vrc_bricks_build for that size; the image is identical
  *                  to brick = 0).
  *   seg_len        adjoint checkpoint interval in samples (0 = default 64).
- *   kernel         0 = automatic (one ray per thread), 1 = one ray per thread,
+ *   kernel         0 = automatic: the split render (6) in vrc_render and vrc_render_host,
+ *                  one ray per thread in vrc_render_noalloc and in the server;
+ *                  1 = one ray per thread;
  *                  2..5 = lane groups: one ray per 32 (2), 4 (3), 8 (4) or 16 (5) lanes,
- *                  each group taking that many consecutive samples per step. All kernels
- *                  compute the same method; images agree within float rounding of the
- *                  compositing order. Other values: VRC_ERR_ARG. */
+ *                  each group taking that many consecutive samples per step;
+ *                  6 = split render: one lane per ray sets the ray up and leaps to its
+ *                  first sample that may be non-zero, then groups of 8 lanes drawn from the
+ *                  whole device finish the queued rays (the context keeps a queue of 112
+ *                  bytes per pixel for each stream it renders on).
+ *                  All kernels compute the same method; images agree within float
+ *                  rounding of the compositing order. Other values: VRC_ERR_ARG. */
 typedef struct {
     float step;
     float ert_threshold;
@@ -149,11 +155,26 @@ vrc_status vrc_occupancy_build(vrc_ctx *ctx, int vol_id, int tf_id, int B, void 
 vrc_status vrc_occupancy_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint8_t *occ_host,
                              void *stream);
 
+/* Copies the cell transparency mask that renders with brick size B use alongside the brick
+ * occupancy (an auxiliary empty-space structure in the sense of Sec. "Analysis", Pros (b), at
+ * the finest grain; the paper names no such table). Cell c per axis (c = -1 .. n-1, index
+ * c' = c + 1) holds the samples whose floor is c; its bit is the occupancy rule above applied
+ * to the min/max of the 64 cubic taps c-1 .. c+2 (clamped), so a sample in a cell of bit 0
+ * has opacity exactly 0 and renders skip it. Layout: uint32 words of 32 cells along x,
+ * word (c'_z * (ny + 1) + c'_y) * ceil((nx + 1) / 32) + c'_x / 32, bit c'_x % 32; bits past
+ * c'_x = nx are unspecified. nwords must equal ceil((nx+1)/32) * (ny+1) * (nz+1), else
+ * VRC_ERR_ARG; B must be 8 or 16 with its brick table built (VRC_ERR_STATE otherwise).
+ * Synchronises `stream`. */
+vrc_status vrc_cellmask_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint32_t *words_host,
+                            long nwords, void *stream);
+
 /* Renders `cam` into out_rgba_dev: height x width x 4 floats (RGBA, row py = 0 on top),
  * colour premultiplied by opacity, black background: (C_r, C_g, C_b, 1 - T).
  * counters_dev: NULL, or 2 caller-owned uint64 that the kernel increments by the number of
- * nominal samples (segments inside the box, summed over rays) and executed samples
- * (samples resampled and composited). Asynchronous on `stream`. */
+ * nominal samples (segments inside the box, summed over rays) and executed samples (samples
+ * up to termination that lie in occupied bricks, or every sample up to termination when
+ * params->brick = 0; those in clear cells are counted though not resampled).
+ * Asynchronous on `stream`. */
 vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                       const vrc_params *params, float *out_rgba_dev,
                       unsigned long long *counters_dev, void *stream);
@@ -196,7 +217,8 @@ vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **server_ou
  * aligned, untouched by the caller until completion). Returns a ticket for vrc_server_poll.
  * Brick tables for params->brick must exist; the first request of a (volume, transfer
  * function, brick size) builds its occupancy. VRC_ERR_BUSY when max_slots are in flight.
- * params->kernel 2..5 is rejected (VRC_ERR_ARG): the server renders with the per-ray body. */
+ * params->kernel 2..6 is rejected (VRC_ERR_ARG): the server renders with the per-ray body
+ * (kernel 0 and 1). */
 vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id, const vrc_camera *cam,
                              const vrc_params *params, float *out_rgba_dev, long long *ticket);
 /* Launches the persistent kernel if it is not running and requests are pending; *running
@@ -220,7 +242,10 @@ vrc_status vrc_server_destroy(vrc_server *s);
  * cudaFree; the volume, its brick table for params->brick (vrc_bricks_build) and the
  * transfer function must already exist. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any stream capture.
- * Arguments, outputs and the image are those of vrc_render (same pixels, bit for bit).
+ * Arguments, outputs and the image are those of vrc_render (same pixels, bit for bit);
+ * the cell transparency mask is rebuilt there too when it fits behind the brick fields,
+ * else samples in transparent cells are resampled (same pixels, more executed samples).
+ * params->kernel 6 (split render) is rejected with VRC_ERR_ARG: its queue needs memory.
  * Returns VRC_ERR_ARG, with a message naming the sizes, when the brick grid needs more than
  * the array holds (about 9 bytes per brick plus a 4-byte summed-volume table entry per
  * brick). All calls share the one array: calls that can overlap on the GPU (other streams,

@@ -25,7 +25,9 @@ class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, volume, tf, dr, cam, step, ert, brick, seg_len):
         dr._load(volume, tf, brick)
-        img = dr.renderer.render(dr.vol_id, dr.tf_id, cam, step=step, ert=ert, brick=brick)
+        # the per-ray kernel: the compositing order the adjoint replays
+        img = dr.renderer.render(dr.vol_id, dr.tf_id, cam, step=step, ert=ert, brick=brick,
+                                 kernel=1)
         ctx.save_for_backward(volume, tf)
         ctx.dr, ctx.cam = dr, cam
         ctx.args = (step, ert, brick, seg_len)

@@ -236,6 +236,142 @@ cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbr
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- cell transparency mask ----
+// Cell c (per axis c = -1 .. n-1, index c' = c + 1) holds the samples with floor(p) = c; their
+// 64 cubic taps are voxels c-1 .. c+2, i.e. padded indices c' .. c'+3. The B-spline weights are
+// non-negative and sum to one, so such a sample lies in [min, max] of the taps (up to float
+// rounding, which the +-1 index margin covers); bit c' of the mask is the occupancy rule on
+// that range, and a sample in a cell of bit 0 has opacity exactly zero. Bits: words of 32
+// cells along x, word (c'_z * (ny + 1) + c'_y) * cwx + c'_x / 32, bit c'_x % 32.
+//
+// One CTA per 32 x 8 cells in x, y and a run of CM_ZC cells in z. It streams the padded z
+// slices: each slice's 35 x 11 values go to shared memory and are reduced over the 4-row y
+// window into a ring of the last 4 slices; once 4 slices are in, each warp reduces one row of
+// cells over the z ring and the 4-column x window, applies the rule and writes one word.
+constexpr int CM_TX = 32, CM_TY = 8, CM_ZC = 32;
+constexpr int CM_HX = CM_TX + 3, CM_HY = CM_TY + 3;
+constexpr int CM_THREADS = 32 * CM_TY;
+
+template <typename T>
+__global__ void __launch_bounds__(CM_THREADS) cellmask_kernel(VolView v,
+                                                               const int *__restrict__ prefix,
+                                                               float lo, float du,
+                                                               uint32_t *__restrict__ cells,
+                                                               int cwx) {
+    __shared__ float s_in[CM_HY][CM_HX];
+    __shared__ float s_mn[4][CM_TY][CM_HX], s_mx[4][CM_TY][CM_HX];
+    __shared__ float s_zmn[CM_TY][CM_HX], s_zmx[CM_TY][CM_HX];
+    __shared__ int pre[257];
+    const int cx0 = blockIdx.x * CM_TX, cy0 = blockIdx.y * CM_TY, cz0 = blockIdx.z * CM_ZC;
+    const int zend = min(cz0 + CM_ZC, v.n[2] + 1);  // cells cz0 .. zend - 1
+    const T *base = (const T *)v.base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 257; i += CM_THREADS) pre[i] = prefix[i];
+    // this thread's two elements of a slice (CM_HY * CM_HX <= 2 * CM_THREADS); cells beyond n
+    // read clamped values, their bits are never used
+    static_assert(CM_HY * CM_HX <= 2 * CM_THREADS, "two slice elements per thread");
+    long off[2];
+    int sy[2], sx[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = min((int)threadIdx.x + e * CM_THREADS, CM_HY * CM_HX - 1);
+        sy[e] = i / CM_HX;
+        sx[e] = i % CM_HX;
+        off[e] = (long)min(cy0 + sy[e], v.pny - 1) * v.pnx + min(cx0 + sx[e], v.pnx - 1);
+    }
+    const long slice = (long)v.pny * v.pnx;
+    static_assert(CM_TY * CM_HX <= 2 * CM_THREADS, "two row-block positions per thread");
+    int ry[2], rx[2];
+    bool ry_ok[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = (int)threadIdx.x + e * CM_THREADS;
+        ry_ok[e] = i < CM_TY * CM_HX;
+        ry[e] = ry_ok[e] ? i / CM_HX : 0;
+        rx[e] = ry_ok[e] ? i % CM_HX : 0;
+    }
+    // padded slice zp holds taps of cells zp - 3 .. zp; the next slice is loaded into
+    // registers while the current one is reduced
+    float nxt[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) nxt[e] = as_f32(base[(long)min(cz0, v.pnz - 1) * slice + off[e]]);
+    for (int zp = cz0; zp < zend + 3; ++zp) {
+        __syncthreads();  // s_in and the ring slot of zp are free
+#pragma unroll
+        for (int e = 0; e < 2; ++e) s_in[sy[e]][sx[e]] = nxt[e];
+        if (zp + 1 < zend + 3) {
+            const long zo = (long)min(zp + 1, v.pnz - 1) * slice;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) nxt[e] = as_f32(base[zo + off[e]]);
+        }
+        __syncthreads();
+        // y window into the ring slot of zp, then (once 4 slices are in) the z window over the
+        // ring; each thread owns the same two (y, x) positions of the 8 x 35 row block
+        const int r = zp & 3;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (!ry_ok[e]) continue;
+            float mn = s_in[ry[e]][rx[e]], mx = mn;
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                mn = fminf(mn, s_in[ry[e] + k][rx[e]]);
+                mx = fmaxf(mx, s_in[ry[e] + k][rx[e]]);
+            }
+            s_mn[r][ry[e]][rx[e]] = mn;
+            s_mx[r][ry[e]][rx[e]] = mx;
+        }
+        if (zp < cz0 + 3) continue;
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (!ry_ok[e]) continue;
+            float mn = s_mn[0][ry[e]][rx[e]], mx = s_mx[0][ry[e]][rx[e]];
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                mn = fminf(mn, s_mn[k][ry[e]][rx[e]]);
+                mx = fmaxf(mx, s_mx[k][ry[e]][rx[e]]);
+            }
+            s_zmn[ry[e]][rx[e]] = mn;
+            s_zmx[ry[e]][rx[e]] = mx;
+        }
+        __syncthreads();
+        const int cz = zp - 3, cy = cy0 + warp;
+        float mn = s_zmn[warp][lane], mx = s_zmx[warp][lane];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            mn = fminf(mn, s_zmn[warp][lane + k]);
+            mx = fmaxf(mx, s_zmx[warp][lane + k]);
+        }
+        const float ulo = u_index(mn, lo, du), uhi = u_index(mx, lo, du);
+        const int k0 = max((int)floorf(ulo) - 1, 0);
+        const int k1 = min((int)ceilf(uhi) + 1, 255);
+        const unsigned w = __ballot_sync(0xffffffffu, (pre[k1 + 1] - pre[k0]) > 0);
+        if (lane == 0 && cy <= v.n[1])
+            cells[((long)cz * (v.n[1] + 1) + cy) * cwx + blockIdx.x] = w;
+    }
+}
+
+long cellmask_words(const int n[3]) {
+    return (long)((n[0] + 1 + 31) / 32) * (n[1] + 1) * (n[2] + 1);
+}
+
+cudaError_t launch_cellmask(const VolView &v, const int *prefix_dev, float lo, float du,
+                            uint32_t *cells, cudaStream_t st) {
+    const int cwx = (v.n[0] + 1 + 31) / 32;
+    const dim3 grid(cwx, (v.n[1] + 1 + CM_TY - 1) / CM_TY, (v.n[2] + 1 + CM_ZC - 1) / CM_ZC);
+    switch (v.dtype) {
+    case DT_U16:
+        cellmask_kernel<uint16_t><<<grid, CM_THREADS, 0, st>>>(v, prefix_dev, lo, du, cells, cwx);
+        break;
+    case DT_I16:
+        cellmask_kernel<int16_t><<<grid, CM_THREADS, 0, st>>>(v, prefix_dev, lo, du, cells, cwx);
+        break;
+    default:
+        cellmask_kernel<float><<<grid, CM_THREADS, 0, st>>>(v, prefix_dev, lo, du, cells, cwx);
+    }
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- empty-box distance (leaping) ----
 // For each of the 8 direction octants s = (sx, sy, sz) in {+1, -1}^3 and each brick b:
 // dist[oct][b] = 0 for an occupied brick, else the smallest r >= 1 such that the forward box

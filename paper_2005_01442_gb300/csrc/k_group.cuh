@@ -9,10 +9,10 @@
 // back by a group-wide inclusive scan of the "over" operator
 // (C_a, T_a) o (C_b, T_b) = (C_a + T_a C_b, T_a T_b) on (alpha rgb, 1 - alpha) and prepended by
 // what the ray has accumulated so far; early ray termination picks the first lane whose
-// accumulated opacity exceeds the threshold (ballot). Samples known to lie in empty bricks
-// enter the scan as the identity (0, 1), which is exactly what computing them gives (their
-// opacity is exactly zero), so the result is bit-identical with and without leaping. Between
-// blocks the group leaps over empty space (Sec. "Analysis", Pros (b)).
+// accumulated opacity exceeds the threshold (ballot). Samples known to have zero opacity (in
+// an empty brick or a transparent cell) enter the scan as the identity (0, 1), which is
+// exactly what computing them gives, so the result is bit-identical with and without
+// skipping. Between blocks the group leaps over empty space (Sec. "Analysis", Pros (b)).
 #pragma once
 
 #include "vrc_internal.h"
@@ -46,8 +46,9 @@ __device__ __forceinline__ int advance_to_occupied(const RayPos &rp, const Rende
 
 // Lane q of a group of G lanes (mask gmask, first lane gbase) marches the ray from sample jlo
 // on, compositing onto (RC, RT); on return RC and RT are the ray's colour and transmittance,
-// equal in every lane of the group. `executed` grows by the samples composited (counted in
-// every lane; callers count it once per group).
+// equal in every lane of the group. `executed` grows by the samples in occupied bricks up to
+// termination, resampled or skipped as clear cells (counted in every lane; callers count it
+// once per group).
 template <bool ESL, int G>
 __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos &rp,
                                             const uint8_t *__restrict__ dist, const float Pf[3],
@@ -63,12 +64,16 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
         const int j = blk * G + q;
         float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, eT = 1.0f;  // identity of "over"
         bool live = j >= jlo && j < rp.nseg;
+        bool in_occ = live;  // sample in range and in an occupied brick
         if (live) {
             float delta;
             int ip[3];
             float f[3];
             place(rp, step, L.grid.n, j, ip, f, delta);
-            if (ESL && dist[brick_of(L.bricks, ip)] != 0) live = false;
+            if (ESL) {
+                in_occ = dist[brick_of(L.bricks, ip)] == 0;
+                live = in_occ && (!L.cells || cell_open(L.cells, L.cwx, L.grid.n, ip));
+            }
             if (live) {
                 const float s = tricubic_rep(L.rep, ip, f);
                 const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
@@ -101,10 +106,10 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
         // prepend what the ray has accumulated before this block
         const float t0 = fmaf(RT, e0, RC0), t1 = fmaf(RT, e1, RC1), t2 = fmaf(RT, e2, RC2);
         const float tT = RT * eT;
-        const unsigned live_bits = (__ballot_sync(gmask, live) >> gbase) & low;
+        const unsigned occ_bits = (__ballot_sync(gmask, in_occ) >> gbase) & low;
         const unsigned stop_bits = (__ballot_sync(gmask, live && (1.0f - tT > thr)) >> gbase) & low;
         const int last = stop_bits ? __ffs(stop_bits) - 1 : G - 1;
-        executed += __popc(live_bits & (0xffffffffu >> (31 - last)));
+        executed += __popc(occ_bits & (0xffffffffu >> (31 - last)));
         RC0 = __shfl_sync(gmask, t0, last, G);
         RC1 = __shfl_sync(gmask, t1, last, G);
         RC2 = __shfl_sync(gmask, t2, last, G);
@@ -113,8 +118,8 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
         ++blk;
         // leap from the next block's first sample (uniform across the group) unless the block
         // ended inside an occupied brick
-        const bool tail_live = (live_bits >> (G - 1)) & 1u;
-        if (ESL && !tail_live && blk * G < rp.nseg) {
+        const bool tail_occ = (occ_bits >> (G - 1)) & 1u;
+        if (ESL && !tail_occ && blk * G < rp.nseg) {
             jlo = advance_to_occupied(rp, L, dist, Pf, df, inv_df, inv_step, blk * G);
             blk = jlo >> SH;
         } else {

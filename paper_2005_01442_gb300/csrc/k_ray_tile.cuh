@@ -8,15 +8,18 @@
 // post-classification through the 256-entry table, opacity corrected to the segment length,
 // front-to-back compositing, early ray termination. With a brick table the ray leaps over
 // boxes of empty bricks ahead of it (Sec. "Analysis", Pros (b): auxiliary structures to skip
-// empty space), using the forward-box distance field of its direction octant. A sample is
-// skipped only when it lies, by a margin of LEAP_MARGIN voxels beyond any rounding of its
-// position, inside an empty brick, where its opacity is exactly zero; the image is therefore
-// identical bit for bit with and without leaping.
+// empty space), using the forward-box distance field of its direction octant, and inside
+// occupied bricks it skips samples whose cell is transparent (cell mask: all 64 taps in a
+// zero-opacity range). A sample is skipped only when its opacity is exactly zero (leaps keep
+// a margin of LEAP_MARGIN voxels beyond any rounding of the position), so the image is
+// identical bit for bit with and without skipping.
 #pragma once
 
 #include "vrc_internal.h"
 
 namespace vrc {
+
+constexpr int SKIP_PER_STEP = 1;  // clear cells a lane may skip per step of its warp
 
 __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by, int bz) {
     return (bz * bv.nb[1] + by) * bv.nb[0] + bx;
@@ -25,12 +28,11 @@ __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by,
 // Renders the 8 x 4 pixel tile `tile` (raster order over the image) of launch L with the
 // calling warp (all 32 lanes must call it together).
 //
-// SPLIT (first phase of the split render, k_render_split.cu): a ray that has composited
-// SPLIT_K0 samples of non-zero opacity and is still running stops at the first sample index
-// that is a multiple of SPLIT_G after that point and is queued in L.split with its colour and
-// transmittance so far; the second phase finishes it with SPLIT_G lanes. The hand-over index
-// depends only on the ray's own non-zero samples, which are the same with and without leaping,
-// so the split image is also identical with and without leaping.
+// SPLIT (first phase of the split render, k_render_split.cu): a ray still running when its
+// next sample to composite has index >= SPLIT_J0 (a multiple of SPLIT_G) is queued in L.split
+// with its colour and transmittance so far; the second phase finishes it with SPLIT_G lanes
+// in blocks aligned to SPLIT_G. Samples between SPLIT_J0 and the queued index have opacity
+// zero, so the split image is also identical with and without skipping.
 template <bool ESL, bool SPLIT = false>
 __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile) {
     const int lane = threadIdx.x & 31;
@@ -46,6 +48,8 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     const ReplView rep = L.rep;
     const int gn[3] = {L.grid.n[0], L.grid.n[1], L.grid.n[2]};
     const float tf_lo = L.tf.lo, tf_du = L.tf.du;
+    const uint32_t *cells = L.cells;
+    const int cwx = L.cwx;
 
     RaySetup ray;
     ray.nseg = 0;
@@ -71,12 +75,15 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     bool done = ray.nseg == 0;
     bool queued = false;
     int j = 0;
-    int npos = 0;           // samples of non-zero opacity composited (SPLIT)
-    int jsw = 0x7fffffff;   // hand-over index once npos reaches SPLIT_K0 (SPLIT)
+    const int jsw = SPLIT ? SPLIT_J0 : 0x7fffffff;  // hand-over index (SPLIT)
     while (true) {
-        // advance this lane to its next sample to composite
+        // advance this lane to its next sample to composite; a lane that has skipped
+        // SKIP_PER_STEP clear cells sits this step out (idle), so that long clear runs of
+        // some lanes do not hold the others
         int ip[3];
         float f[3], delta = 0.0f;
+        bool idle = false;
+        int skips = 0;
         while (!done) {
             if (j >= ray.nseg) {
                 done = true;
@@ -91,8 +98,27 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                 }
                 in_run = true;
             }
+            int qs = QS_EXACT;
+            if (ESL && cells && j < ray.nseg - 1) {
+                qs = quick_skip(bricks, dist, cells, cwx, gn, Pf, df, step, j, run_lin,
+                                run_empty);
+                if (qs == QS_EMPTY_BRICK) {  // opacity zero, back to leaping
+                    ++j;
+                    in_run = false;
+                    continue;
+                }
+                if (qs == QS_CLEAR_CELL) {  // counted as executed: in an occupied brick
+                    ++j;
+                    ++executed;
+                    if (++skips == SKIP_PER_STEP) {
+                        idle = true;
+                        break;
+                    }
+                    continue;
+                }
+            }
             place(rp, step, gn, j, ip, f, delta);
-            if (ESL) {
+            if (ESL && qs == QS_EXACT) {
                 const int lin = brick_linear(bricks, max(ip[0], 0) >> bricks.shift,
                                              max(ip[1], 0) >> bricks.shift,
                                              max(ip[2], 0) >> bricks.shift);
@@ -105,12 +131,21 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                     in_run = false;
                     continue;
                 }
+                if (cells && !cell_open(cells, cwx, gn, ip)) {  // clear cell: opacity 0
+                    ++j;
+                    ++executed;
+                    if (++skips == SKIP_PER_STEP) {
+                        idle = true;
+                        break;
+                    }
+                    continue;
+                }
             }
             break;
         }
         if (SPLIT) {
             // hand long rays over to the second phase (warp-aggregated queue append)
-            const bool push = !done && j >= jsw;
+            const bool push = !done && j >= jsw;  // (an idle lane hands over from j on)
             const unsigned pm = __ballot_sync(0xffffffffu, push);
             if (pm) {
                 const int leader = __ffs(pm) - 1;
@@ -120,8 +155,8 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                 if (push) {
                     const unsigned idx = base + __popc(pm & ((1u << lane) - 1u));
                     if (idx < L.split.cap) {  // at most one record per pixel: always true
-                        L.split.rec_pj[idx] = make_int2(py * L.cam.width + px, j);
-                        L.split.rec_ct[idx] = make_float4(C0, C1, C2, Tr);
+                        split_store(L.split.rec + (long)idx * SPLIT_REC, rp, j,
+                                    py * L.cam.width + px, C0, C1, C2, Tr);
                         done = true;
                         queued = true;
                     } else {
@@ -131,7 +166,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             }
         }
         if (__all_sync(0xffffffffu, done)) break;
-        if (!done) {
+        if (!done && !idle) {
             const float s = tricubic_rep(rep, ip, f);
             // post-classification: u = (s - lo) * du on [0, 255], linear between entries
             const float u = fminf(fmaxf((s - tf_lo) * tf_du, 0.0f), 255.0f);
@@ -142,7 +177,6 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             const float4 c0 = __ldg(tf_rgba + i0), dc = __ldg(tf_drgba + i0);
             const float a = fmaf(fu, dc.w, c0.w);
             const float alpha = segment_alpha(a, delta);
-            if (SPLIT && alpha > 0.0f && ++npos == SPLIT_K0) jsw = (j / SPLIT_G + 1) * SPLIT_G;
             const float w = Tr * alpha;
             C0 = fmaf(w, fmaf(fu, dc.x, c0.x), C0);
             C1 = fmaf(w, fmaf(fu, dc.y, c0.y), C1);

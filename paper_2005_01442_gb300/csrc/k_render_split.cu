@@ -1,21 +1,22 @@
-// Split render (params.kernel 0 and 6): two launches that bound the cost any one warp carries.
+// Split render (params.kernel 6, and 0 in vrc_render): two launches that bound the cost any
+// one warp carries.
 //
-// One warp per 8 x 4 pixel tile is the cheapest way to march the many short rays of a CT view
-// (air, rays that stop at a bone surface), but the rays through low-opacity tissue run for
-// hundreds of samples; a tile full of them keeps its warp busy for the whole frame while the
-// rest of the device idles. So:
+// One warp per 8 x 4 pixel tile renders a CT view's many short rays cheaply (air, rays that
+// stop at a bone surface), but rays through regions of low opacity run for hundreds of
+// samples, and a tile full of them keeps its warp busy for most of the frame while the rest of
+// the device idles. So:
 //
-// 1. the per-ray body (k_ray_tile.cuh, SPLIT) renders every ray with one lane and finishes
-//    the short ones; a ray still running after SPLIT_K0 samples of non-zero opacity stops at
-//    the next sample index that is a multiple of SPLIT_G and is appended to a queue with its
-//    colour and transmittance so far;
+// 1. the per-ray body (k_ray_tile.cuh, SPLIT) sets every ray up with one lane, leaps over
+//    empty bricks and composites samples 0 .. SPLIT_J0 - 1; rays that never reach a sample
+//    that may be non-zero are written out, the others are appended to a queue with their
+//    colour and transmittance so far and the index of that sample;
 // 2. a grid sized to fill the device drains the queue, each group of SPLIT_G lanes claiming
 //    one ray at a time and finishing it with group_march (k_group.cuh): blocks of SPLIT_G
 //    consecutive samples composited by a scan of the "over" operator.
 //
 // Each ray is composited in the same order whatever the other rays do, and with the same
-// result with and without leaping (the hand-over point depends only on the ray's own
-// non-zero samples; skipped samples are exact identities in both phases).
+// result with and without skipping (the hand-over index is fixed and blocks are aligned to
+// SPLIT_G; skipped samples are exact identities in both phases).
 #include "k_group.cuh"
 #include "k_ray_tile.cuh"
 
@@ -37,8 +38,7 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 2) split_tail_kernel(RenderL
     const int q = lane & (G - 1);       // lane within the group
     const int gbase = lane & ~(G - 1);  // first lane of the group
     const unsigned gmask = ((1u << G) - 1u) << gbase;
-    const float step = L.grid.step;
-    const float inv_step = 1.0f / step;
+    const float inv_step = 1.0f / L.grid.step;
     const long nbricks = ESL ? (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2] : 0;
     const unsigned total = min(__ldcg(&L.split.head[0]), L.split.cap);  // final: first phase done
     unsigned long long executed = 0;
@@ -47,20 +47,15 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 2) split_tail_kernel(RenderL
         if (q == 0) qi = atomicAdd(&L.split.head[1], 1u);
         qi = __shfl_sync(gmask, qi, 0, G);
         if (qi >= total) break;
-        const int2 pj = __ldcg(&L.split.rec_pj[qi]);
-        const float4 ct = __ldcg(&L.split.rec_ct[qi]);
-        const int pix = pj.x;
-        // the same ray record as the first phase (same code, same inputs)
-        RaySetup ray;
-        ray_setup(L.cam, L.grid, pix % L.cam.width, pix / L.cam.width, ray);
         RayPos rp;
-        ray_pos_init(ray, step, rp);
+        int jlo, pix;
+        float RC0, RC1, RC2, RT;
+        split_load(L.split.rec + (long)qi * SPLIT_REC, rp, jlo, pix, RC0, RC1, RC2, RT);
         float Pf[3], df[3], inv_df[3];
         ray_float(rp, Pf, df, inv_df);
         const uint8_t *dist = nullptr;
         if (ESL) dist = L.dist + octant_of(df) * nbricks;
-        float RC0 = ct.x, RC1 = ct.y, RC2 = ct.z, RT = ct.w;
-        group_march<ESL, G>(L, rp, dist, Pf, df, inv_df, inv_step, pj.y, gmask, q, gbase, RC0,
+        group_march<ESL, G>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q, gbase, RC0,
                             RC1, RC2, RT, executed);
         if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
     }

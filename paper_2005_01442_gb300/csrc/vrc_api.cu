@@ -31,6 +31,7 @@ struct Occ {
     uint8_t *dev = nullptr;   // occupancy bytes
     uint8_t *dist = nullptr;  // 8 forward-box distance fields (0 = occupied)
     int *scratch = nullptr;   // summed-volume table used while building dist
+    uint32_t *cells = nullptr;  // cell transparency mask (cellmask_words words)
     long n = 0;
     unsigned brick_version = 0, tf_version = 0;
 };
@@ -60,7 +61,7 @@ int lanes_of(int kernel) { return kernel == 3 ? 4 : kernel == 4 ? 8 : kernel == 
 
 // Queue of the split render, one per stream that renders with it (renders on one stream run
 // in order, so they can share it): a 256-byte header (pushed, claimed counts), then `cap`
-// (pixel, sample) records and `cap` (colour, transmittance) records.
+// ray records of SPLIT_REC float4.
 struct SplitBuf {
     unsigned char *base = nullptr;
     size_t cap = 0;
@@ -129,6 +130,7 @@ void free_volume(Volume &v) {
         cudaFree(kv.second.dev);
         cudaFree(kv.second.dist);
         cudaFree(kv.second.scratch);
+        cudaFree(kv.second.cells);
     }
     v.occ.clear();
 }
@@ -264,7 +266,8 @@ vrc_status upload_tf(vrc_ctx *ctx, Tf &t, const float *rgba, float lo, float hi)
 
 // Occupancy of (volume, B, tf), rebuilt when the bricks or the table changed.
 vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStream_t st,
-                      const uint8_t **out, const uint8_t **dist_out = nullptr) {
+                      const uint8_t **out, const uint8_t **dist_out = nullptr,
+                      const uint32_t **cells_out = nullptr) {
     Bricks &b = v.bricks[slot_of(B)];
     if (!b.mn || b.B != B) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
     long key = (long)tf_id * 2 + slot_of(B);
@@ -273,12 +276,16 @@ vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStre
         cudaFree(o.dev);
         cudaFree(o.dist);
         cudaFree(o.scratch);
+        cudaFree(o.cells);
         o.dev = o.dist = nullptr;
         o.scratch = nullptr;
+        o.cells = nullptr;
         o.n = 0;
         CK(cudaMalloc(&o.dev, (size_t)b.count()), "cudaMalloc(occupancy)");
         CK(cudaMalloc(&o.dist, 8 * (size_t)b.count()), "cudaMalloc(occupancy)");
         CK(cudaMalloc(&o.scratch, box_dist_scratch_bytes(b.nb)), "cudaMalloc(occupancy)");
+        CK(cudaMalloc(&o.cells, sizeof(uint32_t) * (size_t)cellmask_words(v.n)),
+           "cudaMalloc(cell mask)");
         o.n = b.count();
         o.brick_version = o.tf_version = 0;
     }
@@ -286,11 +293,13 @@ vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStre
         CK(launch_occupancy(b.mn, b.mx, v.dtype, b.count(), t.prefix, t.lo, t.du, o.dev, st),
            "occupancy launch");
         CK(launch_box_dist(o.dev, b.nb, o.scratch, o.dist, st), "distance launch");
+        CK(launch_cellmask(view_of(v), t.prefix, t.lo, t.du, o.cells, st), "cell mask launch");
         o.brick_version = b.version;
         o.tf_version = t.version;
     }
     *out = o.dev;
     if (dist_out) *dist_out = o.dist;
+    if (cells_out) *cells_out = o.cells;
     return VRC_OK;
 }
 
@@ -332,10 +341,13 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     L.err = ctx->err_word;
     if (p->brick) {
         const uint8_t *occ = nullptr, *dist = nullptr;
-        s = ensure_occ(ctx, *v, tf_id, *t, p->brick, st, &occ, &dist);
+        const uint32_t *cells = nullptr;
+        s = ensure_occ(ctx, *v, tf_id, *t, p->brick, st, &occ, &dist, &cells);
         if (s != VRC_OK) return s;
         Bricks &b = v->bricks[slot_of(p->brick)];
         L.dist = dist;
+        L.cells = cells;
+        L.cwx = (v->n[0] + 1 + 31) / 32;
         L.bricks.B = b.B;
         L.bricks.shift = b.B == 16 ? 4 : 3;
         for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b.nb[k];
@@ -353,23 +365,22 @@ vrc_status split_queue(vrc_ctx *ctx, cudaStream_t st, size_t need, RaySplit &q) 
         cudaFree(b.base);
         b.base = nullptr;
         b.cap = 0;
-        const size_t bytes = 256 + ((need * sizeof(int2) + 255) & ~(size_t)255) + need * sizeof(float4);
+        const size_t bytes = 256 + need * SPLIT_REC * sizeof(float4);
         CK(cudaMalloc(&b.base, bytes), "cudaMalloc(split queue)");
         b.cap = need;
     }
     q.head = (unsigned *)b.base;
-    q.rec_pj = (int2 *)(b.base + 256);
-    q.rec_ct = (float4 *)(b.base + 256 + ((b.cap * sizeof(int2) + 255) & ~(size_t)255));
+    q.rec = (float4 *)(b.base + 256);
     q.cap = (unsigned)b.cap;
     return VRC_OK;
 }
 
-// Launches the render kernel params->kernel selects (0 and 6: split render; 1: per-ray;
-// 2..5: lane groups). allow_split = false renders kernel 0 with the per-ray kernel.
+// Launches the render kernel params->kernel selects (0 and 6: split render, 1: per-ray,
+// 2..5: lane groups). Without a queue (queue_ok = false) kernel 0 runs per ray.
 vrc_status launch_render(vrc_ctx *ctx, const vrc_params *params, RenderLaunch &L,
-                         cudaStream_t st, bool allow_split = true) {
+                         cudaStream_t st, bool queue_ok = true) {
     const int k = params->kernel;
-    if ((k == 0 && allow_split) || k == 6) {
+    if (k == 6 || (k == 0 && queue_ok)) {
         vrc_status s = split_queue(ctx, st, (size_t)L.cam.width * L.cam.height, L.split);
         if (s != VRC_OK) return s;
         CK(cudaMemsetAsync(L.split.head, 0, 2 * sizeof(unsigned), st), "split queue reset");
@@ -621,6 +632,7 @@ vrc_status vrc_tf_free(vrc_ctx *ctx, int tf_id) {
                 cudaFree(it->second.dev);
                 cudaFree(it->second.dist);
                 cudaFree(it->second.scratch);
+                cudaFree(it->second.cells);
                 kv.second.occ.erase(it);
             }
         }
@@ -659,6 +671,29 @@ vrc_status vrc_occupancy_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint8_t
     CK(cudaMemcpyAsync(occ_host, occ, (size_t)v->bricks[slot_of(B)].count(),
                        cudaMemcpyDeviceToHost, st), "occupancy copy");
     CK(cudaStreamSynchronize(st), "occupancy copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_cellmask_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint32_t *words_host,
+                            long nwords, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!words_host) return fail(ctx, VRC_ERR_ARG, "words_host is NULL");
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick must be 8 or 16");
+    if (nwords != cellmask_words(v->n))
+        return fail(ctx, VRC_ERR_ARG, "nwords must be %ld", cellmask_words(v->n));
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t *occ = nullptr;
+    const uint32_t *cells = nullptr;
+    vrc_status s = ensure_occ(ctx, *v, tf_id, *t, B, st, &occ, nullptr, &cells);
+    if (s != VRC_OK) return s;
+    CK(cudaMemcpyAsync(words_host, cells, sizeof(uint32_t) * (size_t)nwords,
+                       cudaMemcpyDeviceToHost, st), "cell mask copy");
+    CK(cudaStreamSynchronize(st), "cell mask copy sync");
     return VRC_OK;
 }
 
@@ -819,7 +854,7 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     Tf *t = get_tf(ctx, tf_id);
     if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
     Bricks *b = nullptr;
-    size_t occ_off = 0, dist_off = 0, svt_off = 0;
+    size_t occ_off = 0, dist_off = 0, svt_off = 0, cells_off = 0;
     if (B) {
         b = &v->bricks[slot_of(B)];
         if (!b->mn || b->B != B) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
@@ -828,6 +863,7 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
         dist_off = align256(n);
         svt_off = dist_off + align256(8 * n);
         const size_t need = svt_off + align256(box_dist_scratch_bytes(b->nb));
+        cells_off = need;
         if (need > (size_t)VRC_NOALLOC_SCRATCH_BYTES)
             return fail(ctx, VRC_ERR_ARG,
                         "vrc_render_noalloc: %ld bricks of size %d need %zu scratch bytes, above "
@@ -851,6 +887,15 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
         CK(launch_occupancy(b->mn, b->mx, v->dtype, b->count(), t->prefix, t->lo, t->du, occ, st),
            "occupancy launch");
         CK(launch_box_dist(occ, b->nb, svt, dist, st), "distance launch");
+        // the cell mask too when it fits behind the tables (it only saves work)
+        if (cells_off + sizeof(uint32_t) * (size_t)cellmask_words(v->n) <=
+            (size_t)VRC_NOALLOC_SCRATCH_BYTES) {
+            uint32_t *cells = (uint32_t *)(scratch + cells_off);
+            CK(launch_cellmask(view_of(*v), t->prefix, t->lo, t->du, cells, st),
+               "cell mask launch");
+            L.cells = cells;
+            L.cwx = (v->n[0] + 1 + 31) / 32;
+        }
         L.dist = dist;
         L.bricks.B = b->B;
         L.bricks.shift = b->B == 16 ? 4 : 3;
@@ -860,7 +905,7 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     }
     L.out = (float4 *)out_rgba_dev;
     L.counters = counters_dev;
-    // no queue here (it would need device memory): kernel 0 renders with the per-ray kernel
+    // no queue here (it would need device memory): kernel 0 renders per ray
     if (params->kernel == 6)
         return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not run the split render (kernel 6)");
     return launch_render(ctx, params, L, st, false);

@@ -146,18 +146,58 @@ __device__ __forceinline__ int octant_of(const float df[3]) {
     return (df[0] < 0.0f) | ((df[1] < 0.0f) << 1) | ((df[2] < 0.0f) << 2);
 }
 
-// Split render (k_render_split.cu): the first phase renders every ray with one lane and hands
-// rays that are still running after SPLIT_K0 samples of non-zero opacity to a queue; the second
-// phase finishes each queued ray with SPLIT_G lanes (blocks of SPLIT_G consecutive samples
-// composited by a scan), so no ray's cost rests on one lane.
-constexpr int SPLIT_K0 = 32;
+// Split render (k_render_split.cu): the first phase composites samples 0 .. SPLIT_J0 - 1 of
+// every ray with one lane and hands rays that go on to a queue; the second phase finishes
+// each queued ray with SPLIT_G lanes (blocks of SPLIT_G consecutive samples composited by a
+// scan), so no ray's cost rests on one lane. With SPLIT_J0 = 0 (the measured best on the
+// 512^2 x 400 CT) the first phase only sets rays up and leaps each to its first sample that
+// may be non-zero.
 constexpr int SPLIT_G = 8;
+constexpr int SPLIT_J0 = 0;  // a multiple of SPLIT_G
 struct RaySplit {
     unsigned *head;  // NULL: no split; else [records pushed, records claimed by the second phase]
-    int2 *rec_pj;    // (linear pixel, first sample index left)
-    float4 *rec_ct;  // (colour so far, transmittance so far)
+    float4 *rec;     // SPLIT_REC float4 per queued ray (split_store)
     unsigned cap;    // records the queue holds (>= the image's pixels)
 };
+constexpr int SPLIT_REC = 7;
+
+// A queued ray: its sample placement record, the next sample index, the colour and
+// transmittance composited so far and its pixel.
+__device__ __forceinline__ void split_store(float4 *r, const RayPos &rp, int j, int pix, float C0,
+                                            float C1, float C2, float T) {
+    r[0] = make_float4(__int_as_float(rp.I0[0]), __int_as_float(rp.I0[1]),
+                       __int_as_float(rp.I0[2]), __int_as_float(rp.nseg));
+    r[1] = make_float4(rp.r0[0].hi, rp.r0[0].lo, rp.r0[1].hi, rp.r0[1].lo);
+    r[2] = make_float4(rp.r0[2].hi, rp.r0[2].lo, rp.d[0].hi, rp.d[0].lo);
+    r[3] = make_float4(rp.d[1].hi, rp.d[1].lo, rp.d[2].hi, rp.d[2].lo);
+    r[4] = make_float4(rp.mlast.hi, rp.mlast.lo, rp.dlast, __int_as_float(j));
+    r[5] = make_float4(C0, C1, C2, T);
+    r[6] = make_float4(__int_as_float(pix), 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void split_load(const float4 *r, RayPos &rp, int &j, int &pix,
+                                           float &C0, float &C1, float &C2, float &T) {
+    const float4 a = __ldcg(r), b = __ldcg(r + 1), c = __ldcg(r + 2), d = __ldcg(r + 3);
+    const float4 e = __ldcg(r + 4), f = __ldcg(r + 5), g = __ldcg(r + 6);
+    rp.I0[0] = __float_as_int(a.x);
+    rp.I0[1] = __float_as_int(a.y);
+    rp.I0[2] = __float_as_int(a.z);
+    rp.nseg = __float_as_int(a.w);
+    rp.r0[0] = {b.x, b.y};
+    rp.r0[1] = {b.z, b.w};
+    rp.r0[2] = {c.x, c.y};
+    rp.d[0] = {c.z, c.w};
+    rp.d[1] = {d.x, d.y};
+    rp.d[2] = {d.z, d.w};
+    rp.mlast = {e.x, e.y};
+    rp.dlast = e.z;
+    j = __float_as_int(e.w);
+    C0 = f.x;
+    C1 = f.y;
+    C2 = f.z;
+    T = f.w;
+    pix = __float_as_int(g.x);
+}
 
 struct RenderLaunch {
     VolView vol;
@@ -171,7 +211,51 @@ struct RenderLaunch {
     unsigned long long *counters;  // NULL or [nominal, executed]
     int *err;                      // device error word
     RaySplit split;                // used by the split render only
+    const uint32_t *cells;         // NULL, or the cell transparency mask (with dist)
+    int cwx;                       // mask words per row of cells along x
 };
+
+// Bit of the cell holding sample base ip (ip in [-1, n-1]); 0: the sample's opacity is zero.
+__device__ __forceinline__ bool cell_open(const uint32_t *__restrict__ cells, int cwx,
+                                          const int n[3], const int ip[3]) {
+    const int cx = ip[0] + 1, cy = ip[1] + 1, cz = ip[2] + 1;
+    const uint32_t w = __ldg(cells + ((long)cz * (n[1] + 1) + cy) * cwx + (cx >> 5));
+    return (w >> (cx & 31)) & 1u;
+}
+
+// Quick skip test of sample j < nseg - 1 from its float position (the leap path's, within
+// ~1.5e-3 voxel of the exact one for coordinates up to 4096). Away from cell faces (by
+// LEAP_MARGIN) the float cell is the exact cell, so the brick and cell tests need no exact
+// placement: QS_EMPTY_BRICK and QS_CLEAR_CELL mean opacity zero (skip), QS_OPEN means the
+// sample must be resampled; QS_EXACT (near a face) means take the exact position first.
+// Without a cell mask (cells == NULL) only the brick is tested.
+enum { QS_EXACT = 0, QS_EMPTY_BRICK = 1, QS_CLEAR_CELL = 2, QS_OPEN = 3 };
+__device__ __forceinline__ int quick_skip(const BrickView &bv, const uint8_t *__restrict__ dist,
+                                          const uint32_t *__restrict__ cells, int cwx,
+                                          const int n[3], const float Pf[3], const float df[3],
+                                          float step, int j, int &cache_lin, int &cache_empty) {
+    const float m = ((float)j + 0.5f) * step;
+    int c[3];
+    bool near = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float pk = fmaf(m, df[k], Pf[k]);
+        const float fl = floorf(pk);
+        const float fr = pk - fl;
+        near |= !(fr >= LEAP_MARGIN && fr <= 1.0f - LEAP_MARGIN);
+        c[k] = min(max((int)fl, -1), n[k] - 1);
+    }
+    if (near) return QS_EXACT;
+    const int lin = ((max(c[2], 0) >> bv.shift) * bv.nb[1] + (max(c[1], 0) >> bv.shift)) *
+                        bv.nb[0] + (max(c[0], 0) >> bv.shift);
+    if (lin != cache_lin) {
+        cache_lin = lin;
+        cache_empty = dist[lin] != 0;
+    }
+    if (cache_empty) return QS_EMPTY_BRICK;
+    if (!cells) return QS_OPEN;
+    return cell_open(cells, cwx, n, c) ? QS_OPEN : QS_CLEAR_CELL;
+}
 
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_pad_volume(const void *src, int dtype, const int n[3], void *dst, int pnx,
@@ -182,6 +266,11 @@ cudaError_t launch_brick_minmax(const VolView &v, int B, void *mn, void *mx, cud
 cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbricks,
                              const int *prefix_dev, float lo, float du, uint8_t *occ,
                              cudaStream_t st);
+// Cell transparency mask of a padded volume for a transfer function (prefix counts of its
+// non-zero opacities): cellmask_words(n) words.
+long cellmask_words(const int n[3]);
+cudaError_t launch_cellmask(const VolView &v, const int *prefix_dev, float lo, float du,
+                            uint32_t *cells, cudaStream_t st);
 size_t box_dist_scratch_bytes(const int nb[3]);
 // dist: 8 x nbricks bytes (one forward-box distance field per direction octant)
 cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,

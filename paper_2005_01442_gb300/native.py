@@ -23,7 +23,7 @@ EXPORTS = [
     "vrc_create", "vrc_destroy", "vrc_volume_upload", "vrc_volume_update", "vrc_volume_free",
     "vrc_volume_info",
     "vrc_bricks_build", "vrc_bricks_get", "vrc_tf_set", "vrc_tf_update", "vrc_tf_free",
-    "vrc_occupancy_build", "vrc_occupancy_get", "vrc_render", "vrc_render_host",
+    "vrc_occupancy_build", "vrc_occupancy_get", "vrc_cellmask_get", "vrc_render", "vrc_render_host",
     "vrc_render_noalloc", "vrc_render_backward", "vrc_server_create", "vrc_server_submit",
     "vrc_server_pump", "vrc_server_poll", "vrc_server_destroy", "vrc_last_device_error",
     "vrc_last_error_message", "vrc_status_str", "vrc_version",
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = False):
     L.vrc_tf_free.argtypes = [vp, ip]
     L.vrc_occupancy_build.argtypes = [vp, ip, ip, ip, vp]
     L.vrc_occupancy_get.argtypes = [vp, ip, ip, ip, vp, vp]
+    L.vrc_cellmask_get.argtypes = [vp, ip, ip, ip, vp, C.c_long, vp]
     L.vrc_render.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp, vp]
     L.vrc_render_host.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp]
     L.vrc_render_noalloc.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,

@@ -152,6 +152,19 @@ class Renderer:
                                             occ.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
         return occ
 
+    def cellmask(self, vol_id: int, tf_id: int, B: int, stream=None):
+        """Cell transparency mask unpacked to bytes, shape (nz+1, ny+1, nx+1): entry
+        [c2+1, c1+1, c0+1] is 0 when samples with floor (c0, c1, c2) have zero opacity."""
+        _, (nx, ny, nz) = self.volume_info(vol_id)
+        cwx = (nx + 1 + 31) // 32
+        words = np.empty((nz + 1, ny + 1, cwx), np.uint32)
+        self._ck(self.lib.vrc_cellmask_get(self.ctx, int(vol_id), int(tf_id), int(B),
+                                           words.ctypes.data_as(C.c_void_p), words.size,
+                                           _stream_ptr(stream)))
+        bits = np.unpackbits(words.view(np.uint8).reshape(nz + 1, ny + 1, cwx * 4),
+                             axis=-1, bitorder="little")
+        return bits[..., :nx + 1].copy()
+
     # -- rendering ----------------------------------------------------------------------------
     def render(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
                brick: int = 0, out=None, counters=None, stream=None, kernel: int = 0):

@@ -123,12 +123,19 @@ def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
                                      brick=B, return_margin=True, return_counts=True)
         _check(img, ref, margin if ert < 1 else None)
         assert cnt[0].item() == rc[0] or abs(cnt[0].item() - rc[0]) <= 8  # segment counts
+        # executed: samples in occupied bricks up to termination, as the oracle counts them
+        # (a pixel whose termination float rounding decides may stop one sample apart)
+        if ert >= 1.0:
+            assert cnt[1].item() == rc[1]
+        else:
+            assert abs(cnt[1].item() - rc[1]) <= int((margin < ERT_MARGIN).sum()) + 8
     R.free_volume(vid)
     R.free_tf(tid)
 
 
 @pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_empty_space_leaping_bit_identical(R, torch, kernel):
+    """Skipping (leaps over empty bricks, clear cells) changes no pixel, bit for bit."""
     vol = _ct_small(seed=5)
     vid = R.upload_volume(vol)
     R.build_bricks(vid, 8)
@@ -345,5 +352,56 @@ def test_split_queue_grows_and_streams_are_independent(R, torch):
     torch.cuda.synchronize()
     for i, img in outs:
         assert torch.equal(img, ref[i])
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+# ------------------------------------------------------- cell transparency mask (a10)
+
+@pytest.mark.parametrize("kind", ["u16", "i16", "f32"])
+def test_cell_mask_bit_exact(R, orc, kind):
+    """The GPU cell mask equals the oracle's byte for byte (ragged sizes across word
+    boundaries; every dtype)."""
+    if kind == "u16":
+        vol = synth.phantom(40, seed=3)[:, :37, :]
+        tf, lo, hi = synth.tf_random(5).copy(), synth.PHANTOM_LO, synth.PHANTOM_HI
+        tf[:120, 3] = 0.0  # a transparent low range
+    elif kind == "i16":
+        vol = _ct_small(shape=(45, 50, 63))
+        tf, lo, hi = synth.tf_ct(), synth.CT_LO, synth.CT_HI
+    else:
+        vol = (np.random.default_rng(4).normal(0, 1, (33, 29, 70)).cumsum(0) * 60).astype(
+            np.float32)
+        tf, lo, hi = synth.tf_random(8, 5).copy(), -300.0, 300.0
+        tf[:200, 3] = 0.0
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, lo, hi)
+    got = R.cellmask(vid, tid, 8)
+    ref = orc.cellmask(vol, tf, lo, hi)
+    assert 0 < ref.sum() < ref.size
+    assert np.array_equal(got, ref)
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+def test_cell_mask_follows_updates(R, orc):
+    """The mask is rebuilt when the volume or the table changes."""
+    vol = _ct_small(seed=8)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tf = synth.tf_ct()
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    assert np.array_equal(R.cellmask(vid, tid, 8), orc.cellmask(vol, tf, synth.CT_LO, synth.CT_HI))
+    tf2 = synth.tf_ct(3)
+    R.update_tf(tid, tf2, synth.CT_LO, synth.CT_HI)
+    assert np.array_equal(R.cellmask(vid, tid, 8),
+                          orc.cellmask(vol, tf2, synth.CT_LO, synth.CT_HI))
+    vol2 = vol.copy()
+    vol2[10:20, 5:30, 7:40] = 1300
+    R.update_volume(vid, vol2)
+    R.build_bricks(vid, 8)
+    assert np.array_equal(R.cellmask(vid, tid, 8),
+                          orc.cellmask(vol2, tf2, synth.CT_LO, synth.CT_HI))
     R.free_tf(tid)
     R.free_volume(vid)

@@ -65,7 +65,8 @@ def test_batched_images_equal_alone(env):
         assert time.time() - t0 < 60.0
     torch.cuda.synchronize()
     for r, o in zip(reqs, outs):
-        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick)
+        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick,
+                         kernel=1)
         assert torch.equal(o, alone)
     srv.close()
 
@@ -87,7 +88,8 @@ def test_kernel_leaves_when_idle_and_relaunches(env):
         time.sleep(0.05)  # > idle limit: the kernel must have left by itself
         torch.cuda.synchronize()
         assert srv.pump() is False
-        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick)
+        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick,
+                         kernel=1)
         assert torch.equal(o, alone)
     srv.close()
 
