@@ -245,9 +245,10 @@ cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbr
 // cells along x, word (c'_z * (ny + 1) + c'_y) * cwx + c'_x / 32, bit c'_x % 32.
 //
 // One CTA per 32 x 8 cells in x, y and a run of CM_ZC cells in z. It streams the padded z
-// slices: each slice's 35 x 11 values go to shared memory and are reduced over the 4-row y
-// window into a ring of the last 4 slices; once 4 slices are in, each warp reduces one row of
-// cells over the z ring and the 4-column x window, applies the rule and writes one word.
+// slices: each slice's 35 x 11 values go to shared memory; each thread reduces its two
+// positions of the 8 x 35 row block over the 4-row y window into a register ring of the last
+// 4 slices and, once 4 slices are in, over the z window; then each warp reduces one row of
+// cells over the 4-column x window, applies the rule and writes one word.
 constexpr int CM_TX = 32, CM_TY = 8, CM_ZC = 32;
 constexpr int CM_HX = CM_TX + 3, CM_HY = CM_TY + 3;
 constexpr int CM_THREADS = 32 * CM_TY;
@@ -259,7 +260,6 @@ __global__ void __launch_bounds__(CM_THREADS) cellmask_kernel(VolView v,
                                                                uint32_t *__restrict__ cells,
                                                                int cwx) {
     __shared__ float s_in[CM_HY][CM_HX];
-    __shared__ float s_mn[4][CM_TY][CM_HX], s_mx[4][CM_TY][CM_HX];
     __shared__ float s_zmn[CM_TY][CM_HX], s_zmx[CM_TY][CM_HX];
     __shared__ int pre[257];
     const int cx0 = blockIdx.x * CM_TX, cy0 = blockIdx.y * CM_TY, cz0 = blockIdx.z * CM_ZC;
@@ -283,12 +283,15 @@ __global__ void __launch_bounds__(CM_THREADS) cellmask_kernel(VolView v,
     static_assert(CM_TY * CM_HX <= 2 * CM_THREADS, "two row-block positions per thread");
     int ry[2], rx[2];
     bool ry_ok[2];
+    float rmn[2][4], rmx[2][4];  // y-window min/max of the last 4 slices, newest first
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int i = (int)threadIdx.x + e * CM_THREADS;
         ry_ok[e] = i < CM_TY * CM_HX;
         ry[e] = ry_ok[e] ? i / CM_HX : 0;
         rx[e] = ry_ok[e] ? i % CM_HX : 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rmn[e][k] = rmx[e][k] = 0.0f;
     }
     // padded slice zp holds taps of cells zp - 3 .. zp; the next slice is loaded into
     // registers while the current one is reduced
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(CM_THREADS) cellmask_kernel(VolView v,
 #pragma unroll
     for (int e = 0; e < 2; ++e) nxt[e] = as_f32(base[(long)min(cz0, v.pnz - 1) * slice + off[e]]);
     for (int zp = cz0; zp < zend + 3; ++zp) {
-        __syncthreads();  // s_in and the ring slot of zp are free
+        __syncthreads();  // s_in and s_zmn / s_zmx are free
 #pragma unroll
         for (int e = 0; e < 2; ++e) s_in[sy[e]][sx[e]] = nxt[e];
         if (zp + 1 < zend + 3) {
@@ -305,34 +308,30 @@ __global__ void __launch_bounds__(CM_THREADS) cellmask_kernel(VolView v,
             for (int e = 0; e < 2; ++e) nxt[e] = as_f32(base[zo + off[e]]);
         }
         __syncthreads();
-        // y window into the ring slot of zp, then (once 4 slices are in) the z window over the
-        // ring; each thread owns the same two (y, x) positions of the 8 x 35 row block
-        const int r = zp & 3;
+        // y window of the thread's two (y, x) positions of the 8 x 35 row block, shifted into
+        // a register ring of the last 4 slices; once 4 slices are in, the z window
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            if (!ry_ok[e]) continue;
             float mn = s_in[ry[e]][rx[e]], mx = mn;
 #pragma unroll
             for (int k = 1; k < 4; ++k) {
                 mn = fminf(mn, s_in[ry[e] + k][rx[e]]);
                 mx = fmaxf(mx, s_in[ry[e] + k][rx[e]]);
             }
-            s_mn[r][ry[e]][rx[e]] = mn;
-            s_mx[r][ry[e]][rx[e]] = mx;
+#pragma unroll
+            for (int k = 3; k > 0; --k) {
+                rmn[e][k] = rmn[e][k - 1];
+                rmx[e][k] = rmx[e][k - 1];
+            }
+            rmn[e][0] = mn;
+            rmx[e][0] = mx;
         }
         if (zp < cz0 + 3) continue;
-        __syncthreads();
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             if (!ry_ok[e]) continue;
-            float mn = s_mn[0][ry[e]][rx[e]], mx = s_mx[0][ry[e]][rx[e]];
-#pragma unroll
-            for (int k = 1; k < 4; ++k) {
-                mn = fminf(mn, s_mn[k][ry[e]][rx[e]]);
-                mx = fmaxf(mx, s_mx[k][ry[e]][rx[e]]);
-            }
-            s_zmn[ry[e]][rx[e]] = mn;
-            s_zmx[ry[e]][rx[e]] = mx;
+            s_zmn[ry[e]][rx[e]] = fminf(fminf(rmn[e][0], rmn[e][1]), fminf(rmn[e][2], rmn[e][3]));
+            s_zmx[ry[e]][rx[e]] = fmaxf(fmaxf(rmx[e][0], rmx[e][1]), fmaxf(rmx[e][2], rmx[e][3]));
         }
         __syncthreads();
         const int cz = zp - 3, cy = cy0 + warp;

@@ -60,6 +60,8 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
     constexpr unsigned low = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
     const float step = L.grid.step, thr = L.grid.ert;
     int blk = jlo >> SH;
+    int cache_lin = -1;     // brick of this lane's last sample
+    bool cache_occ = false;
     while (blk * G < rp.nseg) {
         const int j = blk * G + q;
         float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, eT = 1.0f;  // identity of "over"
@@ -71,7 +73,12 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
             float f[3];
             place(rp, step, L.grid.n, j, ip, f, delta);
             if (ESL) {
-                in_occ = dist[brick_of(L.bricks, ip)] == 0;
+                const int lin = brick_of(L.bricks, ip);
+                if (lin != cache_lin) {  // lane q's samples of successive blocks share bricks
+                    cache_lin = lin;
+                    cache_occ = dist[lin] == 0;
+                }
+                in_occ = cache_occ;
                 live = in_occ && (!L.cells || cell_open(L.cells, L.cwx, L.grid.n, ip));
             }
             if (live) {

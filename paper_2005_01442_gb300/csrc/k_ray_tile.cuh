@@ -166,6 +166,8 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             }
         }
         if (__all_sync(0xffffffffu, done)) break;
+        // a first phase that hands every ray over at its first sample composites nothing
+        if constexpr (SPLIT && SPLIT_J0 == 0) continue;
         if (!done && !idle) {
             const float s = tricubic_rep(rep, ip, f);
             // post-classification: u = (s - lo) * du on [0, 255], linear between entries

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(32 * SPLIT_RAY_WARPS, 16 / SPLIT_RAY_WARPS)
 }
 
 template <bool ESL>
-__global__ void __launch_bounds__(32 * SPLIT_WARPS, 2) split_tail_kernel(RenderLaunch L) {
+__global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderLaunch L) {
     constexpr int G = SPLIT_G;
     const int lane = threadIdx.x & 31;
     const int q = lane & (G - 1);       // lane within the group
