@@ -240,113 +240,147 @@ cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbr
 // Cell c (per axis c = -1 .. n-1, index c' = c + 1) holds the samples with floor(p) = c; their
 // 64 cubic taps are voxels c-1 .. c+2, i.e. padded indices c' .. c'+3. The B-spline weights are
 // non-negative and sum to one, so such a sample lies in [min, max] of the taps (up to float
-// rounding, which the +-1 index margin covers); bit c' of the mask is the occupancy rule on
-// that range, and a sample in a cell of bit 0 has opacity exactly zero. Bits: words of 32
-// cells along x, word (c'_z * (ny + 1) + c'_y) * cwx + c'_x / 32, bit c'_x % 32.
+// rounding, which the +-1 index margin covers). Bit c' of the mask is the occupancy rule on
+// that range: open when an entry of non-zero opacity lies in
+// [floor(u(min)) - 1, ceil(u(max)) + 1]; a sample in a clear cell has opacity exactly zero.
+// Bits: words of 32 cells along x, word (c'_z * (ny + 1) + c'_y) * cwx + c'_x / 32, bit
+// c'_x % 32.
 //
-// One CTA per 32 x 8 cells in x, y and a run of CM_ZC cells in z. It streams the padded z
-// slices: each slice's 35 x 11 values go to shared memory; each thread reduces its two
-// positions of the 8 x 35 row block over the 4-row y window into a register ring of the last
-// 4 slices and, once 4 slices are in, over the z window; then each warp reduces one row of
-// cells over the 4-column x window, applies the rule and writes one word.
-constexpr int CM_TX = 32, CM_TY = 8, CM_ZC = 32;
-constexpr int CM_HX = CM_TX + 3, CM_HY = CM_TY + 3;
-constexpr int CM_THREADS = 32 * CM_TY;
+// The rule is evaluated without a min/max: u is monotone in the value, so the range is the
+// union of the taps' own index intervals [floor(u_i) - 1, ceil(u_i) + 1], and it holds no
+// non-zero entry exactly when all those intervals lie in one run of zero-opacity entries.
+// Each tap is therefore reduced to a byte, the id of the zero run holding its interval (0
+// when none does), and a cell is clear exactly when its 64 bytes are equal and non-zero,
+// i.e. when their bitwise OR equals their bitwise AND and is non-zero.
+//
+// Pass 1 (zero_run_id_kernel) writes that byte for every padded voxel, 8 voxels per thread.
+// Pass 2 (cellmask_kernel) gives each thread 4 cells along x (one 32-bit word of bytes and the
+// next) in one (y, z-run) column: per padded z slice it ORs / ANDs the 4 rows of the y window
+// into a register ring of the last 4 slices, then the z window over the ring, then the x
+// window by funnel shifts; 8 lanes combine their 4 bits into one mask word.
+constexpr int CM_ZC = 16;  // cells per thread along z
 
 template <typename T>
-__global__ void __launch_bounds__(CM_THREADS) cellmask_kernel(VolView v,
-                                                               const int *__restrict__ prefix,
-                                                               float lo, float du,
-                                                               uint32_t *__restrict__ cells,
-                                                               int cwx) {
-    __shared__ float s_in[CM_HY][CM_HX];
-    __shared__ float s_zmn[CM_TY][CM_HX], s_zmx[CM_TY][CM_HX];
-    __shared__ int pre[257];
-    const int cx0 = blockIdx.x * CM_TX, cy0 = blockIdx.y * CM_TY, cz0 = blockIdx.z * CM_ZC;
-    const int zend = min(cz0 + CM_ZC, v.n[2] + 1);  // cells cz0 .. zend - 1
-    const T *base = (const T *)v.base;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 257; i += CM_THREADS) pre[i] = prefix[i];
-    // this thread's two elements of a slice (CM_HY * CM_HX <= 2 * CM_THREADS); cells beyond n
-    // read clamped values, their bits are never used
-    static_assert(CM_HY * CM_HX <= 2 * CM_THREADS, "two slice elements per thread");
-    long off[2];
-    int sy[2], sx[2];
+__device__ __forceinline__ void load8(const T *__restrict__ src, long g, float v[8]) {
+    const uint4 q = __ldg((const uint4 *)src + g);  // 8 two-byte values
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int i = min((int)threadIdx.x + e * CM_THREADS, CM_HY * CM_HX - 1);
-        sy[e] = i / CM_HX;
-        sx[e] = i % CM_HX;
-        off[e] = (long)min(cy0 + sy[e], v.pny - 1) * v.pnx + min(cx0 + sx[e], v.pnx - 1);
+    for (int e = 0; e < 4; ++e) {
+        v[2 * e] = (float)(T)(w[e] & 0xffffu);
+        v[2 * e + 1] = (float)(T)(w[e] >> 16);
     }
-    const long slice = (long)v.pny * v.pnx;
-    static_assert(CM_TY * CM_HX <= 2 * CM_THREADS, "two row-block positions per thread");
-    int ry[2], rx[2];
-    bool ry_ok[2];
-    float rmn[2][4], rmx[2][4];  // y-window min/max of the last 4 slices, newest first
+}
+
+template <>
+__device__ __forceinline__ void load8<float>(const float *__restrict__ src, long g, float v[8]) {
+    const float4 a = __ldg((const float4 *)src + 2 * g), b = __ldg((const float4 *)src + 2 * g + 1);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) zero_run_id_kernel(const T *__restrict__ src, long n8,
+                                                          const uint8_t *__restrict__ zrun,
+                                                          float lo, float du,
+                                                          uint2 *__restrict__ out) {
+    __shared__ uint8_t rid[256];
+    rid[threadIdx.x] = zrun[threadIdx.x];
+    __syncthreads();
+    for (long g = blockIdx.x * 256L + threadIdx.x; g < n8; g += (long)gridDim.x * 256) {
+        float v[8];
+        load8<T>(src, g, v);
+        uint32_t w[2] = {0u, 0u};
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int i = (int)threadIdx.x + e * CM_THREADS;
-        ry_ok[e] = i < CM_TY * CM_HX;
-        ry[e] = ry_ok[e] ? i / CM_HX : 0;
-        rx[e] = ry_ok[e] ? i % CM_HX : 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) rmn[e][k] = rmx[e][k] = 0.0f;
+        for (int e = 0; e < 8; ++e) {
+            const float u = u_index(v[e], lo, du);
+            const int k0 = max((int)floorf(u) - 1, 0);
+            const int k1 = min((int)ceilf(u) + 1, 255);
+            const uint32_t r0 = rid[k0], r1 = rid[k1];
+            w[e >> 2] |= (r0 == r1 ? r0 : 0u) << (8 * (e & 3));
+        }
+        out[g] = make_uint2(w[0], w[1]);
     }
-    // padded slice zp holds taps of cells zp - 3 .. zp; the next slice is loaded into
-    // registers while the current one is reduced
-    float nxt[2];
+}
+
+// gid: the run-id bytes as words (wpr words per padded row); kpad: threads per (y, z-run)
+// column, a multiple of 8 >= ceil((nx + 1) / 4), so that the 8 lanes building one mask word
+// share a column.
+__global__ void __launch_bounds__(128) cellmask_kernel(const uint32_t *__restrict__ gid, int wpr,
+                                                       int pny, int nx, int ny, int nz,
+                                                       uint32_t *__restrict__ cells, int cwx,
+                                                       int kpad) {
+    const long t = blockIdx.x * 128L + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int k = (int)(t % kpad);  // cells 4k .. 4k+3 (k & 7 == lane & 7)
+    const long col = t / kpad;      // the same for the 8 lanes of a mask word
+    const int cy = (int)(col % (ny + 1));
+    const int cz0 = (int)(col / (ny + 1)) * CM_ZC;
+    if (cz0 > nz) return;  // past the last column: whole groups of 8 lanes leave
+    const int cz1 = min(cz0 + CM_ZC, nz + 1);
+    const bool kval = k < (nx + 1 + 3) / 4;
+    // cells past nx read clamped words; their bits are never used
+    const int kw0 = min(k, wpr - 1), kw1 = min(k + 1, wpr - 1);
+    uint32_t ro0[4] = {0u, 0u, 0u, 0u}, ra0[4] = {0u, 0u, 0u, 0u};  // newest first
+    uint32_t ro1[4] = {0u, 0u, 0u, 0u}, ra1[4] = {0u, 0u, 0u, 0u};
+    // padded slice zp holds taps of cells zp - 3 .. zp; rows cy .. cy+3 the y window. The
+    // words of slice zp + 1 are loaded while slice zp is reduced.
+    uint32_t nw0[4], nw1[4];
+    {
+        const uint32_t *row = gid + ((long)cz0 * pny + cy) * wpr;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) nxt[e] = as_f32(base[(long)min(cz0, v.pnz - 1) * slice + off[e]]);
-    for (int zp = cz0; zp < zend + 3; ++zp) {
-        __syncthreads();  // s_in and s_zmn / s_zmx are free
-#pragma unroll
-        for (int e = 0; e < 2; ++e) s_in[sy[e]][sx[e]] = nxt[e];
-        if (zp + 1 < zend + 3) {
-            const long zo = (long)min(zp + 1, v.pnz - 1) * slice;
-#pragma unroll
-            for (int e = 0; e < 2; ++e) nxt[e] = as_f32(base[zo + off[e]]);
+        for (int dy = 0; dy < 4; ++dy) {
+            nw0[dy] = __ldg(row + dy * wpr + kw0);
+            nw1[dy] = __ldg(row + dy * wpr + kw1);
         }
-        __syncthreads();
-        // y window of the thread's two (y, x) positions of the 8 x 35 row block, shifted into
-        // a register ring of the last 4 slices; once 4 slices are in, the z window
+    }
+    for (int zp = cz0; zp < cz1 + 3; ++zp) {
+        uint32_t o0 = 0u, a0 = 0xffffffffu, o1 = 0u, a1 = 0xffffffffu;
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            float mn = s_in[ry[e]][rx[e]], mx = mn;
-#pragma unroll
-            for (int k = 1; k < 4; ++k) {
-                mn = fminf(mn, s_in[ry[e] + k][rx[e]]);
-                mx = fmaxf(mx, s_in[ry[e] + k][rx[e]]);
-            }
-#pragma unroll
-            for (int k = 3; k > 0; --k) {
-                rmn[e][k] = rmn[e][k - 1];
-                rmx[e][k] = rmx[e][k - 1];
-            }
-            rmn[e][0] = mn;
-            rmx[e][0] = mx;
+        for (int dy = 0; dy < 4; ++dy) {
+            o0 |= nw0[dy];
+            a0 &= nw0[dy];
+            o1 |= nw1[dy];
+            a1 &= nw1[dy];
         }
+        if (zp + 1 < cz1 + 3) {
+            const uint32_t *row = gid + ((long)(zp + 1) * pny + cy) * wpr;
+#pragma unroll
+            for (int dy = 0; dy < 4; ++dy) {
+                nw0[dy] = __ldg(row + dy * wpr + kw0);
+                nw1[dy] = __ldg(row + dy * wpr + kw1);
+            }
+        }
+#pragma unroll
+        for (int r = 3; r > 0; --r) {
+            ro0[r] = ro0[r - 1];
+            ra0[r] = ra0[r - 1];
+            ro1[r] = ro1[r - 1];
+            ra1[r] = ra1[r - 1];
+        }
+        ro0[0] = o0;
+        ra0[0] = a0;
+        ro1[0] = o1;
+        ra1[0] = a1;
         if (zp < cz0 + 3) continue;
+        const uint32_t O0 = (ro0[0] | ro0[1]) | (ro0[2] | ro0[3]);
+        const uint32_t A0 = (ra0[0] & ra0[1]) & (ra0[2] & ra0[3]);
+        const uint32_t O1 = (ro1[0] | ro1[1]) | (ro1[2] | ro1[3]);
+        const uint32_t A1 = (ra1[0] & ra1[1]) & (ra1[2] & ra1[3]);
+        // byte i of Ox / Ax: OR / AND over the columns 4k+i .. 4k+i+3 of cell 4k+i
+        const uint32_t Ox = O0 | __funnelshift_r(O0, O1, 8) | __funnelshift_r(O0, O1, 16) |
+                            __funnelshift_r(O0, O1, 24);
+        const uint32_t Ax = A0 & __funnelshift_r(A0, A1, 8) & __funnelshift_r(A0, A1, 16) &
+                            __funnelshift_r(A0, A1, 24);
+        uint32_t open = 0u;
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            if (!ry_ok[e]) continue;
-            s_zmn[ry[e]][rx[e]] = fminf(fminf(rmn[e][0], rmn[e][1]), fminf(rmn[e][2], rmn[e][3]));
-            s_zmx[ry[e]][rx[e]] = fmaxf(fmaxf(rmx[e][0], rmx[e][1]), fmaxf(rmx[e][2], rmx[e][3]));
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t ob = (Ox >> (8 * i)) & 0xffu, ab = (Ax >> (8 * i)) & 0xffu;
+            open |= (uint32_t)(!(ob == ab && ob != 0u)) << i;
         }
-        __syncthreads();
-        const int cz = zp - 3, cy = cy0 + warp;
-        float mn = s_zmn[warp][lane], mx = s_zmx[warp][lane];
-#pragma unroll
-        for (int k = 1; k < 4; ++k) {
-            mn = fminf(mn, s_zmn[warp][lane + k]);
-            mx = fmaxf(mx, s_zmx[warp][lane + k]);
-        }
-        const float ulo = u_index(mn, lo, du), uhi = u_index(mx, lo, du);
-        const int k0 = max((int)floorf(ulo) - 1, 0);
-        const int k1 = min((int)ceilf(uhi) + 1, 255);
-        const unsigned w = __ballot_sync(0xffffffffu, (pre[k1 + 1] - pre[k0]) > 0);
-        if (lane == 0 && cy <= v.n[1])
-            cells[((long)cz * (v.n[1] + 1) + cy) * cwx + blockIdx.x] = w;
+        if (!kval) open = 0u;
+        const uint32_t w = __reduce_or_sync(0xffu << (lane & 24), open << (4 * (k & 7)));
+        if ((lane & 7) == 0 && (k >> 3) < cwx)
+            cells[((long)(zp - 3) * (ny + 1) + cy) * cwx + (k >> 3)] = w;
     }
 }
 
@@ -354,20 +388,31 @@ long cellmask_words(const int n[3]) {
     return (long)((n[0] + 1 + 31) / 32) * (n[1] + 1) * (n[2] + 1);
 }
 
-cudaError_t launch_cellmask(const VolView &v, const int *prefix_dev, float lo, float du,
-                            uint32_t *cells, cudaStream_t st) {
-    const int cwx = (v.n[0] + 1 + 31) / 32;
-    const dim3 grid(cwx, (v.n[1] + 1 + CM_TY - 1) / CM_TY, (v.n[2] + 1 + CM_ZC - 1) / CM_ZC);
+size_t cellmask_scratch_bytes(const VolView &v) { return (size_t)v.pnx * v.pny * v.pnz; }
+
+cudaError_t launch_cellmask(const VolView &v, const uint8_t *zrun_dev, float lo, float du,
+                            uint8_t *scratch, uint32_t *cells, cudaStream_t st) {
+    const long n8 = (long)v.pnx * v.pny * v.pnz / 8;  // pnx is a multiple of 8
+    long b1 = (n8 + 255) / 256;
+    if (b1 > 152L * 16) b1 = 152L * 16;
     switch (v.dtype) {
     case DT_U16:
-        cellmask_kernel<uint16_t><<<grid, CM_THREADS, 0, st>>>(v, prefix_dev, lo, du, cells, cwx);
+        zero_run_id_kernel<uint16_t><<<(unsigned)b1, 256, 0, st>>>(
+            (const uint16_t *)v.base, n8, zrun_dev, lo, du, (uint2 *)scratch);
         break;
     case DT_I16:
-        cellmask_kernel<int16_t><<<grid, CM_THREADS, 0, st>>>(v, prefix_dev, lo, du, cells, cwx);
+        zero_run_id_kernel<int16_t><<<(unsigned)b1, 256, 0, st>>>(
+            (const int16_t *)v.base, n8, zrun_dev, lo, du, (uint2 *)scratch);
         break;
     default:
-        cellmask_kernel<float><<<grid, CM_THREADS, 0, st>>>(v, prefix_dev, lo, du, cells, cwx);
+        zero_run_id_kernel<float><<<(unsigned)b1, 256, 0, st>>>(
+            (const float *)v.base, n8, zrun_dev, lo, du, (uint2 *)scratch);
     }
+    const int cwx = (v.n[0] + 1 + 31) / 32;
+    const int kpad = ((v.n[0] + 1 + 3) / 4 + 7) / 8 * 8;
+    const long threads = (long)kpad * (v.n[1] + 1) * ((v.n[2] + 1 + CM_ZC - 1) / CM_ZC);
+    cellmask_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
+        (const uint32_t *)scratch, v.pnx / 4, v.pny, v.n[0], v.n[1], v.n[2], cells, cwx, kpad);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ struct Volume {
     int pnx = 0, pny = 0, pnz = 0;
     void *dpad = nullptr;          // compact padded copy (brick tables)
     float4 *drep = nullptr;        // x-replicated float4 copy (rendering)
+    uint8_t *mask_scratch = nullptr;  // cell-mask build scratch (cellmask_scratch_bytes)
     Bricks bricks[2];               // B = 8, B = 16
     std::map<long, Occ> occ;        // key: tf_id * 2 + (B == 16)
 };
@@ -51,6 +52,7 @@ struct Tf {
     float4 *rgba = nullptr;   // 256
     float4 *drgba = nullptr;  // 256
     int *prefix = nullptr;    // 257
+    uint8_t *zrun = nullptr;  // 256: run id of each zero-opacity entry (0: non-zero entry)
     unsigned version = 0;
 };
 
@@ -122,6 +124,7 @@ struct DeviceGuard {
 void free_volume(Volume &v) {
     cudaFree(v.dpad);
     cudaFree(v.drep);
+    cudaFree(v.mask_scratch);
     for (auto &b : v.bricks) {
         cudaFree(b.mn);
         cudaFree(b.mx);
@@ -139,6 +142,7 @@ void free_tf(Tf &t) {
     cudaFree(t.rgba);
     cudaFree(t.drgba);
     cudaFree(t.prefix);
+    cudaFree(t.zrun);
 }
 
 bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
@@ -236,10 +240,15 @@ vrc_status upload_tf(vrc_ctx *ctx, Tf &t, const float *rgba, float lo, float hi)
         if (!isfinite(rgba[i])) return fail(ctx, VRC_ERR_ARG, "transfer function has non-finite entries");
     std::vector<float4> a(256), d(256);
     std::vector<int> pre(257);
+    std::vector<uint8_t> zrun(256);
     pre[0] = 0;
+    int runs = 0;
     for (int i = 0; i < 256; ++i) {
         a[i] = make_float4(rgba[4 * i], rgba[4 * i + 1], rgba[4 * i + 2], rgba[4 * i + 3]);
-        pre[i + 1] = pre[i] + (rgba[4 * i + 3] > 0.0f ? 1 : 0);
+        const bool nz = rgba[4 * i + 3] > 0.0f;
+        pre[i + 1] = pre[i] + (nz ? 1 : 0);
+        if (!nz && (i == 0 || rgba[4 * i - 1] > 0.0f)) ++runs;  // at most 128 runs
+        zrun[i] = nz ? 0 : (uint8_t)runs;
     }
     for (int i = 0; i < 255; ++i)
         d[i] = make_float4(rgba[4 * i + 4] - rgba[4 * i], rgba[4 * i + 5] - rgba[4 * i + 1],
@@ -249,6 +258,7 @@ vrc_status upload_tf(vrc_ctx *ctx, Tf &t, const float *rgba, float lo, float hi)
         CK(cudaMalloc(&t.rgba, 256 * sizeof(float4)), "cudaMalloc(tf)");
         CK(cudaMalloc(&t.drgba, 256 * sizeof(float4)), "cudaMalloc(tf)");
         CK(cudaMalloc(&t.prefix, 257 * sizeof(int)), "cudaMalloc(tf)");
+        CK(cudaMalloc(&t.zrun, 256), "cudaMalloc(tf)");
     } else {
         // tables may be in use by queued kernels on any stream
         CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize(tf update)");
@@ -256,6 +266,7 @@ vrc_status upload_tf(vrc_ctx *ctx, Tf &t, const float *rgba, float lo, float hi)
     CK(cudaMemcpy(t.rgba, a.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice), "tf upload");
     CK(cudaMemcpy(t.drgba, d.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice), "tf upload");
     CK(cudaMemcpy(t.prefix, pre.data(), 257 * sizeof(int), cudaMemcpyHostToDevice), "tf upload");
+    CK(cudaMemcpy(t.zrun, zrun.data(), 256, cudaMemcpyHostToDevice), "tf upload");
     volatile float range = hi - lo;
     t.lo = lo;
     t.hi = hi;
@@ -293,7 +304,11 @@ vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStre
         CK(launch_occupancy(b.mn, b.mx, v.dtype, b.count(), t.prefix, t.lo, t.du, o.dev, st),
            "occupancy launch");
         CK(launch_box_dist(o.dev, b.nb, o.scratch, o.dist, st), "distance launch");
-        CK(launch_cellmask(view_of(v), t.prefix, t.lo, t.du, o.cells, st), "cell mask launch");
+        if (!v.mask_scratch)
+            CK(cudaMalloc(&v.mask_scratch, cellmask_scratch_bytes(view_of(v))),
+               "cudaMalloc(cell mask scratch)");
+        CK(launch_cellmask(view_of(v), t.zrun, t.lo, t.du, v.mask_scratch, o.cells, st),
+           "cell mask launch");
         o.brick_version = b.version;
         o.tf_version = t.version;
     }
@@ -887,11 +902,12 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
         CK(launch_occupancy(b->mn, b->mx, v->dtype, b->count(), t->prefix, t->lo, t->du, occ, st),
            "occupancy launch");
         CK(launch_box_dist(occ, b->nb, svt, dist, st), "distance launch");
-        // the cell mask too when it fits behind the tables (it only saves work)
-        if (cells_off + sizeof(uint32_t) * (size_t)cellmask_words(v->n) <=
-            (size_t)VRC_NOALLOC_SCRATCH_BYTES) {
+        // the cell mask too when it and its build scratch fit behind the tables (it only
+        // saves work)
+        const size_t mask_off = cells_off + align256(sizeof(uint32_t) * (size_t)cellmask_words(v->n));
+        if (mask_off + cellmask_scratch_bytes(view_of(*v)) <= (size_t)VRC_NOALLOC_SCRATCH_BYTES) {
             uint32_t *cells = (uint32_t *)(scratch + cells_off);
-            CK(launch_cellmask(view_of(*v), t->prefix, t->lo, t->du, cells, st),
+            CK(launch_cellmask(view_of(*v), t->zrun, t->lo, t->du, scratch + mask_off, cells, st),
                "cell mask launch");
             L.cells = cells;
             L.cwx = (v->n[0] + 1 + 31) / 32;

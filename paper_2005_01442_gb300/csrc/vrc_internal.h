@@ -266,11 +266,14 @@ cudaError_t launch_brick_minmax(const VolView &v, int B, void *mn, void *mx, cud
 cudaError_t launch_occupancy(const void *mn, const void *mx, int dtype, long nbricks,
                              const int *prefix_dev, float lo, float du, uint8_t *occ,
                              cudaStream_t st);
-// Cell transparency mask of a padded volume for a transfer function (prefix counts of its
-// non-zero opacities): cellmask_words(n) words.
+// Cell transparency mask of a padded volume for a transfer function, given the run id of
+// each zero-opacity table entry (1, 2, ... per maximal run of zero entries; 0 for entries of
+// non-zero opacity): cellmask_words(n) words.
+// `scratch` holds cellmask_scratch_bytes(v) bytes (16-byte aligned) for the build.
 long cellmask_words(const int n[3]);
-cudaError_t launch_cellmask(const VolView &v, const int *prefix_dev, float lo, float du,
-                            uint32_t *cells, cudaStream_t st);
+size_t cellmask_scratch_bytes(const VolView &v);
+cudaError_t launch_cellmask(const VolView &v, const uint8_t *zrun_dev, float lo, float du,
+                            uint8_t *scratch, uint32_t *cells, cudaStream_t st);
 size_t box_dist_scratch_bytes(const int nb[3]);
 // dist: 8 x nbricks bytes (one forward-box distance field per direction octant)
 cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,

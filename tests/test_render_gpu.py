@@ -405,3 +405,31 @@ def test_cell_mask_follows_updates(R, orc):
                           orc.cellmask(vol2, tf2, synth.CT_LO, synth.CT_HI))
     R.free_tf(tid)
     R.free_volume(vid)
+
+
+@pytest.mark.parametrize("pattern", ["alternate", "all_zero", "all_open", "blocks"])
+def test_cell_mask_zero_runs(R, orc, pattern):
+    """Tables with many, one or no runs of zero opacity (the mask kernel reduces taps to the
+    id of the zero run holding them): still equal to the oracle's min/max rule."""
+    vol = _ct_small(seed=11, shape=(37, 41, 70))
+    tf = synth.tf_ct().copy()
+    if pattern == "alternate":
+        tf[:, 3] = np.where(np.arange(256) % 2 == 1, 0.2, 0.0)
+    elif pattern == "all_zero":
+        tf[:, 3] = 0.0
+    elif pattern == "all_open":
+        tf[:, 3] = 0.05
+    else:
+        tf[:, 3] = np.where((np.arange(256) // 7) % 3 == 0, 0.3, 0.0)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    got = R.cellmask(vid, tid, 8)
+    ref = orc.cellmask(vol, tf, synth.CT_LO, synth.CT_HI)
+    assert np.array_equal(got, ref)
+    if pattern == "all_zero":
+        assert ref.sum() == 0
+    if pattern == "all_open":
+        assert ref.all()
+    R.free_tf(tid)
+    R.free_volume(vid)
