@@ -8,9 +8,10 @@ brick min/max table, rebuild the occupancy for the transfer function, render the
 L2 is flushed (a 256 MB write) before every step, outside the step's events.
 
 Printed: one JSON line on rank 0. `value` is executed samples per second (Gsamples/s, all
-ranks); Mrays/s and nominal Gsamples/s ride along. `roofline` reports the render kernel
-against the FP32 issue roof (152 SMs x 128 lanes x 2 flop x 2.07 GHz), using the algorithmic
-flop count per executed sample. `cpu_baseline` times the FP64 oracle on host cores on a
+ranks; executed = samples in occupied bricks up to termination, the oracle's count); Mrays/s
+and nominal Gsamples/s ride along. `roofline` reports one render call (the split render's two
+kernels) against the FP32 issue roof (152 SMs x 128 lanes x 2 flop x 2.07 GHz), using the
+algorithmic flop count per executed sample. `cpu_baseline` times the FP64 oracle on host cores on a
 bounded sample of the same workload. `e2e` repeats the measurement through
 vrc_render_host (image read back to pinned host memory inside the timed region).
 
@@ -31,6 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_SAMPLE = 230      # algorithmic FP32 flops per executed sample (FMA = 2)
+# DRAM bytes (read + write) of one default render call (both split-render kernels) on this
+# workload with 8^3 bricks, from the ncu capture summarised in
+# profiles/split_render_ct512x400_1024sq_B8.md; None for any other kernel or brick size.
+TRAFFIC_PER_RENDER_B8 = 70.11e6
 SM_COUNT_NOMINAL = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -382,7 +387,9 @@ def main():
             "samples_per_step": {"nominal": nominal, "executed": executed},
             "render_kernel_ms": kernel_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC_PER_RENDER_B8 if args.kernel in (0, 6) and B == 8
+                                     else None),
                          "kernel": ("one render call: split_head_kernel + split_tail_kernel"
                                     if args.kernel in (0, 6) else f"render kernel {args.kernel}"),
                          "basis": f"{FLOPS_PER_SAMPLE} flop/executed sample; peak = {sms} SMs x "
