@@ -96,32 +96,37 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
                 eT = 1.0f - alpha;
             }
         }
-        // inclusive scan of "over" across the group's block
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) {
-            const float p0 = __shfl_up_sync(gmask, e0, o, G);
-            const float p1 = __shfl_up_sync(gmask, e1, o, G);
-            const float p2 = __shfl_up_sync(gmask, e2, o, G);
-            const float pT = __shfl_up_sync(gmask, eT, o, G);
-            if (q >= o) {
-                e0 = fmaf(pT, e0, p0);
-                e1 = fmaf(pT, e1, p1);
-                e2 = fmaf(pT, e2, p2);
-                eT = pT * eT;
-            }
-        }
-        // prepend what the ray has accumulated before this block
-        const float t0 = fmaf(RT, e0, RC0), t1 = fmaf(RT, e1, RC1), t2 = fmaf(RT, e2, RC2);
-        const float tT = RT * eT;
         const unsigned occ_bits = (__ballot_sync(gmask, in_occ) >> gbase) & low;
-        const unsigned stop_bits = (__ballot_sync(gmask, live && (1.0f - tT > thr)) >> gbase) & low;
-        const int last = stop_bits ? __ffs(stop_bits) - 1 : G - 1;
-        executed += __popc(occ_bits & (0xffffffffu >> (31 - last)));
-        RC0 = __shfl_sync(gmask, t0, last, G);
-        RC1 = __shfl_sync(gmask, t1, last, G);
-        RC2 = __shfl_sync(gmask, t2, last, G);
-        RT = __shfl_sync(gmask, tT, last, G);
-        if (stop_bits) break;
+        if (__ballot_sync(gmask, live) & gmask) {
+            // inclusive scan of "over" across the group's block
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const float p0 = __shfl_up_sync(gmask, e0, o, G);
+                const float p1 = __shfl_up_sync(gmask, e1, o, G);
+                const float p2 = __shfl_up_sync(gmask, e2, o, G);
+                const float pT = __shfl_up_sync(gmask, eT, o, G);
+                if (q >= o) {
+                    e0 = fmaf(pT, e0, p0);
+                    e1 = fmaf(pT, e1, p1);
+                    e2 = fmaf(pT, e2, p2);
+                    eT = pT * eT;
+                }
+            }
+            // prepend what the ray has accumulated before this block
+            const float t0 = fmaf(RT, e0, RC0), t1 = fmaf(RT, e1, RC1), t2 = fmaf(RT, e2, RC2);
+            const float tT = RT * eT;
+            const unsigned stop_bits =
+                (__ballot_sync(gmask, live && (1.0f - tT > thr)) >> gbase) & low;
+            const int last = stop_bits ? __ffs(stop_bits) - 1 : G - 1;
+            executed += __popc(occ_bits & (0xffffffffu >> (31 - last)));
+            RC0 = __shfl_sync(gmask, t0, last, G);
+            RC1 = __shfl_sync(gmask, t1, last, G);
+            RC2 = __shfl_sync(gmask, t2, last, G);
+            RT = __shfl_sync(gmask, tT, last, G);
+            if (stop_bits) break;
+        } else {
+            executed += __popc(occ_bits);  // a block of identities: (RC, RT) unchanged
+        }
         ++blk;
         // leap from the next block's first sample (uniform across the group) unless the block
         // ended inside an occupied brick

@@ -24,6 +24,8 @@ namespace vrc {
 
 constexpr int SPLIT_RAY_WARPS = 2;  // warps per CTA of the first phase
 constexpr int SPLIT_WARPS = 8;      // warps per CTA of the second phase
+constexpr int SPLIT_CLAIM = 1;      // queued rays a group claims per atomic (more: the long
+                                    // rays of a claim serialise and the frame waits on them)
 
 template <bool ESL>
 __global__ void __launch_bounds__(32 * SPLIT_RAY_WARPS, 16 / SPLIT_RAY_WARPS)
@@ -37,15 +39,20 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderL
     const int lane = threadIdx.x & 31;
     const int q = lane & (G - 1);       // lane within the group
     const int gbase = lane & ~(G - 1);  // first lane of the group
-    const unsigned gmask = ((1u << G) - 1u) << gbase;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
     const float inv_step = 1.0f / L.grid.step;
     const long nbricks = ESL ? (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2] : 0;
     const unsigned total = min(__ldcg(&L.split.head[0]), L.split.cap);  // final: first phase done
     unsigned long long executed = 0;
+    unsigned next = 0, end = 0;  // rays claimed by this group and not yet started
     while (true) {
-        unsigned qi = 0;
-        if (q == 0) qi = atomicAdd(&L.split.head[1], 1u);
-        qi = __shfl_sync(gmask, qi, 0, G);
+        if (next == end) {  // claim SPLIT_CLAIM consecutive rays with one atomic
+            unsigned qi = 0;
+            if (q == 0) qi = atomicAdd(&L.split.head[1], (unsigned)SPLIT_CLAIM);
+            next = __shfl_sync(gmask, qi, 0, G);
+            end = min(next + SPLIT_CLAIM, total);
+        }
+        const unsigned qi = next++;
         if (qi >= total) break;
         RayPos rp;
         int jlo, pix;
