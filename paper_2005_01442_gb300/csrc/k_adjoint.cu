@@ -16,8 +16,9 @@
 // and chain through alpha = 1 - (1-a)^delta, the table interpolation (into the two entries)
 // and the 64 B-spline taps (into the voxels). Transfer-function gradients are summed in
 // shared memory per CTA, voxel gradients with global float atomics (the summation order, and
-// so the last bits, vary from run to run). Samples in empty bricks (opacity exactly zero,
-// whose derivative is taken as zero at the clamp) are skipped exactly as in the forward.
+// so the last bits, vary from run to run). Samples in empty bricks or clear cells (opacity
+// exactly zero, whose derivative is taken as zero at the clamp, so that every contribution of
+// such a sample is exactly zero) are skipped exactly as in the forward.
 #include "vrc_internal.h"
 
 namespace vrc {
@@ -50,6 +51,34 @@ __device__ __forceinline__ void eval_sample(const RenderLaunch &L, const int ip[
     e.rgba.z = fmaf(e.fu, e.drgba.z, c0.z);
     e.rgba.w = fmaf(e.fu, e.drgba.w, c0.w);
     e.alpha = segment_alpha(e.rgba.w, delta);
+}
+
+// Adds (v0, v1, v2, v3) to the voxel gradients of taps x0 .. x0+3 of a row, clamped to
+// [0, nx-1], with the fewest aligned vector atomics (one float4, two float2 or float + float2
+// + float away from the edges).
+__device__ __forceinline__ void add_taps_x(float *row, int x0, int nx, float v0, float v1,
+                                           float v2, float v3) {
+    if (x0 >= 0 && x0 + 3 < nx) {
+        float *a = row + x0;
+        switch ((unsigned)((uintptr_t)a & 15u)) {
+        case 0:
+            atomicAdd((float4 *)a, make_float4(v0, v1, v2, v3));
+            return;
+        case 8:
+            atomicAdd((float2 *)a, make_float2(v0, v1));
+            atomicAdd((float2 *)(a + 2), make_float2(v2, v3));
+            return;
+        default:  // 4 or 12: a + 1 is 8-byte aligned
+            atomicAdd(a, v0);
+            atomicAdd((float2 *)(a + 1), make_float2(v1, v2));
+            atomicAdd(a + 3, v3);
+            return;
+        }
+    }
+    atomicAdd(row + min(max(x0, 0), nx - 1), v0);
+    atomicAdd(row + min(max(x0 + 1, 0), nx - 1), v1);
+    atomicAdd(row + min(max(x0 + 2, 0), nx - 1), v2);
+    atomicAdd(row + min(max(x0 + 3, 0), nx - 1), v3);
 }
 
 template <bool ESL, bool VOLGRAD>
@@ -119,6 +148,10 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
                     in_run = false;
                     continue;
                 }
+                if (L.cells && !cell_open(L.cells, L.cwx, L.grid.n, ip)) {  // opacity 0
+                    ++j;
+                    continue;
+                }
             }
             const int k = j / seg;
             while (filled <= k) ckpt[filled++] = Tr;
@@ -147,7 +180,9 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
             int ip[3];
             float f[3], delta;
             place(rp, step, L.grid.n, j, ip, f, delta);
-            if (ESL && dist[brick_of(L.bricks, ip)] != 0) continue;
+            if (ESL && (dist[brick_of(L.bricks, ip)] != 0 ||
+                        (L.cells && !cell_open(L.cells, L.cwx, L.grid.n, ip))))
+                continue;
             SampleEval e;
             eval_sample(L, ip, f, delta, e);
             buf_s[n] = e.s;
@@ -214,11 +249,8 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
                             const int y = min(max(ip[1] - 1 + cy, 0), ny - 1);
                             const float wyz = wy[cy] * wzc;
                             float *row = A.grad_vol + ((long)z * ny + y) * nx;
-#pragma unroll
-                            for (int cx = 0; cx < 4; ++cx) {
-                                const int x = min(max(ip[0] - 1 + cx, 0), nx - 1);
-                                atomicAdd(row + x, wx[cx] * wyz);
-                            }
+                            add_taps_x(row, ip[0] - 1, nx, wx[0] * wyz, wx[1] * wyz,
+                                       wx[2] * wyz, wx[3] * wyz);
                         }
                     }
                 }
