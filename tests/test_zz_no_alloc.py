@@ -75,3 +75,23 @@ def test_noalloc_rejects_brick_grids_beyond_the_array(env):
     assert "scratch" in msg and "maximum" in msg
     R.free_volume(vid)
     R.free_tf(tid)
+
+
+def test_noalloc_kernel_choice(env):
+    """kernel 0 renders with the per-ray kernel (the split render's queue would need memory,
+    kernel 6 is rejected)."""
+    torch, native, R = env
+    vol = synth.ct_volume((40, 48, 56), seed=14)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(24, 1, synth.dims_of(vol), 64, 48)[0]
+    ref = R.render(vid, tid, cam, ert=0.999, brick=8, kernel=1)
+    out = torch.full_like(ref, float("nan"))
+    native.check(R.ctx, _noalloc(torch, native, R, vid, tid, cam, 8, 0, out, None))
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    assert _noalloc(torch, native, R, vid, tid, cam, 8, 6, out, None) == -1  # VRC_ERR_ARG
+    assert "split" in R.lib.vrc_last_error_message(R.ctx).decode()
+    R.free_tf(tid)
+    R.free_volume(vid)
