@@ -31,7 +31,8 @@ class Camera(C.Structure):
 
 
 class Params(C.Structure):
-    _fields_ = [("step", C.c_double), ("ert", C.c_double), ("brick", C.c_int), ("pad", C.c_int)]
+    _fields_ = [("step", C.c_double), ("ert", C.c_double), ("brick", C.c_int),
+                ("interp", C.c_int), ("preclass", C.c_int), ("pad", C.c_int)]
 
 
 class Ball(C.Structure):
@@ -64,6 +65,10 @@ def lib():
         L.orc_bspline_dweights.argtypes = [C.c_double, dp]
         L.orc_sample.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double]
         L.orc_sample.restype = C.c_double
+        L.orc_sample_linear.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double]
+        L.orc_sample_linear.restype = C.c_double
+        L.orc_sample_rgba.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double,
+                                      ip, ip, vp, C.c_double, C.c_double, dp]
         L.orc_classify.argtypes = [C.c_double, vp, C.c_double, C.c_double, dp]
         L.orc_ray.argtypes = [C.POINTER(Camera), vp, ip, ip, dp, dp, dp, dp]
         L.orc_ray.restype = C.c_int
@@ -123,6 +128,27 @@ def sample(vol: np.ndarray, p) -> float:
     vol = np.ascontiguousarray(vol)
     nz, ny, nx = vol.shape
     return float(lib().orc_sample(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, *map(float, p)))
+
+
+def sample_linear(vol: np.ndarray, p) -> float:
+    """Trilinear value of `vol` (nz, ny, nx) at the point p = (x, y, z)."""
+    vol = np.ascontiguousarray(vol)
+    nz, ny, nx = vol.shape
+    return float(lib().orc_sample_linear(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz,
+                                         *map(float, p)))
+
+
+def sample_rgba(vol: np.ndarray, p, tf: np.ndarray, lo: float, hi: float, interp: int = 0,
+                preclass: int = 0) -> np.ndarray:
+    """rgba of the sample at p under an interpolation (0 cubic, 1 trilinear) and
+    classification (0 post, 1 pre) variant."""
+    vol = np.ascontiguousarray(vol)
+    tf = np.ascontiguousarray(tf, np.float32)
+    nz, ny, nx = vol.shape
+    out = (C.c_double * 4)()
+    lib().orc_sample_rgba(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, *map(float, p), int(interp),
+                          int(preclass), _ptr(tf), float(lo), float(hi), out)
+    return np.array(out[:])
 
 
 def classify(s: float, tf: np.ndarray, lo: float, hi: float) -> np.ndarray:
@@ -191,7 +217,8 @@ def _pix(pixels):
 
 
 def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
-           return_margin=False, return_counts=False, return_executed=False):
+           return_margin=False, return_counts=False, return_executed=False, interp=0,
+           preclass=0):
     """FP64 render. Returns float64 (H, W, 4) (or (npix, 4) for a pixel list), plus the ERT
     margins, the (nominal, executed) sample counts and the per-pixel executed samples when
     asked."""
@@ -208,7 +235,7 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
     margin = np.empty(n, np.float64) if return_margin else None
     counts = np.zeros(2, np.int64)
     expp = np.zeros(n, np.int32) if return_executed else None
-    par = Params(float(step), float(ert), int(brick), 0)
+    par = Params(float(step), float(ert), int(brick), int(interp), int(preclass), 0)
     b = None
     if ball is not None:
         b = Ball(1, (C.c_double * 3)(*map(float, ball[0])), float(ball[1]))
@@ -243,7 +270,7 @@ def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, wa
     g = np.ascontiguousarray(np.asarray(g, np.float64).reshape(-1, 4))
     gtf = np.zeros((256, 4), np.float64)
     gvol = np.zeros(vol.shape, np.float64) if want_vol else None
-    par = Params(float(step), float(ert), int(brick), 0)
+    par = Params(float(step), float(ert), int(brick), 0, 0, 0)
     rc = lib().orc_render_grad(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
                                float(hi), C.byref(_cam(cam)), C.byref(par), _ptr(occ),
                                _ptr(pix), npix, _ptr(g), _ptr(gtf), _ptr(gvol))

@@ -31,22 +31,34 @@ def beta3(t):
     return out
 
 
-class Field:
-    """Volume extended by edge replication; s(p) by the full kernel sum."""
+def tent(t):
+    """Linear B-spline (the trilinear kernel per axis): max(0, 1 - |t|)."""
+    return np.maximum(0.0, 1.0 - np.abs(np.asarray(t, np.float64)))
 
-    def __init__(self, vol):
-        v = np.asarray(vol, np.float64)
-        self.ext = np.pad(v, PAD, mode="edge")  # (nz+6, ny+6, nx+6)
-        nz, ny, nx = v.shape
+
+class Field:
+    """Volume extended by edge replication; s(p) by the full kernel sum with the cubic
+    B-spline (kernel="cubic") or the tent (kernel="linear"). With `channels` (an array of
+    shape vol.shape + (c,)), the same sum of those per-voxel values instead."""
+
+    def __init__(self, vol, kernel="cubic", channels=None):
+        v = np.asarray(vol if channels is None else channels, np.float64)
+        if channels is None:
+            v = v[..., None]
+        self.ext = np.pad(v, [(PAD, PAD)] * 3 + [(0, 0)], mode="edge")
+        nz, ny, nx = v.shape[:3]
+        self.kern = beta3 if kernel == "cubic" else tent
+        self.scalar = channels is None
         self.gx = np.arange(-PAD, nx + PAD, dtype=np.float64)
         self.gy = np.arange(-PAD, ny + PAD, dtype=np.float64)
         self.gz = np.arange(-PAD, nz + PAD, dtype=np.float64)
 
     def __call__(self, p):
-        bx = beta3(p[0] - self.gx)
-        by = beta3(p[1] - self.gy)
-        bz = beta3(p[2] - self.gz)
-        return float(np.einsum("k,j,i,kji->", bz, by, bx, self.ext))
+        bx = self.kern(p[0] - self.gx)
+        by = self.kern(p[1] - self.gy)
+        bz = self.kern(p[2] - self.gz)
+        r = np.einsum("k,j,i,kjic->c", bz, by, bx, self.ext)
+        return float(r[0]) if self.scalar else r
 
 
 def camera_rays(cam, dims):
@@ -93,11 +105,21 @@ def tf_lookup(s, tf, lo, hi):
     return np.array([np.interp(u, k, tf[:, c].astype(np.float64)) for c in range(4)])
 
 
-def render(vol, tf, lo, hi, cam, step, ert=1.0):
-    """(H, W, 4) float64 image: front-to-back compositing over segment midpoints."""
+def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0):
+    """(H, W, 4) float64 image: front-to-back compositing over segment midpoints.
+    interp 0/1: cubic B-spline / trilinear kernel; preclass 1: classify every voxel, then
+    interpolate the rgba."""
     nz, ny, nx = vol.shape
     dims = (nx, ny, nz)
-    field = Field(vol)
+    kernel = "cubic" if interp == 0 else "linear"
+    if preclass:
+        rgba_vol = np.stack([tf_lookup(float(v), tf, lo, hi)
+                             for v in np.asarray(vol, np.float64).ravel()])
+        pre = Field(vol, kernel, rgba_vol.reshape(vol.shape + (4,)))
+        sample = pre
+    else:
+        field = Field(vol, kernel)
+        sample = lambda p: tf_lookup(field(p), tf, lo, hi)  # noqa: E731
     org, dirs = camera_rays(cam, dims)
     img = np.zeros((cam.height, cam.width, 4))
     amax = 1.0 - 2.0 ** -24
@@ -114,7 +136,7 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0):
             trans = 1.0
             for a, b in zip(edges[:-1], edges[1:]):
                 p = o + 0.5 * (a + b) * d
-                rgba = tf_lookup(field(p), tf, lo, hi)
+                rgba = sample(p)
                 alpha = 1.0 - (1.0 - min(max(rgba[3], 0.0), amax)) ** (b - a)
                 col += trans * alpha * rgba[:3]
                 trans *= 1.0 - alpha

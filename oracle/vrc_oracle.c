@@ -35,6 +35,14 @@
  *   ESL        a sample is skipped when the brick holding floor(p) is empty; runs of samples
  *              inside an empty brick are jumped over. Skipped samples have alpha == 0, so the
  *              image equals the no-skip image bit for bit.
+ *   variants   (the paper's Fig. 4 comparison) trilinear: the 8 voxels floor(p) + {0,1}^3
+ *              (clamped) with weights (1-f, f) per axis, interpolating at voxel centres.
+ *              Pre-classification: every tap voxel is classified first and the sample's
+ *              rgba (colour and opacity, not opacity-weighted) is the weighted sum of the
+ *              taps' rgba with the same weights; opacity correction and compositing follow
+ *              unchanged. Bricks, occupancy and leaping are unchanged (both variants read a
+ *              subset of the cubic taps with non-negative weights, so an empty brick still
+ *              gives opacity exactly zero).
  *   gradient   reverse mode through compositing, opacity, classification and resampling,
  *              w.r.t. the TF entries and the voxel values (see orc_render_grad). At the kinks
  *              of the opacity clamp (a = 0, a = 1-2^-24) and of the index clamp (u = 0, 255)
@@ -81,6 +89,8 @@ typedef struct {
     double step;     /* ds, voxel units */
     double ert;      /* threshold; >= 1 disables */
     int brick;       /* B for ESL; 0 disables */
+    int interp;      /* 0: cubic B-spline, 1: trilinear */
+    int preclass;    /* 0: post-classification, 1: pre-classification */
     int pad;
 } orc_params;
 
@@ -159,6 +169,28 @@ static void taps_at(const double p[3], taps_t *t) {
     }
 }
 
+/* Trilinear weights and base: taps floor(p) + {0, 1} per axis. */
+static void lin_taps_at(const double p[3], long base[3], double w[3][2]) {
+    for (int k = 0; k < 3; ++k) {
+        double fl = floor(p[k]);
+        base[k] = (long)fl;
+        w[k][1] = p[k] - fl;
+        w[k][0] = 1.0 - w[k][1];
+    }
+}
+
+static double resample_linear(const orc_volume *v, const double p[3]) {
+    long base[3];
+    double w[3][2];
+    lin_taps_at(p, base, w);
+    double s = 0.0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a)
+                s += w[0][a] * w[1][b] * w[2][c] * voxel(v, base[0] + a, base[1] + b, base[2] + c);
+    return s;
+}
+
 static double resample(const orc_volume *v, const double p[3]) {
     taps_t t;
     taps_at(p, &t);
@@ -176,6 +208,13 @@ double orc_sample(const void *data, int dtype, int nx, int ny, int nz, double x,
     orc_volume v = {data, dtype, {nx, ny, nz}};
     double p[3] = {x, y, z};
     return resample(&v, p);
+}
+
+double orc_sample_linear(const void *data, int dtype, int nx, int ny, int nz, double x,
+                         double y, double z) {
+    orc_volume v = {data, dtype, {nx, ny, nz}};
+    double p[3] = {x, y, z};
+    return resample_linear(&v, p);
 }
 
 /* ------------------------------------------------------------- classification (a6) ---- */
@@ -209,6 +248,50 @@ void orc_classify(double s, const float *tf, double lo, double hi, double rgba[4
 }
 
 static double clamp_alpha(double a) { return a < 0.0 ? 0.0 : (a > ALPHA_MAX ? ALPHA_MAX : a); }
+
+/* Pre-classification: the taps' classified rgba, summed with the interpolation weights. */
+static void preclassified_rgba(const orc_volume *v, const double p[3], int interp,
+                               const float *tf, double lo, double hi, double rgba[4]) {
+    rgba[0] = rgba[1] = rgba[2] = rgba[3] = 0.0;
+    class_t c;
+    if (interp == 1) {
+        long base[3];
+        double w[3][2];
+        lin_taps_at(p, base, w);
+        for (int z = 0; z < 2; ++z)
+            for (int y = 0; y < 2; ++y)
+                for (int x = 0; x < 2; ++x) {
+                    classify(voxel(v, base[0] + x, base[1] + y, base[2] + z), tf, lo, hi, &c);
+                    const double wt = w[0][x] * w[1][y] * w[2][z];
+                    for (int q = 0; q < 4; ++q) rgba[q] += wt * c.rgba[q];
+                }
+        return;
+    }
+    taps_t t;
+    taps_at(p, &t);
+    for (int z = 0; z < 4; ++z)
+        for (int y = 0; y < 4; ++y)
+            for (int x = 0; x < 4; ++x) {
+                classify(voxel(v, t.base[0] + x, t.base[1] + y, t.base[2] + z), tf, lo, hi, &c);
+                const double wt = t.w[0][x] * t.w[1][y] * t.w[2][z];
+                for (int q = 0; q < 4; ++q) rgba[q] += wt * c.rgba[q];
+            }
+}
+
+/* The rgba of one sample under any variant (for the tests). */
+void orc_sample_rgba(const void *data, int dtype, int nx, int ny, int nz, double x, double y,
+                     double z, int interp, int preclass, const float *tf, double lo, double hi,
+                     double rgba[4]) {
+    orc_volume v = {data, dtype, {nx, ny, nz}};
+    double p[3] = {x, y, z};
+    if (preclass) {
+        preclassified_rgba(&v, p, interp, tf, lo, hi, rgba);
+        return;
+    }
+    class_t c;
+    classify(interp == 1 ? resample_linear(&v, p) : resample(&v, p), tf, lo, hi, &c);
+    memcpy(rgba, c.rgba, sizeof(c.rgba));
+}
 
 /* --------------------------------------------------------------------- rays (a3) ------ */
 
@@ -438,7 +521,18 @@ static double field(const scene_t *S, const double p[3]) {
         for (int k = 0; k < 3; ++k) r2 += (p[k] - S->ball->c[k]) * (p[k] - S->ball->c[k]);
         return r2 <= S->ball->r * S->ball->r ? 1.0 : 0.0;
     }
-    return resample(S->vol, p);
+    return S->par->interp == 1 ? resample_linear(S->vol, p) : resample(S->vol, p);
+}
+
+/* rgba of the sample at p under the scene's interpolation and classification variant. */
+static void sample_rgba(const scene_t *S, const double p[3], double rgba[4]) {
+    if (S->par->preclass && !(S->ball && S->ball->enabled)) {
+        preclassified_rgba(S->vol, p, S->par->interp, S->tf, S->lo, S->hi, rgba);
+        return;
+    }
+    class_t c;
+    classify(field(S, p), S->tf, S->lo, S->hi, &c);
+    memcpy(rgba, c.rgba, sizeof(c.rgba));
 }
 
 /* First sample index past the empty brick b containing sample j, minus a one-sample margin,
@@ -510,12 +604,11 @@ static void render_ray(const scene_t *S, const orc_camera *cam, const int dims[3
                 continue;
             }
         }
-        double s = field(S, p);
-        class_t c;
-        classify(s, S->tf, S->lo, S->hi, &c);
-        double a = clamp_alpha(c.rgba[3]);
+        double rgba[4];
+        sample_rgba(S, p, rgba);
+        double a = clamp_alpha(rgba[3]);
         double alpha = -expm1(dl * log1p(-a));
-        for (int q = 0; q < 3; ++q) C[q] += T * alpha * c.rgba[q];
+        for (int q = 0; q < 3; ++q) C[q] += T * alpha * rgba[q];
         T *= (1.0 - alpha);
         st->executed++;
         if (thr < 1.0) {
@@ -598,6 +691,7 @@ int orc_render_grad(const void *data, int dtype, int nx, int ny, int nz, const f
                     double *grad_tf, double *grad_vol) {
     if (!cam || !par || !g || !grad_tf || par->step <= 0.0 || !(hi > lo)) return ORC_EARG;
     if (par->brick > 0 && !occ) return ORC_EARG;
+    if (par->interp != 0 || par->preclass != 0) return ORC_EARG; /* cubic post only */
     orc_volume v = {data, dtype, {nx, ny, nz}};
     scene_t S;
     scene_init(&S, &v, NULL, tf, lo, hi, par, occ);

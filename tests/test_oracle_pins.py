@@ -84,6 +84,87 @@ def test_bilinear_cross_term_is_reproduced(orc):
         assert abs(orc.sample(vol, p) - (p[0] * p[1] - 2.0 * p[1] * p[2])) < 1e-9
 
 
+# ------------------------------------- interpolation / classification variants (next 1)
+
+def test_trilinear_reproduces_multilinear_fields_and_interpolates(orc):
+    # Trilinear interpolation reproduces every function a + bx + cy + dz + exy + fyz + gxz +
+    # hxyz exactly in the interior and passes through the voxel values.
+    nz, ny, nx = 7, 9, 11
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    f = lambda x, y, z: 3.0 + 0.5 * x - 2.0 * y + 1.5 * z + 0.25 * x * y - 0.75 * y * z \
+        + 0.1 * x * z + 0.05 * x * y * z  # noqa: E731
+    vol = f(x, y, z).astype(np.float64).astype(np.float32)
+    rng = np.random.default_rng(8)
+    for _ in range(80):
+        p = rng.uniform([0.0, 0.0, 0.0], [nx - 1.0, ny - 1.0, nz - 1.0])
+        assert abs(orc.sample_linear(vol, p) - f(*p)) < 1e-4 * max(1.0, abs(f(*p)))
+    for _ in range(20):
+        i, j, k = rng.integers(0, nx), rng.integers(0, ny), rng.integers(0, nz)
+        assert orc.sample_linear(vol, (i, j, k)) == float(vol[k, j, i])
+
+
+def test_trilinear_matches_tent_kernel_sum_with_clamping(orc):
+    # the tent-kernel sum over the edge-extended grid (NumPy), including points outside
+    # the voxel grid where taps are clamped
+    rng = np.random.default_rng(9)
+    vol = rng.normal(0, 1, (5, 6, 7)).astype(np.float32)
+    field = mini.Field(vol, "linear")
+    for _ in range(100):
+        p = rng.uniform([-0.5, -0.5, -0.5], [6.5, 5.5, 4.5])
+        assert abs(orc.sample_linear(vol, p) - field(p)) < 1e-12
+
+
+def test_preclassification_equals_post_for_an_affine_table(orc):
+    # With a table affine in the index and values inside the window, classification commutes
+    # with any interpolation whose weights sum to one: pre == post, cubic and trilinear.
+    k = np.arange(256, dtype=np.float64)
+    tf = np.stack([0.1 + 0.003 * k, 0.9 - 0.002 * k, 0.2 + 0.001 * k, 0.001 + 0.0015 * k],
+                  -1).astype(np.float32)
+    rng = np.random.default_rng(10)
+    vol = rng.uniform(100, 3900, (6, 7, 8)).astype(np.float32)
+    for interp in (0, 1):
+        for _ in range(40):
+            p = rng.uniform([1.0, 1.0, 1.0], [6.0, 5.0, 4.0])
+            post = orc.sample_rgba(vol, p, tf, 0.0, 4095.0, interp, 0)
+            pre = orc.sample_rgba(vol, p, tf, 0.0, 4095.0, interp, 1)
+            np.testing.assert_allclose(pre, post, atol=1e-7)
+    # ... and differs for a table with a step (the variants are not the same method)
+    tf2 = tf.copy()
+    tf2[128:, 3] = 0.9
+    p = (3.3, 3.1, 2.7)
+    assert np.abs(orc.sample_rgba(vol, p, tf2, 0.0, 4095.0, 0, 1)
+                  - orc.sample_rgba(vol, p, tf2, 0.0, 4095.0, 0, 0)).max() > 1e-3
+
+
+@pytest.mark.parametrize("interp,preclass", [(1, 0), (0, 1), (1, 1)])
+def test_variant_renders_match_kernel_sum_brute_force(orc, interp, preclass):
+    rng = np.random.default_rng(12)
+    vol = rng.integers(0, 4096, (7, 8, 6)).astype(np.uint16)
+    tf = synth.tf_random(5, 6)
+    tf[:, 3] *= 0.6
+    nz, ny, nx = vol.shape
+    for cam in _cams_tiny((nx, ny, nz)):
+        for step, ert in [(0.5, 1.0), (0.41, 0.6)]:
+            a = orc.render(vol, tf, 0.0, 4095.0, cam, step, ert=ert, interp=interp,
+                           preclass=preclass)
+            b = mini.render(vol, tf, 0.0, 4095.0, cam, step, ert=ert, interp=interp,
+                            preclass=preclass)
+            assert np.abs(a - b).max() < 1e-11
+
+
+@pytest.mark.parametrize("interp,preclass", [(1, 0), (0, 1), (1, 1)])
+def test_variant_renders_unchanged_by_leaping(orc, interp, preclass):
+    vol = synth.ct_volume((30, 34, 38), seed=13)
+    tf = synth.tf_ct()
+    cam = synth.orbit_cameras(17, 1, synth.dims_of(vol), 12, 10)[0]
+    ref = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, interp=interp,
+                     preclass=preclass)
+    for B in (4, 8):
+        img, (nom, ex) = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, brick=B,
+                                    interp=interp, preclass=preclass, return_counts=True)
+        assert np.array_equal(img, ref) and ex < nom
+
+
 # ------------------------------------------------ whole path vs brute force (a3-a9)
 
 def _cams_tiny(dims):
