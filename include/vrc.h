@@ -90,13 +90,23 @@ typedef struct {
  *                  whole device finish the queued rays (the context keeps a queue of 112
  *                  bytes per pixel for each stream it renders on).
  *                  All kernels compute the same method; images agree within float
- *                  rounding of the compositing order. Other values: VRC_ERR_ARG. */
+ *                  rounding of the compositing order. Other values: VRC_ERR_ARG.
+ *   interp         0 = uniform cubic B-spline (64 taps, the paper's choice), 1 = trilinear
+ *                  (8 taps).
+ *   preclass       0 = post-classification (classify the interpolated value, the paper's
+ *                  choice), 1 = pre-classification (classify every tap voxel, interpolate
+ *                  its rgba). The four combinations are the paper's Fig. 4 comparison; the
+ *                  variants run with kernel 0, 1 and 6 and in vrc_render_noalloc; the lane-
+ *                  group kernels, the server and vrc_render_backward take only 0, 0
+ *                  (VRC_ERR_ARG otherwise). */
 typedef struct {
     float step;
     float ert_threshold;
     int brick;
     int seg_len;
     int kernel;
+    int interp;
+    int preclass;
 } vrc_params;
 
 /* Creates a context bound to CUDA device `device`. */

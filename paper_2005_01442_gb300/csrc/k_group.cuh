@@ -49,7 +49,7 @@ __device__ __forceinline__ int advance_to_occupied(const RayPos &rp, const Rende
 // equal in every lane of the group. `executed` grows by the samples in occupied bricks up to
 // termination, resampled or skipped as clear cells (counted in every lane; callers count it
 // once per group).
-template <bool ESL, int G>
+template <bool ESL, int G, int MODE = MODE_CUBIC_POST>
 __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos &rp,
                                             const uint8_t *__restrict__ dist, const float Pf[3],
                                             const float df[3], const float inv_df[3],
@@ -82,17 +82,11 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
                 live = in_occ && (!L.cells || cell_open(L.cells, L.cwx, L.grid.n, ip));
             }
             if (live) {
-                const float s = tricubic_rep(L.rep, ip, f);
-                const float u = fminf(fmaxf((s - L.tf.lo) * L.tf.du, 0.0f), 255.0f);
-                int i0;
-                floor_small(u, i0);
-                i0 = min(i0, 254);
-                const float fu = u - (float)i0;
-                const float4 c0 = __ldg(L.tf.rgba + i0), dc = __ldg(L.tf.drgba + i0);
-                const float alpha = segment_alpha(fmaf(fu, dc.w, c0.w), delta);
-                e0 = alpha * fmaf(fu, dc.x, c0.x);
-                e1 = alpha * fmaf(fu, dc.y, c0.y);
-                e2 = alpha * fmaf(fu, dc.z, c0.z);
+                const float4 rgba = sample_rgba<MODE>(L.rep, L.tf, ip, f);
+                const float alpha = segment_alpha(rgba.w, delta);
+                e0 = alpha * rgba.x;
+                e1 = alpha * rgba.y;
+                e2 = alpha * rgba.z;
                 eT = 1.0f - alpha;
             }
         }

@@ -33,21 +33,19 @@ __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by,
 // with its colour and transmittance so far; the second phase finishes it with SPLIT_G lanes
 // in blocks aligned to SPLIT_G. Samples between SPLIT_J0 and the queued index have opacity
 // zero, so the split image is also identical with and without skipping.
-template <bool ESL, bool SPLIT = false>
+template <bool ESL, bool SPLIT = false, int MODE = MODE_CUBIC_POST>
 __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile) {
     const int lane = threadIdx.x & 31;
     const int tiles_x = (L.cam.width + 7) >> 3;
     const int px = (tile % tiles_x) * 8 + (lane & 7);
     const int py = (tile / tiles_x) * 4 + (lane >> 3);
     const bool valid = px < L.cam.width && py < L.cam.height;
-    const float4 *__restrict__ tf_rgba = L.tf.rgba;
-    const float4 *__restrict__ tf_drgba = L.tf.drgba;
     // launch fields read in the sample loop, copied once (free for a kernel parameter, one
     // load per tile when the launch record sits in shared memory)
     const BrickView bricks = L.bricks;
     const ReplView rep = L.rep;
     const int gn[3] = {L.grid.n[0], L.grid.n[1], L.grid.n[2]};
-    const float tf_lo = L.tf.lo, tf_du = L.tf.du;
+    const TfView tfv = L.tf;
     const uint32_t *cells = L.cells;
     const int cwx = L.cwx;
 
@@ -169,20 +167,14 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
         // a first phase that hands every ray over at its first sample composites nothing
         if constexpr (SPLIT && SPLIT_J0 == 0) continue;
         if (!done && !idle) {
-            const float s = tricubic_rep(rep, ip, f);
-            // post-classification: u = (s - lo) * du on [0, 255], linear between entries
-            const float u = fminf(fmaxf((s - tf_lo) * tf_du, 0.0f), 255.0f);
-            int i0;
-            floor_small(u, i0);
-            i0 = min(i0, 254);
-            const float fu = u - (float)i0;
-            const float4 c0 = __ldg(tf_rgba + i0), dc = __ldg(tf_drgba + i0);
-            const float a = fmaf(fu, dc.w, c0.w);
-            const float alpha = segment_alpha(a, delta);
+            // resampling and classification (post: u = (s - lo) * du on [0, 255], linear
+            // between entries; or the variant MODE selects)
+            const float4 rgba = sample_rgba<MODE>(rep, tfv, ip, f);
+            const float alpha = segment_alpha(rgba.w, delta);
             const float w = Tr * alpha;
-            C0 = fmaf(w, fmaf(fu, dc.x, c0.x), C0);
-            C1 = fmaf(w, fmaf(fu, dc.y, c0.y), C1);
-            C2 = fmaf(w, fmaf(fu, dc.z, c0.z), C2);
+            C0 = fmaf(w, rgba.x, C0);
+            C1 = fmaf(w, rgba.y, C1);
+            C2 = fmaf(w, rgba.z, C2);
             Tr = Tr - w;
             ++executed;
             if (1.0f - Tr > thr) done = true;

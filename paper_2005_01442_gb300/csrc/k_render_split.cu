@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(32 * SPLIT_RAY_WARPS, 16 / SPLIT_RAY_WARPS)
     render_ray_tile<ESL, true>(L, blockIdx.x * SPLIT_RAY_WARPS + (threadIdx.x >> 5));
 }
 
-template <bool ESL>
+template <bool ESL, int MODE>
 __global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderLaunch L) {
     constexpr int G = SPLIT_G;
     const int lane = threadIdx.x & 31;
@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderL
         ray_float(rp, Pf, df, inv_df);
         const uint8_t *dist = nullptr;
         if (ESL) dist = L.dist + octant_of(df) * nbricks;
-        group_march<ESL, G>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q, gbase, RC0,
-                            RC1, RC2, RT, executed);
+        group_march<ESL, G, MODE>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q,
+                                  gbase, RC0, RC1, RC2, RT, executed);
         if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
     }
     if (L.counters) {
@@ -83,8 +83,8 @@ int tail_ctas(cudaError_t &e) {
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_tail_kernel<true>,
-                                                      32 * SPLIT_WARPS, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, split_tail_kernel<true, MODE_CUBIC_POST>, 32 * SPLIT_WARPS, 0);
     if (e != cudaSuccess) return 0;
     const int n = sms * (per_sm > 0 ? per_sm : 1);
     if (dev >= 0 && dev < 64) cached[dev] = n;
@@ -92,18 +92,25 @@ int tail_ctas(cudaError_t &e) {
 }
 }  // namespace
 
+template <int MODE>
+static void launch_tail(const RenderLaunch &L, int ctas, cudaStream_t st) {
+    if (L.dist) split_tail_kernel<true, MODE><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+    else split_tail_kernel<false, MODE><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+}
+
 cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     const int ctas = tail_ctas(e);
     if (e != cudaSuccess) return e;
     const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
     const unsigned grid = (unsigned)((tiles + SPLIT_RAY_WARPS - 1) / SPLIT_RAY_WARPS);
-    if (L.dist) {
-        split_head_kernel<true><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
-        split_tail_kernel<true><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
-    } else {
-        split_head_kernel<false><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
-        split_tail_kernel<false><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+    if (L.dist) split_head_kernel<true><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+    else split_head_kernel<false><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+    switch (L.mode) {
+    case MODE_LINEAR_POST: launch_tail<MODE_LINEAR_POST>(L, ctas, st); break;
+    case MODE_CUBIC_PRE: launch_tail<MODE_CUBIC_PRE>(L, ctas, st); break;
+    case MODE_LINEAR_PRE: launch_tail<MODE_LINEAR_PRE>(L, ctas, st); break;
+    default: launch_tail<MODE_CUBIC_POST>(L, ctas, st);
     }
     return cudaGetLastError();
 }

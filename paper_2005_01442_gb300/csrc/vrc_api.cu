@@ -341,6 +341,10 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     if (p->brick != 0 && p->brick != 8 && p->brick != 16)
         return fail(ctx, VRC_ERR_ARG, "brick must be 0, 8 or 16");
     if (p->kernel < 0 || p->kernel > 6) return fail(ctx, VRC_ERR_ARG, "kernel must be 0..6");
+    if ((p->interp != 0 && p->interp != 1) || (p->preclass != 0 && p->preclass != 1))
+        return fail(ctx, VRC_ERR_ARG, "interp and preclass must be 0 or 1");
+    if ((p->interp || p->preclass) && p->kernel >= 2 && p->kernel <= 5)
+        return fail(ctx, VRC_ERR_ARG, "the lane-group kernels render the default variant only");
     memset(&L, 0, sizeof(L));
     vrc_status s = build_camera(ctx, cam, L.cam);
     if (s != VRC_OK) return s;
@@ -353,6 +357,7 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     for (int k = 0; k < 3; ++k) L.grid.n[k] = v->n[k];
     L.grid.step = p->step;
     L.grid.ert = p->ert_threshold;
+    L.mode = p->interp + 2 * p->preclass;
     L.err = ctx->err_word;
     if (p->brick) {
         const uint8_t *occ = nullptr, *dist = nullptr;
@@ -775,6 +780,8 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
         return fail(ctx, VRC_ERR_ARG, "gradient buffers must be 4-byte aligned");
     const int seg = params->seg_len == 0 ? 64 : params->seg_len;
     if (seg < 1 || seg > ADJ_MAX_SEG) return fail(ctx, VRC_ERR_ARG, "seg_len must be 0..128");
+    if (params->interp || params->preclass)
+        return fail(ctx, VRC_ERR_ARG, "the adjoint differentiates the default variant only");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     AdjointLaunch A;
@@ -1031,6 +1038,8 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
         return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be a 16-byte aligned device pointer");
     if (params && params->kernel >= 2)
         return fail(ctx, VRC_ERR_ARG, "the server renders with the per-ray kernel (kernel 0 or 1)");
+    if (params && (params->interp || params->preclass))
+        return fail(ctx, VRC_ERR_ARG, "the server renders the default variant only");
     DeviceGuard g(ctx->device);
     const int slot = (int)(s->next_seq % s->max_slots);
     if (!server_slot_free(s, slot)) return fail(ctx, VRC_ERR_BUSY, "all %d slots in flight", s->max_slots);

@@ -137,6 +137,97 @@ __device__ __forceinline__ float tricubic_rep(const ReplView &rp, const int ip[3
     return s;
 }
 
+// Trilinear sample at integer base ip (taps ip .. ip+1, clamped) with fractions f, from the
+// x-replicated float4 volume: entry (ip0 + 1, ip1 + 1 + b, ip2 + 1 + c) for b, c in {1, 2},
+// components y and z (voxels ip0 and ip0 + 1).
+__device__ __forceinline__ float trilinear_rep(const ReplView &rp, const int ip[3],
+                                               const float f[3]) {
+    const long rslice = (long)rp.rnx * rp.rny;
+    const float4 *p0 = rp.base + ((long)(ip[2] + 2) * rp.rny + (ip[1] + 2)) * rp.rnx + (ip[0] + 1);
+    const float4 a = __ldg(p0), b = __ldg(p0 + rp.rnx);
+    const float4 c = __ldg(p0 + rslice), d = __ldg(p0 + rslice + rp.rnx);
+    const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
+    const float r0 = fmaf(f[0], a.z, gx * a.y), r1 = fmaf(f[0], b.z, gx * b.y);
+    const float r2 = fmaf(f[0], c.z, gx * c.y), r3 = fmaf(f[0], d.z, gx * d.y);
+    const float q0 = fmaf(f[1], r1, gy * r0), q1 = fmaf(f[1], r3, gy * r2);
+    return fmaf(f[2], q1, gz * q0);
+}
+
+// Post-classification of value v: u = (v - lo) * du on [0, 255], linear between entries.
+__device__ __forceinline__ float4 tf_classify(const TfView &tf, float v) {
+    const float u = fminf(fmaxf((v - tf.lo) * tf.du, 0.0f), 255.0f);
+    int i0;
+    floor_small(u, i0);
+    i0 = min(i0, 254);
+    const float fu = u - (float)i0;
+    const float4 c0 = __ldg(tf.rgba + i0), dc = __ldg(tf.drgba + i0);
+    return make_float4(fmaf(fu, dc.x, c0.x), fmaf(fu, dc.y, c0.y), fmaf(fu, dc.z, c0.z),
+                       fmaf(fu, dc.w, c0.w));
+}
+
+// Interpolation and classification variants (the paper's Fig. 4 comparison):
+// MODE = interp + 2 * preclass. Post-classification classifies the interpolated value;
+// pre-classification sums the taps' classified rgba with the interpolation weights.
+enum { MODE_CUBIC_POST = 0, MODE_LINEAR_POST = 1, MODE_CUBIC_PRE = 2, MODE_LINEAR_PRE = 3 };
+
+template <int MODE>
+__device__ __forceinline__ float4 sample_rgba(const ReplView &rp, const TfView &tf,
+                                              const int ip[3], const float f[3]) {
+    if constexpr (MODE == MODE_CUBIC_POST) {
+        return tf_classify(tf, tricubic_rep(rp, ip, f));
+    } else if constexpr (MODE == MODE_LINEAR_POST) {
+        return tf_classify(tf, trilinear_rep(rp, ip, f));
+    } else if constexpr (MODE == MODE_CUBIC_PRE) {
+        float wx[4], wy[4], wz[4];
+        bspline_w(f[0], wx);
+        bspline_w(f[1], wy);
+        bspline_w(f[2], wz);
+        const long rslice = (long)rp.rnx * rp.rny;
+        const float4 *p0 =
+            rp.base + ((long)(ip[2] + 1) * rp.rny + (ip[1] + 1)) * rp.rnx + (ip[0] + 1);
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float4 v = __ldg(p0 + c * rslice + b * rp.rnx);
+                const float vals[4] = {v.x, v.y, v.z, v.w};
+                const float wyz = wy[b] * wz[c];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 t = tf_classify(tf, vals[a]);
+                    const float w = wx[a] * wyz;
+                    acc.x = fmaf(w, t.x, acc.x);
+                    acc.y = fmaf(w, t.y, acc.y);
+                    acc.z = fmaf(w, t.z, acc.z);
+                    acc.w = fmaf(w, t.w, acc.w);
+                }
+            }
+        }
+        return acc;
+    } else {
+        const long rslice = (long)rp.rnx * rp.rny;
+        const float4 *p0 =
+            rp.base + ((long)(ip[2] + 2) * rp.rny + (ip[1] + 2)) * rp.rnx + (ip[0] + 1);
+        const float w1[3] = {f[0], f[1], f[2]};
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float4 v = __ldg(p0 + c * rslice + b * rp.rnx);
+                const float wyz = (b ? w1[1] : 1.0f - w1[1]) * (c ? w1[2] : 1.0f - w1[2]);
+                const float4 t0 = tf_classify(tf, v.y), t1 = tf_classify(tf, v.z);
+                const float wa = (1.0f - w1[0]) * wyz, wb = w1[0] * wyz;
+                acc.x = fmaf(wb, t1.x, fmaf(wa, t0.x, acc.x));
+                acc.y = fmaf(wb, t1.y, fmaf(wa, t0.y, acc.y));
+                acc.z = fmaf(wb, t1.z, fmaf(wa, t0.z, acc.z));
+                acc.w = fmaf(wb, t1.w, fmaf(wa, t0.w, acc.w));
+            }
+        }
+        return acc;
+    }
+}
+
 __device__ __forceinline__ int brick_of(const BrickView &bv, const int ip[3]) {
     return ((max(ip[2], 0) >> bv.shift) * bv.nb[1] + (max(ip[1], 0) >> bv.shift)) * bv.nb[0] +
            (max(ip[0], 0) >> bv.shift);
@@ -213,6 +304,7 @@ struct RenderLaunch {
     RaySplit split;                // used by the split render only
     const uint32_t *cells;         // NULL, or the cell transparency mask (with dist)
     int cwx;                       // mask words per row of cells along x
+    int mode;                      // interpolation / classification variant (MODE_*)
 };
 
 // Bit of the cell holding sample base ip (ip in [-1, n-1]); 0: the sample's opacity is zero.

@@ -44,7 +44,8 @@ class vrc_camera(C.Structure):
 
 class vrc_params(C.Structure):
     _fields_ = [("step", C.c_float), ("ert_threshold", C.c_float), ("brick", C.c_int),
-                ("seg_len", C.c_int), ("kernel", C.c_int)]
+                ("seg_len", C.c_int), ("kernel", C.c_int), ("interp", C.c_int),
+                ("preclass", C.c_int)]
 
 
 _lib = None
@@ -126,5 +127,7 @@ def camera_struct(cam) -> vrc_camera:
     return c
 
 
-def params_struct(step=0.5, ert=1.0, brick=0, seg_len=64, kernel=0) -> vrc_params:
-    return vrc_params(float(step), float(ert), int(brick), int(seg_len), int(kernel))
+def params_struct(step=0.5, ert=1.0, brick=0, seg_len=64, kernel=0, interp=0,
+                  preclass=0) -> vrc_params:
+    return vrc_params(float(step), float(ert), int(brick), int(seg_len), int(kernel),
+                      int(interp), int(preclass))

@@ -49,7 +49,30 @@ def test_host_only_calls(lib):
     assert lib.vrc_bricks_build(None, 1, 8, None) == -1
 
 
+def _header_struct(name):
+    # (field name, C type, array length) of `typedef struct { ... } name;` in include/vrc.h
+    text = open(os.path.join(ROOT, "include", "vrc.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, names = decl.split(None, 1)
+        for n in names.split(","):
+            m = re.match(r"\s*(\w+)\s*(?:\[(\d+)\])?", n)
+            fields.append((m.group(1), typ, int(m.group(2) or 1)))
+    return fields
+
+
 def test_struct_layouts_match_header():
-    # vrc_camera: int + 9 floats + float + 2 floats + 2 ints; vrc_params: 2 floats + 3 ints
-    assert C.sizeof(native.vrc_camera) == 4 * (1 + 9 + 1 + 2 + 2)
-    assert C.sizeof(native.vrc_params) == 4 * 5
+    ctype = {"int": C.c_int, "float": C.c_float}
+    for py, name in ((native.vrc_camera, "vrc_camera"), (native.vrc_params, "vrc_params")):
+        hdr = _header_struct(name)
+        got = [(f, t) for f, t in py._fields_]
+        assert [f for f, _ in got] == [f for f, _, _ in hdr], name
+        for (f, t), (_, typ, n) in zip(got, hdr):
+            want = ctype[typ] * n if n > 1 else ctype[typ]
+            assert C.sizeof(t) == C.sizeof(want) and getattr(t, "_type_", t) == getattr(
+                want, "_type_", want), (name, f)

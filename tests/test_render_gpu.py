@@ -433,3 +433,81 @@ def test_cell_mask_zero_runs(R, orc, pattern):
         assert ref.all()
     R.free_tf(tid)
     R.free_volume(vid)
+
+
+# ------------------------------- interpolation / classification variants (the next row 1)
+
+VARIANTS = [(1, 0), (0, 1), (1, 1)]
+
+
+@pytest.mark.parametrize("interp,preclass", VARIANTS)
+@pytest.mark.parametrize("kernel", [0, 1, 6])
+@pytest.mark.parametrize("B", [0, 8])
+def test_variant_parity(R, orc, torch, interp, preclass, kernel, B):
+    """Trilinear and pre-classification variants against the oracle (perspective CT views,
+    ERT 0.999), and skipping bit-identical to no skipping."""
+    vol = _ct_small(seed=15, shape=(44, 52, 60))
+    tf = synth.tf_ct(2)
+    vid = R.upload_volume(vol)
+    if B:
+        R.build_bricks(vid, B)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    for cam in synth.orbit_cameras(43, 2, synth.dims_of(vol), 72, 60):
+        img = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=B, kernel=kernel,
+                       interp=interp, preclass=preclass).cpu().numpy()
+        ref, margin = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=0.999,
+                                 brick=B, return_margin=True, interp=interp, preclass=preclass)
+        _check(img, ref, margin)
+        if B:
+            noesl = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=0, kernel=kernel,
+                             interp=interp, preclass=preclass).cpu().numpy()
+            assert np.array_equal(img, noesl)
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+def test_variants_change_the_image_and_are_rejected_where_unsupported(R, torch):
+    vol = _ct_small(seed=16)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(44, 1, synth.dims_of(vol), 64, 64)[0]
+    base = R.render(vid, tid, cam, ert=0.999, brick=8)
+    for interp, preclass in VARIANTS:
+        img = R.render(vid, tid, cam, ert=0.999, brick=8, interp=interp, preclass=preclass)
+        assert float((img - base).abs().max()) > 1e-3
+    from paper_2005_01442_gb300 import native
+    for kernel in (2, 3, 4, 5):
+        with pytest.raises(native.VrcError):
+            R.render(vid, tid, cam, ert=0.999, brick=8, kernel=kernel, interp=1)
+    with pytest.raises(native.VrcError):
+        R.render(vid, tid, cam, interp=2)
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+def test_variants_rejected_by_adjoint_and_server(R, torch):
+    import ctypes as C
+    from paper_2005_01442_gb300 import native
+    vol = _ct_small(seed=17).astype(np.float32)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(45, 1, synth.dims_of(vol), 16, 16)[0]
+    g = torch.zeros((16, 16, 4), device="cuda")
+    gtf = torch.zeros((256, 4), device="cuda")
+    st = R.lib.vrc_render_backward(R.ctx, vid, tid, C.byref(native.camera_struct(cam)),
+                                   C.byref(native.params_struct(0.5, 1.0, 0, 64, 0, 1, 0)),
+                                   C.c_void_p(g.data_ptr()), C.c_void_p(gtf.data_ptr()), None,
+                                   None)
+    assert st == -1
+    srv = C.c_void_p()
+    native.check(R.ctx, R.lib.vrc_server_create(R.ctx, 4, C.byref(srv)))
+    out = torch.empty((16, 16, 4), device="cuda")
+    t = C.c_longlong()
+    st = R.lib.vrc_server_submit(srv, vid, tid, C.byref(native.camera_struct(cam)),
+                                 C.byref(native.params_struct(0.5, 1.0, 0, 64, 0, 0, 1)),
+                                 C.c_void_p(out.data_ptr()), C.byref(t))
+    assert st == -1
+    R.lib.vrc_server_destroy(srv)
+    R.free_tf(tid)
+    R.free_volume(vid)
