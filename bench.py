@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
-    p.add_argument("--mode", default="render", choices=["render", "serve", "adjoint", "large"])
+    p.add_argument("--mode", default="render",
+                   choices=["render", "serve", "adjoint", "large", "variants"])
     p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
@@ -427,6 +428,36 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def _gauss_blur(a, sigma=1.5, radius=5):
+    import numpy as np
+    x = np.arange(-radius, radius + 1, dtype=np.float64)
+    k = np.exp(-0.5 * (x / sigma) ** 2)
+    k /= k.sum()
+    pad = np.pad(a, radius, mode="reflect")
+    tmp = sum(k[i] * pad[i:i + a.shape[0], :] for i in range(k.size))
+    return sum(k[i] * tmp[:, i:i + a.shape[1]] for i in range(k.size))
+
+
+def image_quality(img, ref):
+    """(PSNR in dB, mean SSIM) of an RGBA image against a reference, values in [0, 1];
+    SSIM with the usual 11-tap Gaussian window (sigma 1.5), K1 = 0.01, K2 = 0.03, averaged
+    over the four channels."""
+    import numpy as np
+    mse = float(np.mean((img - ref) ** 2))
+    psnr = float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    ss = []
+    for ch in range(img.shape[-1]):
+        a, b = img[..., ch], ref[..., ch]
+        ma, mb = _gauss_blur(a), _gauss_blur(b)
+        va = _gauss_blur(a * a) - ma * ma
+        vb = _gauss_blur(b * b) - mb * mb
+        cab = _gauss_blur(a * b) - ma * mb
+        m = ((2 * ma * mb + c1) * (2 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2))
+        ss.append(float(m.mean()))
+    return psnr, float(np.mean(ss))
+
+
 def _timed(torch, fn, reps):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -439,8 +470,10 @@ def _timed(torch, fn, reps):
 
 
 def run_mode(args, torch, R, synth):
-    """--mode serve | adjoint | large: the serving, differentiation and large workloads; one
-    JSON line each (not the headline metric)."""
+    """--mode serve | adjoint | large | variants: the serving, differentiation and large
+    workloads and the interpolation / classification variants; one JSON line each (not the
+    headline metric)."""
+    import numpy as np
     dev = torch.device("cuda", 0)
     if args.mode == "serve":
         specs = [((256, 256, 256), 5), ((400, 512, 512), 3), ((1200, 512, 512), 6)]
@@ -499,6 +532,43 @@ def run_mode(args, torch, R, synth):
             "executed_samples_per_step": executed, "loss": loss,
             "value": executed / ((f_ms + b_ms) / 1e3) / 1e9, "unit": "Gsamples/s",
             "gpu_launches": 8 * args.steps * 3}), flush=True)
+        return
+    if args.mode == "variants":
+        # the paper's Fig. 4 comparison on the headline workload: frame time of each
+        # interpolation / classification variant and its PSNR / SSIM against the tricubic
+        # post-classified image
+        vol = synth.ct_volume()
+        dims = synth.dims_of(vol)
+        cams = synth.orbit_cameras(4, args.cameras, dims, 1024, 1024)
+        vid = R.upload_volume(vol)
+        R.build_bricks(vid, args.brick)
+        tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+        out = torch.empty((len(cams), 1024, 1024, 4), device=dev)
+        rows, ref = [], None
+        for interp, preclass, name in [(0, 0, "tricubic post-classification"),
+                                       (1, 0, "trilinear post-classification"),
+                                       (0, 1, "tricubic pre-classification"),
+                                       (1, 1, "trilinear pre-classification")]:
+            def frames():
+                for i, c in enumerate(cams):
+                    R.render(vid, tid, c, ert=0.999, brick=args.brick, out=out[i],
+                             interp=interp, preclass=preclass)
+            for _ in range(args.warmup):
+                frames()
+            ms = _timed(torch, frames, args.steps) / len(cams)
+            imgs = out[:4].cpu().numpy().astype(np.float64)  # quality on the first 4 frames
+            if ref is None:
+                ref = imgs.copy()
+            q = [image_quality(a, b) for a, b in zip(imgs, ref)]
+            rows.append({"variant": name, "interp": interp, "preclass": preclass,
+                         "ms_per_frame": ms, "mrays_per_s": 1024 * 1024 / (ms / 1e3) / 1e6,
+                         "psnr_db": float(np.mean([x[0] for x in q])),
+                         "ssim": float(np.mean([x[1] for x in q]))})
+        print(json.dumps({
+            "mode": "variants", "metric": "ms per frame; PSNR / SSIM vs tricubic "
+            "post-classification (RGBA, peak 1)", "data": "synthetic",
+            "config": workload_config(args), "variants": rows,
+            "gpu_launches": 4 * (args.warmup + args.steps) * len(cams) * 2}), flush=True)
         return
     if args.mode == "large":
         vol = synth.ct_volume((2000, 512, 512), seed=9)
