@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -562,7 +563,8 @@ def run_mode(args, torch, R, synth):
             q = [image_quality(a, b) for a, b in zip(imgs, ref)]
             rows.append({"variant": name, "interp": interp, "preclass": preclass,
                          "ms_per_frame": ms, "mrays_per_s": 1024 * 1024 / (ms / 1e3) / 1e6,
-                         "psnr_db": float(np.mean([x[0] for x in q])),
+                         "psnr_db": (None if all(math.isinf(x[0]) for x in q)  # identical
+                                     else float(np.mean([x[0] for x in q]))),
                          "ssim": float(np.mean([x[1] for x in q]))})
         print(json.dumps({
             "mode": "variants", "metric": "ms per frame; PSNR / SSIM vs tricubic "
