@@ -32,7 +32,9 @@ class Camera(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("step", C.c_double), ("ert", C.c_double), ("brick", C.c_int),
-                ("interp", C.c_int), ("preclass", C.c_int), ("pad", C.c_int)]
+                ("interp", C.c_int), ("preclass", C.c_int), ("shade", C.c_int),
+                ("pad", C.c_int), ("ka", C.c_double), ("kd", C.c_double), ("ks", C.c_double),
+                ("shininess", C.c_double)]
 
 
 class Ball(C.Structure):
@@ -69,6 +71,7 @@ def lib():
         L.orc_sample_linear.restype = C.c_double
         L.orc_sample_rgba.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double,
                                       ip, ip, vp, C.c_double, C.c_double, dp]
+        L.orc_gradient.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double, dp]
         L.orc_classify.argtypes = [C.c_double, vp, C.c_double, C.c_double, dp]
         L.orc_ray.argtypes = [C.POINTER(Camera), vp, ip, ip, dp, dp, dp, dp]
         L.orc_ray.restype = C.c_int
@@ -151,6 +154,15 @@ def sample_rgba(vol: np.ndarray, p, tf: np.ndarray, lo: float, hi: float, interp
     return np.array(out[:])
 
 
+def gradient(vol: np.ndarray, p) -> np.ndarray:
+    """Gradient of the cubic B-spline field of `vol` (nz, ny, nx) at p = (x, y, z)."""
+    vol = np.ascontiguousarray(vol)
+    nz, ny, nx = vol.shape
+    out = (C.c_double * 3)()
+    lib().orc_gradient(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, *map(float, p), out)
+    return np.array(out[:])
+
+
 def classify(s: float, tf: np.ndarray, lo: float, hi: float) -> np.ndarray:
     tf = np.ascontiguousarray(tf, np.float32)
     out = (C.c_double * 4)()
@@ -218,10 +230,11 @@ def _pix(pixels):
 
 def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
            return_margin=False, return_counts=False, return_executed=False, interp=0,
-           preclass=0):
+           preclass=0, phong=None):
     """FP64 render. Returns float64 (H, W, 4) (or (npix, 4) for a pixel list), plus the ERT
     margins, the (nominal, executed) sample counts and the per-pixel executed samples when
-    asked."""
+    asked. interp / preclass select the variant; phong = (ka, kd, ks, shininess) turns on
+    headlight Blinn-Phong shading (cubic post-classification)."""
     vol = np.ascontiguousarray(vol)
     tf = np.ascontiguousarray(tf, np.float32)
     nz, ny, nx = vol.shape
@@ -235,7 +248,10 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
     margin = np.empty(n, np.float64) if return_margin else None
     counts = np.zeros(2, np.int64)
     expp = np.zeros(n, np.int32) if return_executed else None
-    par = Params(float(step), float(ert), int(brick), int(interp), int(preclass), 0)
+    sh = phong is not None
+    ka, kd, ks, shin = phong if sh else (0.0, 0.0, 0.0, 1.0)
+    par = Params(float(step), float(ert), int(brick), int(interp), int(preclass), int(sh), 0,
+                 float(ka), float(kd), float(ks), float(shin))
     b = None
     if ball is not None:
         b = Ball(1, (C.c_double * 3)(*map(float, ball[0])), float(ball[1]))
@@ -270,7 +286,7 @@ def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, wa
     g = np.ascontiguousarray(np.asarray(g, np.float64).reshape(-1, 4))
     gtf = np.zeros((256, 4), np.float64)
     gvol = np.zeros(vol.shape, np.float64) if want_vol else None
-    par = Params(float(step), float(ert), int(brick), 0, 0, 0)
+    par = Params(float(step), float(ert), int(brick), 0, 0, 0, 0, 0.0, 0.0, 0.0, 1.0)
     rc = lib().orc_render_grad(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
                                float(hi), C.byref(_cam(cam)), C.byref(par), _ptr(occ),
                                _ptr(pix), npix, _ptr(g), _ptr(gtf), _ptr(gvol))

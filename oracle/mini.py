@@ -31,6 +31,19 @@ def beta3(t):
     return out
 
 
+def dbeta3(t):
+    """Derivative of beta3 (odd): -2t + 3t|t|/2 on |t| < 1, -sign(t)(2 - |t|)^2 / 2 on
+    1 <= |t| < 2."""
+    t = np.asarray(t, np.float64)
+    a = np.abs(t)
+    out = np.zeros_like(t)
+    m1 = a < 1.0
+    m2 = (a >= 1.0) & (a < 2.0)
+    out[m1] = -2.0 * t[m1] + 1.5 * t[m1] * a[m1]
+    out[m2] = -np.sign(t[m2]) * (2.0 - a[m2]) ** 2 / 2.0
+    return out
+
+
 def tent(t):
     """Linear B-spline (the trilinear kernel per axis): max(0, 1 - |t|)."""
     return np.maximum(0.0, 1.0 - np.abs(np.asarray(t, np.float64)))
@@ -52,6 +65,15 @@ class Field:
         self.gx = np.arange(-PAD, nx + PAD, dtype=np.float64)
         self.gy = np.arange(-PAD, ny + PAD, dtype=np.float64)
         self.gz = np.arange(-PAD, nz + PAD, dtype=np.float64)
+
+    def gradient(self, p):
+        """Gradient of the cubic field at p (the kernel sum with one factor differentiated)."""
+        bx, by, bz = beta3(p[0] - self.gx), beta3(p[1] - self.gy), beta3(p[2] - self.gz)
+        dx, dy, dz = dbeta3(p[0] - self.gx), dbeta3(p[1] - self.gy), dbeta3(p[2] - self.gz)
+        e = self.ext[..., 0]
+        return np.array([np.einsum("k,j,i,kji->", bz, by, dx, e),
+                         np.einsum("k,j,i,kji->", bz, dy, bx, e),
+                         np.einsum("k,j,i,kji->", dz, by, bx, e)])
 
     def __call__(self, p):
         bx = self.kern(p[0] - self.gx)
@@ -105,10 +127,11 @@ def tf_lookup(s, tf, lo, hi):
     return np.array([np.interp(u, k, tf[:, c].astype(np.float64)) for c in range(4)])
 
 
-def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0):
+def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0, phong=None):
     """(H, W, 4) float64 image: front-to-back compositing over segment midpoints.
     interp 0/1: cubic B-spline / trilinear kernel; preclass 1: classify every voxel, then
-    interpolate the rgba."""
+    interpolate the rgba; phong (ka, kd, ks, shininess): headlight shading by the gradient of
+    the cubic field, softened by eps = 0.01 (hi - lo)."""
     nz, ny, nx = vol.shape
     dims = (nx, ny, nz)
     kernel = "cubic" if interp == 0 else "linear"
@@ -137,6 +160,13 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0):
             for a, b in zip(edges[:-1], edges[1:]):
                 p = o + 0.5 * (a + b) * d
                 rgba = sample(p)
+                if phong is not None:
+                    ka, kd, ks, shin = phong
+                    g = field.gradient(p)
+                    eps = 0.01 * (hi - lo)
+                    nl = abs(float(g @ d)) / math.sqrt(float(g @ g) + eps * eps)
+                    rgba = rgba.copy()
+                    rgba[:3] = rgba[:3] * (ka + kd * nl) + ks * nl ** shin
                 alpha = 1.0 - (1.0 - min(max(rgba[3], 0.0), amax)) ** (b - a)
                 col += trans * alpha * rgba[:3]
                 trans *= 1.0 - alpha

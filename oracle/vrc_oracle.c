@@ -43,6 +43,13 @@
  *              unchanged. Bricks, occupancy and leaping are unchanged (both variants read a
  *              subset of the cubic taps with non-negative weights, so an empty brick still
  *              gives opacity exactly zero).
+ *   shading    (local lighting, Sec. "Methodology") Blinn-Phong with a headlight: light and
+ *              view direction L = -d, so the half vector is L as well. The normal is the
+ *              gradient g of the cubic B-spline field (analytic derivative weights, the same
+ *              64 taps), softened near zero: n.L = |g.L| / sqrt(|g|^2 + eps^2) with eps =
+ *              0.01 (hi - lo) per voxel, so that shading fades out in homogeneous regions
+ *              and never divides by zero. rgb <- rgb (ka + kd n.L) + ks (n.L)^shininess;
+ *              opacity is not changed, so bricks, occupancy and leaping are unaffected.
  *   gradient   reverse mode through compositing, opacity, classification and resampling,
  *              w.r.t. the TF entries and the voxel values (see orc_render_grad). At the kinks
  *              of the opacity clamp (a = 0, a = 1-2^-24) and of the index clamp (u = 0, 255)
@@ -91,7 +98,9 @@ typedef struct {
     int brick;       /* B for ESL; 0 disables */
     int interp;      /* 0: cubic B-spline, 1: trilinear */
     int preclass;    /* 0: post-classification, 1: pre-classification */
+    int shade;       /* 1: Phong shading with a headlight (cubic post-classification only) */
     int pad;
+    double ka, kd, ks, shininess; /* Phong coefficients */
 } orc_params;
 
 static const double ALPHA_MAX = 1.0 - 5.9604644775390625e-08; /* 1 - 2^-24 */
@@ -524,8 +533,44 @@ static double field(const scene_t *S, const double p[3]) {
     return S->par->interp == 1 ? resample_linear(S->vol, p) : resample(S->vol, p);
 }
 
-/* rgba of the sample at p under the scene's interpolation and classification variant. */
-static void sample_rgba(const scene_t *S, const double p[3], double rgba[4]) {
+/* Gradient of the cubic B-spline field at p (per voxel). */
+static void resample_gradient(const orc_volume *v, const double p[3], double gr[3]) {
+    taps_t t;
+    taps_at(p, &t);
+    double dw[3][4];
+    for (int k = 0; k < 3; ++k) orc_bspline_dweights(p[k] - floor(p[k]), dw[k]);
+    gr[0] = gr[1] = gr[2] = 0.0;
+    for (int c = 0; c < 4; ++c)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                const double val = voxel(v, t.base[0] + a, t.base[1] + b, t.base[2] + c);
+                gr[0] += dw[0][a] * t.w[1][b] * t.w[2][c] * val;
+                gr[1] += t.w[0][a] * dw[1][b] * t.w[2][c] * val;
+                gr[2] += t.w[0][a] * t.w[1][b] * dw[2][c] * val;
+            }
+}
+
+void orc_gradient(const void *data, int dtype, int nx, int ny, int nz, double x, double y,
+                  double z, double gr[3]) {
+    orc_volume v = {data, dtype, {nx, ny, nz}};
+    double p[3] = {x, y, z};
+    resample_gradient(&v, p, gr);
+}
+
+/* Blinn-Phong with a headlight (see the header). */
+static void shade(const scene_t *S, const double p[3], const double d[3], double rgba[4]) {
+    double gr[3];
+    resample_gradient(S->vol, p, gr);
+    const double eps = 0.01 * (S->hi - S->lo);
+    const double gl = -(gr[0] * d[0] + gr[1] * d[1] + gr[2] * d[2]);
+    const double nl = fabs(gl) / sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+    const double diff = S->par->ka + S->par->kd * nl;
+    const double spec = S->par->ks * pow(nl, S->par->shininess);
+    for (int q = 0; q < 3; ++q) rgba[q] = rgba[q] * diff + spec;
+}
+
+/* rgba of the sample at p (ray direction d) under the scene's variant. */
+static void sample_rgba(const scene_t *S, const double p[3], const double d[3], double rgba[4]) {
     if (S->par->preclass && !(S->ball && S->ball->enabled)) {
         preclassified_rgba(S->vol, p, S->par->interp, S->tf, S->lo, S->hi, rgba);
         return;
@@ -533,6 +578,7 @@ static void sample_rgba(const scene_t *S, const double p[3], double rgba[4]) {
     class_t c;
     classify(field(S, p), S->tf, S->lo, S->hi, &c);
     memcpy(rgba, c.rgba, sizeof(c.rgba));
+    if (S->par->shade && !(S->ball && S->ball->enabled)) shade(S, p, d, rgba);
 }
 
 /* First sample index past the empty brick b containing sample j, minus a one-sample margin,
@@ -605,7 +651,7 @@ static void render_ray(const scene_t *S, const orc_camera *cam, const int dims[3
             }
         }
         double rgba[4];
-        sample_rgba(S, p, rgba);
+        sample_rgba(S, p, d, rgba);
         double a = clamp_alpha(rgba[3]);
         double alpha = -expm1(dl * log1p(-a));
         for (int q = 0; q < 3; ++q) C[q] += T * alpha * rgba[q];
@@ -645,6 +691,7 @@ int orc_render(const void *data, int dtype, int nx, int ny, int nz, const float 
                long *counts, int *executed_per_pixel) {
     if (!cam || !par || !out || !tf || par->step <= 0.0 || !(hi > lo)) return ORC_EARG;
     if (par->brick > 0 && !occ) return ORC_EARG;
+    if (par->shade && (par->interp != 0 || par->preclass != 0)) return ORC_EARG;
     orc_volume v = {data, dtype, {nx, ny, nz}};
     scene_t S;
     scene_init(&S, &v, ball, tf, lo, hi, par, occ);
@@ -691,7 +738,8 @@ int orc_render_grad(const void *data, int dtype, int nx, int ny, int nz, const f
                     double *grad_tf, double *grad_vol) {
     if (!cam || !par || !g || !grad_tf || par->step <= 0.0 || !(hi > lo)) return ORC_EARG;
     if (par->brick > 0 && !occ) return ORC_EARG;
-    if (par->interp != 0 || par->preclass != 0) return ORC_EARG; /* cubic post only */
+    if (par->interp != 0 || par->preclass != 0 || par->shade != 0)
+        return ORC_EARG; /* cubic post-classification without shading only */
     orc_volume v = {data, dtype, {nx, ny, nz}};
     scene_t S;
     scene_init(&S, &v, NULL, tf, lo, hi, par, occ);

@@ -165,6 +165,93 @@ def test_variant_renders_unchanged_by_leaping(orc, interp, preclass):
         assert np.array_equal(img, ref) and ex < nom
 
 
+# ------------------------------------------------------ shading (the next row 2)
+
+def test_bspline_gradient_is_exact_for_linear_and_quadratic_fields(orc):
+    nz, ny, nx = 9, 10, 11
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lin = (2.0 + 1.5 * x - 0.75 * y + 0.5 * z).astype(np.float32)
+    quad = (0.5 * x * x + y * z).astype(np.float32)
+    rng = np.random.default_rng(21)
+    for _ in range(40):
+        p = rng.uniform([2.0, 2.0, 2.0], [nx - 3.0, ny - 3.0, nz - 3.0])
+        np.testing.assert_allclose(orc.gradient(lin, p), [1.5, -0.75, 0.5], atol=1e-10)
+        # x^2/2 -> (x^2 + 1/3)/2 and yz -> yz under the cubic B-spline: gradient (x, z, y)
+        np.testing.assert_allclose(orc.gradient(quad, p), [p[0], p[2], p[1]], atol=1e-9)
+
+
+def test_bspline_gradient_matches_differences_and_kernel_sum(orc):
+    rng = np.random.default_rng(22)
+    vol = rng.normal(0, 100, (7, 8, 9)).astype(np.float32)
+    field = mini.Field(vol)
+    h = 1e-5
+    for _ in range(30):
+        p = rng.uniform([-0.4, -0.4, -0.4], [8.4, 7.4, 6.4])
+        g = orc.gradient(vol, p)
+        np.testing.assert_allclose(g, field.gradient(p), atol=1e-9)
+        fd = [(orc.sample(vol, p + h * e) - orc.sample(vol, p - h * e)) / (2 * h)
+              for e in np.eye(3)]
+        np.testing.assert_allclose(g, fd, atol=1e-4)
+
+
+def test_phong_closed_forms(orc):
+    # ortho view along +z (light and view along -z); constant table colour and opacity
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, :3] = (0.8, 0.5, 0.2)
+    tf[:, 3] = 0.05
+    ka, kd, ks, shin = 0.3, 0.7, 0.4, 8.0
+    n = 20
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    cam = synth.ortho_z_camera((n, n, n), 6, 6)
+    lo, hi = -100.0, 4000.0
+    # ramp along x: gradient normal to the view, n.L = 0: colour scaled by ka, opacity kept
+    vol = (100.0 + 40.0 * x).astype(np.float32)
+    plain = orc.render(vol, tf, lo, hi, cam, 0.5)
+    lit = orc.render(vol, tf, lo, hi, cam, 0.5, phong=(ka, kd, ks, shin))
+    np.testing.assert_allclose(lit[..., :3], ka * plain[..., :3], atol=1e-12)
+    np.testing.assert_allclose(lit[..., 3], plain[..., 3], atol=1e-15)
+    # ramp along z (slope 40 per voxel), opaque only for values 300..700, i.e. away from the
+    # clamped first and last layers: every contributing sample has n.L = 40 / sqrt(40^2 +
+    # eps^2), so the colour is the shaded table colour times the opacity
+    vol = (100.0 + 40.0 * z).astype(np.float32)
+    tf2 = tf.copy()
+    tf2[:, 3] = 0.0
+    tf2[26:49, 3] = 0.05
+    eps = 0.01 * (hi - lo)
+    nl = 40.0 / math.sqrt(40.0 ** 2 + eps ** 2)
+    lit = orc.render(vol, tf2, lo, hi, cam, 0.5, phong=(ka, kd, ks, shin))
+    ref = orc.render(vol, tf2, lo, hi, cam, 0.5)
+    rgb = np.array([0.8, 0.5, 0.2])
+    assert ref[..., 3].min() > 0.1
+    np.testing.assert_array_equal(lit[..., 3], ref[..., 3])
+    want = (rgb * (ka + kd * nl) + ks * nl ** shin)[None, None, :] * ref[..., 3:4]
+    np.testing.assert_allclose(lit[..., :3], want, atol=1e-12)
+
+
+def test_phong_render_matches_kernel_sum_brute_force(orc):
+    rng = np.random.default_rng(23)
+    vol = rng.integers(0, 4096, (7, 8, 6)).astype(np.uint16)
+    tf = synth.tf_random(5, 6)
+    tf[:, 3] *= 0.6
+    nz, ny, nx = vol.shape
+    ph = (0.25, 0.6, 0.3, 12.0)
+    for cam in _cams_tiny((nx, ny, nz)):
+        a = orc.render(vol, tf, 0.0, 4095.0, cam, 0.45, ert=0.7, phong=ph)
+        b = mini.render(vol, tf, 0.0, 4095.0, cam, 0.45, ert=0.7, phong=ph)
+        assert np.abs(a - b).max() < 1e-11
+
+
+def test_phong_unchanged_by_leaping(orc):
+    vol = synth.ct_volume((30, 34, 38), seed=24)
+    tf = synth.tf_ct()
+    cam = synth.orbit_cameras(25, 1, synth.dims_of(vol), 12, 10)[0]
+    ph = (0.3, 0.7, 0.2, 16.0)
+    ref = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, phong=ph)
+    for B in (4, 8):
+        assert np.array_equal(orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, brick=B,
+                                         phong=ph), ref)
+
+
 # ------------------------------------------------ whole path vs brute force (a3-a9)
 
 def _cams_tiny(dims):
