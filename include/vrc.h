@@ -98,7 +98,13 @@ typedef struct {
  *                  its rgba). The four combinations are the paper's Fig. 4 comparison; the
  *                  variants run with kernel 0, 1 and 6 and in vrc_render_noalloc; the lane-
  *                  group kernels, the server and vrc_render_backward take only 0, 0
- *                  (VRC_ERR_ARG otherwise). */
+ *                  (VRC_ERR_ARG otherwise).
+ *   shade          1 = local lighting (with interp = preclass = 0 only, the same kernels):
+ *                  headlight Blinn-Phong, rgb <- rgb (ka + kd n.L) + ks (n.L)^shininess,
+ *                  with n.L = |g . d| / sqrt(|g|^2 + eps^2), g the gradient of the cubic
+ *                  B-spline field (analytic, from the same 64 taps), d the ray direction and
+ *                  eps = 0.01 (hi - lo) of the transfer function's window. Opacity is not
+ *                  shaded. ka, kd, ks finite and >= 0, shininess finite and > 0. */
 typedef struct {
     float step;
     float ert_threshold;
@@ -107,6 +113,8 @@ typedef struct {
     int kernel;
     int interp;
     int preclass;
+    int shade;
+    float ka, kd, ks, shininess;
 } vrc_params;
 
 /* Creates a context bound to CUDA device `device`. */

@@ -82,7 +82,7 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
                 live = in_occ && (!L.cells || cell_open(L.cells, L.cwx, L.grid.n, ip));
             }
             if (live) {
-                const float4 rgba = sample_rgba<MODE>(L.rep, L.tf, ip, f);
+                const float4 rgba = sample_rgba<MODE>(L.rep, L.tf, ip, f, df, &L.phong);
                 const float alpha = segment_alpha(rgba.w, delta);
                 e0 = alpha * rgba.x;
                 e1 = alpha * rgba.y;

@@ -169,7 +169,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
         if (!done && !idle) {
             // resampling and classification (post: u = (s - lo) * du on [0, 255], linear
             // between entries; or the variant MODE selects)
-            const float4 rgba = sample_rgba<MODE>(rep, tfv, ip, f);
+            const float4 rgba = sample_rgba<MODE>(rep, tfv, ip, f, df, &L.phong);
             const float alpha = segment_alpha(rgba.w, delta);
             const float w = Tr * alpha;
             C0 = fmaf(w, rgba.x, C0);

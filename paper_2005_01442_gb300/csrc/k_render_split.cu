@@ -110,6 +110,7 @@ cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st) {
     case MODE_LINEAR_POST: launch_tail<MODE_LINEAR_POST>(L, ctas, st); break;
     case MODE_CUBIC_PRE: launch_tail<MODE_CUBIC_PRE>(L, ctas, st); break;
     case MODE_LINEAR_PRE: launch_tail<MODE_LINEAR_PRE>(L, ctas, st); break;
+    case MODE_CUBIC_PHONG: launch_tail<MODE_CUBIC_PHONG>(L, ctas, st); break;
     default: launch_tail<MODE_CUBIC_POST>(L, ctas, st);
     }
     return cudaGetLastError();

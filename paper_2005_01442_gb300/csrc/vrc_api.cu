@@ -343,7 +343,15 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     if (p->kernel < 0 || p->kernel > 6) return fail(ctx, VRC_ERR_ARG, "kernel must be 0..6");
     if ((p->interp != 0 && p->interp != 1) || (p->preclass != 0 && p->preclass != 1))
         return fail(ctx, VRC_ERR_ARG, "interp and preclass must be 0 or 1");
-    if ((p->interp || p->preclass) && p->kernel >= 2 && p->kernel <= 5)
+    if (p->shade != 0 && p->shade != 1) return fail(ctx, VRC_ERR_ARG, "shade must be 0 or 1");
+    if (p->shade) {
+        if (p->interp || p->preclass)
+            return fail(ctx, VRC_ERR_ARG, "shading needs interp = 0 and preclass = 0");
+        if (!(p->ka >= 0.0f && p->kd >= 0.0f && p->ks >= 0.0f && isfinite(p->ka) &&
+              isfinite(p->kd) && isfinite(p->ks) && p->shininess > 0.0f && isfinite(p->shininess)))
+            return fail(ctx, VRC_ERR_ARG, "Phong coefficients must be finite, >= 0, shininess > 0");
+    }
+    if ((p->interp || p->preclass || p->shade) && p->kernel >= 2 && p->kernel <= 5)
         return fail(ctx, VRC_ERR_ARG, "the lane-group kernels render the default variant only");
     memset(&L, 0, sizeof(L));
     vrc_status s = build_camera(ctx, cam, L.cam);
@@ -354,10 +362,15 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     L.rep.rny = v->n[1] + 4;
     L.rep.rnz = v->n[2] + 4;
     L.tf = tf_view(*t);
+    L.phong.eps = 0.01f * (t->hi - t->lo);
     for (int k = 0; k < 3; ++k) L.grid.n[k] = v->n[k];
     L.grid.step = p->step;
     L.grid.ert = p->ert_threshold;
-    L.mode = p->interp + 2 * p->preclass;
+    L.mode = p->shade ? MODE_CUBIC_PHONG : p->interp + 2 * p->preclass;
+    L.phong.ka = p->ka;
+    L.phong.kd = p->kd;
+    L.phong.ks = p->ks;
+    L.phong.shininess = p->shininess;
     L.err = ctx->err_word;
     if (p->brick) {
         const uint8_t *occ = nullptr, *dist = nullptr;
@@ -780,7 +793,7 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
         return fail(ctx, VRC_ERR_ARG, "gradient buffers must be 4-byte aligned");
     const int seg = params->seg_len == 0 ? 64 : params->seg_len;
     if (seg < 1 || seg > ADJ_MAX_SEG) return fail(ctx, VRC_ERR_ARG, "seg_len must be 0..128");
-    if (params->interp || params->preclass)
+    if (params->interp || params->preclass || params->shade)
         return fail(ctx, VRC_ERR_ARG, "the adjoint differentiates the default variant only");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1038,7 +1051,7 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
         return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be a 16-byte aligned device pointer");
     if (params && params->kernel >= 2)
         return fail(ctx, VRC_ERR_ARG, "the server renders with the per-ray kernel (kernel 0 or 1)");
-    if (params && (params->interp || params->preclass))
+    if (params && (params->interp || params->preclass || params->shade))
         return fail(ctx, VRC_ERR_ARG, "the server renders the default variant only");
     DeviceGuard g(ctx->device);
     const int slot = (int)(s->next_seq % s->max_slots);

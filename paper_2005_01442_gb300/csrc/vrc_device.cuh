@@ -321,6 +321,15 @@ __device__ __forceinline__ void bspline_w(float f, float w[4]) {
     w[2] = 1.0f - w[0] - w[1] - w[3];                   // partition of unity
 }
 
+// Their derivatives with respect to f.
+__device__ __forceinline__ void bspline_dw(float f, float w[4]) {
+    const float g = 1.0f - f;
+    w[0] = -0.5f * g * g;
+    w[1] = f * fmaf(1.5f, f, -2.0f);
+    w[2] = fmaf(f, fmaf(-1.5f, f, 1.0f), 0.5f);
+    w[3] = 0.5f * f * f;
+}
+
 constexpr float ALPHA_MAX = 0.99999994039535522f;  // 1 - 2^-24
 
 // Opacity of a segment of length delta for table opacity a per unit length.

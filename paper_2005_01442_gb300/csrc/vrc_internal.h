@@ -165,16 +165,86 @@ __device__ __forceinline__ float4 tf_classify(const TfView &tf, float v) {
                        fmaf(fu, dc.w, c0.w));
 }
 
+// Headlight Blinn-Phong coefficients (local lighting): rgb <- rgb (ka + kd n.L) +
+// ks (n.L)^shininess with n.L = |g . d| / sqrt(|g|^2 + eps^2), g the field gradient.
+struct Phong {
+    float ka, kd, ks, shininess, eps;
+};
+
+// Value and gradient of the cubic B-spline at integer base ip with fractions f (derivative
+// weights d/df of the weights, the same 16 float4 rows).
+__device__ __forceinline__ float tricubic_grad_rep(const ReplView &rp, const int ip[3],
+                                                   const float f[3], float g[3]) {
+    float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+    bspline_w(f[0], wx);
+    bspline_w(f[1], wy);
+    bspline_w(f[2], wz);
+    bspline_dw(f[0], dx);
+    bspline_dw(f[1], dy);
+    bspline_dw(f[2], dz);
+    const long rslice = (long)rp.rnx * rp.rny;
+    const float4 *p0 = rp.base + ((long)(ip[2] + 1) * rp.rny + (ip[1] + 1)) * rp.rnx + (ip[0] + 1);
+    float s = 0.0f;
+    g[0] = g[1] = g[2] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 *pc = p0 + c * rslice;
+        float ps = 0.0f, pdx = 0.0f, pdy = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float4 v = __ldg(pc + b * rp.rnx);
+            float r = wx[0] * v.x;
+            r = fmaf(wx[1], v.y, r);
+            r = fmaf(wx[2], v.z, r);
+            r = fmaf(wx[3], v.w, r);
+            float rd = dx[0] * v.x;
+            rd = fmaf(dx[1], v.y, rd);
+            rd = fmaf(dx[2], v.z, rd);
+            rd = fmaf(dx[3], v.w, rd);
+            ps = fmaf(wy[b], r, ps);
+            pdx = fmaf(wy[b], rd, pdx);
+            pdy = fmaf(dy[b], r, pdy);
+        }
+        s = fmaf(wz[c], ps, s);
+        g[0] = fmaf(wz[c], pdx, g[0]);
+        g[1] = fmaf(wz[c], pdy, g[1]);
+        g[2] = fmaf(dz[c], ps, g[2]);
+    }
+    return s;
+}
+
 // Interpolation and classification variants (the paper's Fig. 4 comparison):
 // MODE = interp + 2 * preclass. Post-classification classifies the interpolated value;
 // pre-classification sums the taps' classified rgba with the interpolation weights.
-enum { MODE_CUBIC_POST = 0, MODE_LINEAR_POST = 1, MODE_CUBIC_PRE = 2, MODE_LINEAR_PRE = 3 };
+// MODE_CUBIC_PHONG adds headlight shading to cubic post-classification (d: unit ray
+// direction).
+enum {
+    MODE_CUBIC_POST = 0,
+    MODE_LINEAR_POST = 1,
+    MODE_CUBIC_PRE = 2,
+    MODE_LINEAR_PRE = 3,
+    MODE_CUBIC_PHONG = 4
+};
 
 template <int MODE>
 __device__ __forceinline__ float4 sample_rgba(const ReplView &rp, const TfView &tf,
-                                              const int ip[3], const float f[3]) {
+                                              const int ip[3], const float f[3],
+                                              const float d[3] = nullptr,
+                                              const Phong *ph = nullptr) {
     if constexpr (MODE == MODE_CUBIC_POST) {
         return tf_classify(tf, tricubic_rep(rp, ip, f));
+    } else if constexpr (MODE == MODE_CUBIC_PHONG) {
+        float g[3];
+        float4 c = tf_classify(tf, tricubic_grad_rep(rp, ip, f, g));
+        const float gd = fmaf(g[0], d[0], fmaf(g[1], d[1], g[2] * d[2]));
+        const float gg = fmaf(g[0], g[0], fmaf(g[1], g[1], fmaf(g[2], g[2], ph->eps * ph->eps)));
+        const float nl = fabsf(gd) / sqrtf(gg);
+        const float diff = fmaf(ph->kd, nl, ph->ka);
+        const float spec = ph->ks * exp2f(ph->shininess * log2f(nl));
+        c.x = fmaf(c.x, diff, spec);
+        c.y = fmaf(c.y, diff, spec);
+        c.z = fmaf(c.z, diff, spec);
+        return c;
     } else if constexpr (MODE == MODE_LINEAR_POST) {
         return tf_classify(tf, trilinear_rep(rp, ip, f));
     } else if constexpr (MODE == MODE_CUBIC_PRE) {
@@ -305,6 +375,7 @@ struct RenderLaunch {
     const uint32_t *cells;         // NULL, or the cell transparency mask (with dist)
     int cwx;                       // mask words per row of cells along x
     int mode;                      // interpolation / classification variant (MODE_*)
+    Phong phong;                   // MODE_CUBIC_PHONG only
 };
 
 // Bit of the cell holding sample base ip (ip in [-1, n-1]); 0: the sample's opacity is zero.

@@ -511,3 +511,51 @@ def test_variants_rejected_by_adjoint_and_server(R, torch):
     R.lib.vrc_server_destroy(srv)
     R.free_tf(tid)
     R.free_volume(vid)
+
+
+# --------------------------------------------------- local lighting (the next row 2)
+
+PHONG = (0.3, 0.7, 0.25, 16.0)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 6])
+@pytest.mark.parametrize("B", [0, 8])
+def test_phong_parity(R, orc, torch, kernel, B):
+    """Headlight Blinn-Phong from the B-spline gradient against the oracle; skipping
+    bit-identical to no skipping; opacity equal to the unshaded render."""
+    vol = _ct_small(seed=18, shape=(44, 52, 60))
+    tf = synth.tf_ct(1)
+    vid = R.upload_volume(vol)
+    if B:
+        R.build_bricks(vid, B)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    for cam in synth.orbit_cameras(46, 2, synth.dims_of(vol), 72, 60):
+        img = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=B, kernel=kernel,
+                       phong=PHONG).cpu().numpy()
+        ref, margin = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=0.999,
+                                 brick=B, return_margin=True, phong=PHONG)
+        _check(img, ref, margin)
+        plain = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=B, kernel=kernel)
+        assert np.array_equal(img[..., 3], plain.cpu().numpy()[..., 3])
+        if B:
+            noesl = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=0, kernel=kernel,
+                             phong=PHONG).cpu().numpy()
+            assert np.array_equal(img, noesl)
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+def test_phong_argument_checks(R, torch):
+    from paper_2005_01442_gb300 import native
+    vol = _ct_small(seed=19)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(47, 1, synth.dims_of(vol), 16, 16)[0]
+    bad = [dict(phong=PHONG, interp=1), dict(phong=PHONG, preclass=1),
+           dict(phong=(0.3, 0.7, 0.2, 0.0)), dict(phong=(-0.1, 0.7, 0.2, 8.0)),
+           dict(phong=PHONG, kernel=3)]
+    for kw in bad:
+        with pytest.raises(native.VrcError):
+            R.render(vid, tid, cam, **kw)
+    R.free_tf(tid)
+    R.free_volume(vid)
