@@ -142,17 +142,25 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             break;
         }
         if (SPLIT) {
-            // hand long rays over to the second phase (warp-aggregated queue append)
+            // hand rays over to the second phase (warp-aggregated queue appends): rays with
+            // more than long_len samples left fill the queue from the front, the others from
+            // the back, so that the second phase starts the likely long ones first
             const bool push = !done && j >= jsw;  // (an idle lane hands over from j on)
-            const unsigned pm = __ballot_sync(0xffffffffu, push);
-            if (pm) {
-                const int leader = __ffs(pm) - 1;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(&L.split.head[0], (unsigned)__popc(pm));
-                base = __shfl_sync(0xffffffffu, base, leader);
+            const bool lng = push && (unsigned)(ray.nseg - j) > L.split.long_len;
+            const unsigned pl = __ballot_sync(0xffffffffu, lng);
+            const unsigned ps = __ballot_sync(0xffffffffu, push && !lng);
+            if (pl | ps) {
+                unsigned bl = 0, bs = 0;
+                if (pl && lane == __ffs(pl) - 1) bl = atomicAdd(&L.split.head[0], (unsigned)__popc(pl));
+                if (ps && lane == __ffs(ps) - 1) bs = atomicAdd(&L.split.head[2], (unsigned)__popc(ps));
+                if (pl) bl = __shfl_sync(0xffffffffu, bl, __ffs(pl) - 1);
+                if (ps) bs = __shfl_sync(0xffffffffu, bs, __ffs(ps) - 1);
                 if (push) {
-                    const unsigned idx = base + __popc(pm & ((1u << lane) - 1u));
-                    if (idx < L.split.cap) {  // at most one record per pixel: always true
+                    const unsigned lt = (1u << lane) - 1u;
+                    const unsigned k = lng ? bl + __popc(pl & lt) : bs + __popc(ps & lt);
+                    // at most one record per pixel, so the two ends never meet: always true
+                    if (k < L.split.cap) {
+                        const unsigned idx = lng ? k : L.split.cap - 1u - k;
                         split_store(L.split.rec + (long)idx * SPLIT_REC, rp, j,
                                     py * L.cam.width + px, C0, C1, C2, Tr);
                         done = true;

@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderL
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
     const float inv_step = 1.0f / L.grid.step;
     const long nbricks = ESL ? (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2] : 0;
-    const unsigned total = min(__ldcg(&L.split.head[0]), L.split.cap);  // final: first phase done
+    // final counts (the first phase has finished): front records 0 .. nf-1, then back
+    // records cap-1 down to cap-nb
+    const unsigned nf = __ldcg(&L.split.head[0]), nb = __ldcg(&L.split.head[2]);
+    const unsigned total = min(nf + nb, L.split.cap);
     unsigned long long executed = 0;
     unsigned next = 0, end = 0;  // rays claimed by this group and not yet started
     while (true) {
@@ -52,8 +55,9 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderL
             next = __shfl_sync(gmask, qi, 0, G);
             end = min(next + SPLIT_CLAIM, total);
         }
-        const unsigned qi = next++;
-        if (qi >= total) break;
+        const unsigned c = next++;
+        if (c >= total) break;
+        const unsigned qi = c < nf ? c : L.split.cap - 1u - (c - nf);
         RayPos rp;
         int jlo, pix;
         float RC0, RC1, RC2, RT;

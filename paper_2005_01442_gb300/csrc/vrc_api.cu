@@ -416,7 +416,9 @@ vrc_status launch_render(vrc_ctx *ctx, const vrc_params *params, RenderLaunch &L
     if (k == 6 || (k == 0 && queue_ok)) {
         vrc_status s = split_queue(ctx, st, (size_t)L.cam.width * L.cam.height, L.split);
         if (s != VRC_OK) return s;
-        CK(cudaMemsetAsync(L.split.head, 0, 2 * sizeof(unsigned), st), "split queue reset");
+        L.split.long_len = (unsigned)(0.75f * (L.grid.n[0] + L.grid.n[1] + L.grid.n[2]) / 3.0f /
+                                      L.grid.step);
+        CK(cudaMemsetAsync(L.split.head, 0, 3 * sizeof(unsigned), st), "split queue reset");
         CK(launch_render_split(L, st), "render launch");
     } else if (k >= 2 && k <= 5) {
         CK(launch_render_warp(L, lanes_of(k), st), "render launch");

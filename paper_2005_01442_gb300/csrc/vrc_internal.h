@@ -316,9 +316,10 @@ __device__ __forceinline__ int octant_of(const float df[3]) {
 constexpr int SPLIT_G = 8;
 constexpr int SPLIT_J0 = 0;  // a multiple of SPLIT_G
 struct RaySplit {
-    unsigned *head;  // NULL: no split; else [records pushed, records claimed by the second phase]
-    float4 *rec;     // SPLIT_REC float4 per queued ray (split_store)
-    unsigned cap;    // records the queue holds (>= the image's pixels)
+    unsigned *head;     // [records at the front, records claimed, records at the back]
+    float4 *rec;        // SPLIT_REC float4 per queued ray (split_store)
+    unsigned cap;       // records the queue holds (>= the image's pixels)
+    unsigned long_len;  // rays with more samples left go to the front (claimed first)
 };
 constexpr int SPLIT_REC = 7;
 
