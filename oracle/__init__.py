@@ -33,7 +33,7 @@ class Camera(C.Structure):
 class Params(C.Structure):
     _fields_ = [("step", C.c_double), ("ert", C.c_double), ("brick", C.c_int),
                 ("interp", C.c_int), ("preclass", C.c_int), ("shade", C.c_int),
-                ("pad", C.c_int), ("ka", C.c_double), ("kd", C.c_double), ("ks", C.c_double),
+                ("preint", C.c_int), ("ka", C.c_double), ("kd", C.c_double), ("ks", C.c_double),
                 ("shininess", C.c_double)]
 
 
@@ -72,6 +72,8 @@ def lib():
         L.orc_sample_rgba.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double,
                                       ip, ip, vp, C.c_double, C.c_double, dp]
         L.orc_gradient.argtypes = [vp, ip, ip, ip, ip, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_preint_table.argtypes = [vp, C.c_double, vp]
+        L.orc_preint_table.restype = ip
         L.orc_classify.argtypes = [C.c_double, vp, C.c_double, C.c_double, dp]
         L.orc_ray.argtypes = [C.POINTER(Camera), vp, ip, ip, dp, dp, dp, dp]
         L.orc_ray.restype = C.c_int
@@ -154,6 +156,16 @@ def sample_rgba(vol: np.ndarray, p, tf: np.ndarray, lo: float, hi: float, interp
     return np.array(out[:])
 
 
+def preint_table(tf: np.ndarray, step: float) -> np.ndarray:
+    """(256, 256, 4) pre-integration table (front entry, back entry; associated rgb,
+    opacity) for slabs of length `step`."""
+    tf = np.ascontiguousarray(tf, np.float32)
+    out = np.empty((256, 256, 4), np.float64)
+    if lib().orc_preint_table(_ptr(tf), float(step), _ptr(out)) != 0:
+        raise ValueError("orc_preint_table failed")
+    return out
+
+
 def gradient(vol: np.ndarray, p) -> np.ndarray:
     """Gradient of the cubic B-spline field of `vol` (nz, ny, nx) at p = (x, y, z)."""
     vol = np.ascontiguousarray(vol)
@@ -230,11 +242,12 @@ def _pix(pixels):
 
 def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
            return_margin=False, return_counts=False, return_executed=False, interp=0,
-           preclass=0, phong=None):
+           preclass=0, phong=None, preint=0):
     """FP64 render. Returns float64 (H, W, 4) (or (npix, 4) for a pixel list), plus the ERT
     margins, the (nominal, executed) sample counts and the per-pixel executed samples when
     asked. interp / preclass select the variant; phong = (ka, kd, ks, shininess) turns on
-    headlight Blinn-Phong shading (cubic post-classification)."""
+    headlight Blinn-Phong shading (cubic post-classification); preint 1 composites slabs
+    between consecutive samples through the pre-integrated table (no skipping)."""
     vol = np.ascontiguousarray(vol)
     tf = np.ascontiguousarray(tf, np.float32)
     nz, ny, nx = vol.shape
@@ -250,8 +263,8 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
     expp = np.zeros(n, np.int32) if return_executed else None
     sh = phong is not None
     ka, kd, ks, shin = phong if sh else (0.0, 0.0, 0.0, 1.0)
-    par = Params(float(step), float(ert), int(brick), int(interp), int(preclass), int(sh), 0,
-                 float(ka), float(kd), float(ks), float(shin))
+    par = Params(float(step), float(ert), int(brick), int(interp), int(preclass), int(sh),
+                 int(preint), float(ka), float(kd), float(ks), float(shin))
     b = None
     if ball is not None:
         b = Ball(1, (C.c_double * 3)(*map(float, ball[0])), float(ball[1]))

@@ -50,6 +50,16 @@
  *              0.01 (hi - lo) per voxel, so that shading fades out in homogeneous regions
  *              and never divides by zero. rgb <- rgb (ka + kd n.L) + ks (n.L)^shininess;
  *              opacity is not changed, so bricks, occupancy and leaping are unaffected.
+ *   preint     (pre-integrated classification) the ray is composited slab by slab between
+ *              consecutive samples j-1, j (length d = m_j - m_{j-1}) instead of sample by
+ *              sample. A slab's (associated colour, opacity) comes from a 256 x 256 table
+ *              indexed by the clamped table coordinates u of its two samples, bilinear in
+ *              both; entry (i, k) integrates the table along the linear ramp of u from i to
+ *              k over the length ds by PREINT_K equal sub-steps (midpoint rule, each with the
+ *              opacity correction of reading 'opacity'). A slab shorter than ds (the last)
+ *              takes alpha' = 1 - (1 - alpha)^(d/ds) and colour C alpha'/alpha. Cubic post-
+ *              classification without shading; no skipping (a skipped sample's value would
+ *              be needed by its two slabs).
  *   gradient   reverse mode through compositing, opacity, classification and resampling,
  *              w.r.t. the TF entries and the voxel values (see orc_render_grad). At the kinks
  *              of the opacity clamp (a = 0, a = 1-2^-24) and of the index clamp (u = 0, 255)
@@ -99,9 +109,11 @@ typedef struct {
     int interp;      /* 0: cubic B-spline, 1: trilinear */
     int preclass;    /* 0: post-classification, 1: pre-classification */
     int shade;       /* 1: Phong shading with a headlight (cubic post-classification only) */
-    int pad;
+    int preint;      /* 1: pre-integrated classification (cubic post, no skipping) */
     double ka, kd, ks, shininess; /* Phong coefficients */
 } orc_params;
+
+#define PREINT_K 32 /* sub-steps of the pre-integration rule */
 
 static const double ALPHA_MAX = 1.0 - 5.9604644775390625e-08; /* 1 - 2^-24 */
 
@@ -257,6 +269,50 @@ void orc_classify(double s, const float *tf, double lo, double hi, double rgba[4
 }
 
 static double clamp_alpha(double a) { return a < 0.0 ? 0.0 : (a > ALPHA_MAX ? ALPHA_MAX : a); }
+
+/* Pre-integration table for slab length ds: out[(i * 256 + k) * 4 + q], i the front entry,
+ * k the back entry; q = 0..2 associated colour, 3 opacity. */
+int orc_preint_table(const float *tf, double ds, double *out) {
+    if (!tf || !out || !(ds > 0.0)) return -1;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < 256; ++i)
+        for (int k = 0; k < 256; ++k) {
+            double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
+            for (int n = 0; n < PREINT_K; ++n) {
+                const double u = i + (k - i) * (n + 0.5) / PREINT_K;
+                int i0 = (int)floor(u);
+                if (i0 > 254) i0 = 254;
+                const double f = u - i0;
+                double rgba[4];
+                for (int q = 0; q < 4; ++q)
+                    rgba[q] = (1.0 - f) * (double)tf[4 * i0 + q] + f * (double)tf[4 * (i0 + 1) + q];
+                const double a = rgba[3] < 0.0 ? 0.0 : (rgba[3] > ALPHA_MAX ? ALPHA_MAX : rgba[3]);
+                const double alpha = -expm1(ds / PREINT_K * log1p(-a));
+                for (int q = 0; q < 3; ++q) C[q] += T * alpha * rgba[q];
+                T *= 1.0 - alpha;
+            }
+            double *e = out + ((long)i * 256 + k) * 4;
+            e[0] = C[0];
+            e[1] = C[1];
+            e[2] = C[2];
+            e[3] = 1.0 - T;
+        }
+    return 0;
+}
+
+/* Bilinear lookup of the table at clamped coordinates (uf, ub) in [0, 255]. */
+static void preint_lookup(const double *tab, double uf, double ub, double out[4]) {
+    int i0 = (int)floor(uf), k0 = (int)floor(ub);
+    if (i0 > 254) i0 = 254;
+    if (k0 > 254) k0 = 254;
+    const double fi = uf - i0, fk = ub - k0;
+    for (int q = 0; q < 4; ++q) {
+        const double a = tab[((long)i0 * 256 + k0) * 4 + q], b = tab[((long)i0 * 256 + k0 + 1) * 4 + q];
+        const double c = tab[((long)(i0 + 1) * 256 + k0) * 4 + q];
+        const double d = tab[((long)(i0 + 1) * 256 + k0 + 1) * 4 + q];
+        out[q] = (1.0 - fi) * ((1.0 - fk) * a + fk * b) + fi * ((1.0 - fk) * c + fk * d);
+    }
+}
 
 /* Pre-classification: the taps' classified rgba, summed with the interpolation weights. */
 static void preclassified_rgba(const orc_volume *v, const double p[3], int interp,
@@ -490,6 +546,7 @@ typedef struct {
     const orc_params *par;
     const uint8_t *occ; /* NULL disables ESL */
     long nb[3];
+    const double *preint_tab; /* NULL unless pre-integrated classification */
 } scene_t;
 
 /* Brick holding floor(p) (clamped to the brick grid). */
@@ -637,6 +694,39 @@ static void render_ray(const scene_t *S, const orc_camera *cam, const int dims[3
     st->nominal = g.nseg;
     double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
     const double thr = S->par->ert;
+    if (S->preint_tab) { /* slab by slab between consecutive samples (no skipping) */
+        double u_prev = 0.0, dl_prev = 0.0;
+        for (long j = 0; j < g.nseg; ++j) {
+            double m, dl, p[3];
+            segment(&g, j, &m, &dl);
+            point_at(pin, d, m, p);
+            class_t c;
+            classify(field(S, p), S->tf, S->lo, S->hi, &c);
+            st->executed++;
+            if (j > 0) {
+                double e[4];
+                preint_lookup(S->preint_tab, u_prev, c.u, e);
+                double alpha = e[3];
+                const double len = 0.5 * (dl_prev + dl); /* distance between the samples */
+                if (len != g.ds && alpha > 0.0) {
+                    const double a2 = -expm1(len / g.ds * log1p(-alpha));
+                    for (int q = 0; q < 3; ++q) e[q] *= a2 / alpha;
+                    alpha = a2;
+                }
+                for (int q = 0; q < 3; ++q) C[q] += T * e[q];
+                T *= 1.0 - alpha;
+                if (thr < 1.0) {
+                    double mg = fabs((1.0 - T) - thr);
+                    if (mg < *margin) *margin = mg;
+                    if (1.0 - T > thr) break;
+                }
+            }
+            u_prev = c.u;
+            dl_prev = dl;
+        }
+        out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
+        return;
+    }
     long j = 0;
     while (j < g.nseg) {
         double m, dl, p[3];
@@ -676,6 +766,7 @@ static void scene_init(scene_t *S, const orc_volume *v, const orc_ball *ball, co
     S->hi = hi;
     S->par = par;
     S->occ = (par->brick > 0) ? occ : NULL;
+    S->preint_tab = NULL;
     for (int k = 0; k < 3; ++k) S->nb[k] = par->brick > 0 ? nbricks_axis(v->n[k], par->brick) : 1;
 }
 
@@ -692,9 +783,18 @@ int orc_render(const void *data, int dtype, int nx, int ny, int nz, const float 
     if (!cam || !par || !out || !tf || par->step <= 0.0 || !(hi > lo)) return ORC_EARG;
     if (par->brick > 0 && !occ) return ORC_EARG;
     if (par->shade && (par->interp != 0 || par->preclass != 0)) return ORC_EARG;
+    if (par->preint && (par->interp || par->preclass || par->shade || par->brick > 0 || ball))
+        return ORC_EARG;
     orc_volume v = {data, dtype, {nx, ny, nz}};
     scene_t S;
     scene_init(&S, &v, ball, tf, lo, hi, par, occ);
+    double *tab = NULL;
+    if (par->preint) {
+        tab = (double *)malloc(sizeof(double) * 256 * 256 * 4);
+        if (!tab) return ORC_EARG;
+        orc_preint_table(tf, par->step, tab);
+        S.preint_tab = tab;
+    }
     int dims[3] = {nx, ny, nz};
     long n = pix ? npix : (long)cam->width * cam->height;
     long nominal = 0, executed = 0;
@@ -714,6 +814,7 @@ int orc_render(const void *data, int dtype, int nx, int ny, int nz, const float 
         counts[0] = nominal;
         counts[1] = executed;
     }
+    free(tab);
     return ORC_OK;
 }
 

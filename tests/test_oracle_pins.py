@@ -252,6 +252,79 @@ def test_phong_unchanged_by_leaping(orc):
                                          phong=ph), ref)
 
 
+# ------------------------------------------- pre-integrated classification (next row 3)
+
+def test_preint_table_closed_forms_and_brute_force(orc):
+    # constant table: every entry is the constant medium over ds; a random table against the
+    # vectorised NumPy rule and an entry-by-entry Python loop
+    tf = np.zeros((256, 4), np.float32)
+    tf[:] = (0.6, 0.3, 0.9, 0.2)
+    tab = orc.preint_table(tf, 0.5)
+    a = 1.0 - (1.0 - np.float64(np.float32(0.2))) ** 0.5
+    np.testing.assert_allclose(tab[..., 3], a, atol=1e-15)
+    np.testing.assert_allclose(tab[..., :3],
+                               np.broadcast_to(np.array([0.6, 0.3, 0.9], np.float32) * a,
+                                               tab[..., :3].shape), atol=1e-15)
+    tf = synth.tf_random(31, 6)
+    tab = orc.preint_table(tf, 0.37)
+    np.testing.assert_allclose(tab, mini.preint_table(tf, 0.37), atol=1e-13)
+    for i, k in [(0, 255), (17, 201), (200, 3), (128, 128)]:
+        col, trans = np.zeros(3), 1.0
+        for n in range(32):
+            u = i + (k - i) * (n + 0.5) / 32
+            i0 = min(int(math.floor(u)), 254)
+            f = u - i0
+            rgba = (1 - f) * tf[i0].astype(np.float64) + f * tf[i0 + 1].astype(np.float64)
+            al = 1.0 - (1.0 - min(max(rgba[3], 0.0), 1.0 - 2.0 ** -24)) ** (0.37 / 32)
+            col += trans * al * rgba[:3]
+            trans *= 1.0 - al
+        np.testing.assert_allclose(tab[i, k], np.append(col, 1.0 - trans), atol=1e-14)
+
+
+def test_preint_constant_medium_spans_first_to_last_sample(orc):
+    # a constant volume and table: each slab is the constant medium over the distance between
+    # its two samples, so the opacity is that of the length from the first to the last sample
+    n = 16
+    vol = np.full((n, n, n), 1000, np.uint16)
+    tf = np.zeros((256, 4), np.float32)
+    tf[:] = (0.2, 0.7, 0.4, 0.1)
+    cam = synth.ortho_z_camera((n, n, n), 4, 4)  # rays along z through 16 voxels
+    img = orc.render(vol, tf, 0.0, 4095.0, cam, 0.5, preint=1)
+    length = 16.0 - 0.5  # 32 segments of 0.5: midpoints 0.25 .. 15.75 from the entry
+    a = np.float64(np.float32(0.1))
+    np.testing.assert_allclose(img[..., 3], 1.0 - (1.0 - a) ** length, atol=1e-12)
+    np.testing.assert_allclose(img[..., :3], np.array([0.2, 0.7, 0.4], np.float32) * img[..., 3:4],
+                               atol=1e-12)
+
+
+def test_preint_catches_a_thin_feature_that_sampling_misses(orc):
+    # a ramp of 100 values per voxel sampled every half voxel (u jumps ~3.1 entries per
+    # sample) and a table opaque only around one entry: samples step over it, slabs do not
+    n = 24
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vol = (200 + 100 * z).astype(np.uint16)
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, :3] = 1.0
+    tf[100, 3] = 0.9
+    cam = synth.ortho_z_camera((n, n, n), 3, 3)
+    post = orc.render(vol, tf, 0.0, 4095.0, cam, 0.5)
+    pre = orc.render(vol, tf, 0.0, 4095.0, cam, 0.5, preint=1)
+    assert pre[..., 3].min() > 5.0 * post[..., 3].max() and pre[..., 3].min() > 0.01
+
+
+def test_preint_render_matches_numpy_brute_force(orc):
+    rng = np.random.default_rng(32)
+    vol = rng.integers(0, 4096, (7, 8, 6)).astype(np.uint16)
+    tf = synth.tf_random(5, 6)
+    tf[:, 3] *= 0.6
+    nz, ny, nx = vol.shape
+    for cam in _cams_tiny((nx, ny, nz)):
+        for step, ert in [(0.5, 1.0), (0.43, 0.6)]:
+            a = orc.render(vol, tf, 0.0, 4095.0, cam, step, ert=ert, preint=1)
+            b = mini.render(vol, tf, 0.0, 4095.0, cam, step, ert=ert, preint=1)
+            assert np.abs(a - b).max() < 1e-11
+
+
 # ------------------------------------------------ whole path vs brute force (a3-a9)
 
 def _cams_tiny(dims):
