@@ -546,16 +546,20 @@ def run_mode(args, torch, R, synth):
         tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
         out = torch.empty((len(cams), 1024, 1024, 4), device=dev)
         rows, ref = [], None
-        for interp, preclass, phong, name in [
-                (0, 0, None, "tricubic post-classification"),
-                (1, 0, None, "trilinear post-classification"),
-                (0, 1, None, "tricubic pre-classification"),
-                (1, 1, None, "trilinear pre-classification"),
-                (0, 0, (0.3, 0.7, 0.25, 16.0), "tricubic post-classification + Phong")]:
+        for interp, preclass, phong, preint, name in [
+                (0, 0, None, 0, "tricubic post-classification"),
+                (1, 0, None, 0, "trilinear post-classification"),
+                (0, 1, None, 0, "tricubic pre-classification"),
+                (1, 1, None, 0, "trilinear pre-classification"),
+                (0, 0, (0.3, 0.7, 0.25, 16.0), 0, "tricubic post-classification + Phong"),
+                (0, 0, None, 0, "tricubic post-classification, no skipping"),
+                (0, 0, None, 1, "pre-integrated (slabs), no skipping")]:
+            brick = 0 if "no skipping" in name else args.brick
+
             def frames():
                 for i, c in enumerate(cams):
-                    R.render(vid, tid, c, ert=0.999, brick=args.brick, out=out[i],
-                             interp=interp, preclass=preclass, phong=phong)
+                    R.render(vid, tid, c, ert=0.999, brick=brick, out=out[i], interp=interp,
+                             preclass=preclass, phong=phong, preint=preint)
             for _ in range(args.warmup):
                 frames()
             ms = _timed(torch, frames, args.steps) / len(cams)
@@ -564,7 +568,7 @@ def run_mode(args, torch, R, synth):
                 ref = imgs.copy()
             q = [image_quality(a, b) for a, b in zip(imgs, ref)]
             rows.append({"variant": name, "interp": interp, "preclass": preclass,
-                         "phong": phong,
+                         "phong": phong, "preint": preint, "brick": brick,
                          "ms_per_frame": ms, "mrays_per_s": 1024 * 1024 / (ms / 1e3) / 1e6,
                          "psnr_db": (None if all(math.isinf(x[0]) for x in q)  # identical
                                      else float(np.mean([x[0] for x in q]))),
@@ -573,7 +577,7 @@ def run_mode(args, torch, R, synth):
             "mode": "variants", "metric": "ms per frame; PSNR / SSIM vs tricubic "
             "post-classification (RGBA, peak 1)", "data": "synthetic",
             "config": workload_config(args), "variants": rows,
-            "gpu_launches": 5 * (args.warmup + args.steps) * len(cams) * 2}), flush=True)
+            "gpu_launches": 7 * (args.warmup + args.steps) * len(cams) * 2}), flush=True)
         return
     if args.mode == "large":
         vol = synth.ct_volume((2000, 512, 512), seed=9)

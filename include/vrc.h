@@ -104,7 +104,18 @@ typedef struct {
  *                  with n.L = |g . d| / sqrt(|g|^2 + eps^2), g the gradient of the cubic
  *                  B-spline field (analytic, from the same 64 taps), d the ray direction and
  *                  eps = 0.01 (hi - lo) of the transfer function's window. Opacity is not
- *                  shaded. ka, kd, ks finite and >= 0, shininess finite and > 0. */
+ *                  shaded. ka, kd, ks finite and >= 0, shininess finite and > 0.
+ *   preint         1 = pre-integrated classification: the ray is composited slab by slab
+ *                  between consecutive samples through a 256 x 256 table of slab colour and
+ *                  opacity for the step (the table integrated along the linear ramp between
+ *                  the two samples' table coordinates, 32 sub-steps, looked up bilinearly;
+ *                  the shorter last slab takes the opacity correction). Cubic post-
+ *                  classification without shading and without skipping (brick = 0);
+ *                  kernel 0 or 1 (both run the per-ray kernel); vrc_render and
+ *                  vrc_render_host only. The context builds the table (1 MB per transfer
+ *                  function) on first use and again when the step changes; renders with
+ *                  different steps and one transfer function must not overlap on
+ *                  different streams. */
 typedef struct {
     float step;
     float ert_threshold;
@@ -115,6 +126,7 @@ typedef struct {
     int preclass;
     int shade;
     float ka, kd, ks, shininess;
+    int preint;
 } vrc_params;
 
 /* Creates a context bound to CUDA device `device`. */

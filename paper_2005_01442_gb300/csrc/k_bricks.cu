@@ -416,6 +416,42 @@ cudaError_t launch_cellmask(const VolView &v, const uint8_t *zrun_dev, float lo,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------- pre-integration table ------
+// Entry (i, k) for slabs of length ds: the table composited along the linear ramp of the index
+// from i (front sample) to k (back sample) by PREINT_K equal sub-steps (midpoint rule, each
+// with the opacity correction alpha = 1 - (1 - a)^(ds / PREINT_K)); (associated rgb, opacity).
+// Computed in double (65536 entries, 32 sub-steps: negligible), stored as float4.
+__global__ void preint_table_kernel(const float4 *__restrict__ rgba, float ds,
+                                    float4 *__restrict__ tab) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 256 * 256) return;
+    const int i = e >> 8, k = e & 255;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, T = 1.0;
+    const double amax = 1.0 - 5.9604644775390625e-08;
+    for (int n = 0; n < PREINT_K; ++n) {
+        const double u = i + (k - i) * (n + 0.5) / PREINT_K;
+        int i0 = (int)floor(u);
+        i0 = i0 > 254 ? 254 : i0;
+        const double f = u - i0;
+        const float4 a = rgba[i0], b = rgba[i0 + 1];
+        const double r = (1.0 - f) * a.x + f * b.x, g = (1.0 - f) * a.y + f * b.y;
+        const double bl = (1.0 - f) * a.z + f * b.z;
+        double al = (1.0 - f) * a.w + f * b.w;
+        al = al < 0.0 ? 0.0 : (al > amax ? amax : al);
+        const double alpha = -expm1((double)ds / PREINT_K * log1p(-al));
+        c0 += T * alpha * r;
+        c1 += T * alpha * g;
+        c2 += T * alpha * bl;
+        T *= 1.0 - alpha;
+    }
+    tab[e] = make_float4((float)c0, (float)c1, (float)c2, (float)(1.0 - T));
+}
+
+cudaError_t launch_preint_table(const float4 *rgba, float ds, float4 *tab, cudaStream_t st) {
+    preint_table_kernel<<<256, 256, 0, st>>>(rgba, ds, tab);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- empty-box distance (leaping) ----
 // For each of the 8 direction octants s = (sx, sy, sz) in {+1, -1}^3 and each brick b:
 // dist[oct][b] = 0 for an occupied brick, else the smallest r >= 1 such that the forward box

@@ -74,6 +74,8 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     bool queued = false;
     int j = 0;
     const int jsw = SPLIT ? SPLIT_J0 : 0x7fffffff;  // hand-over index (SPLIT)
+    float u_prev = 0.0f, dl_prev = 0.0f;  // previous sample (MODE_PREINT)
+    bool have_prev = false;
     while (true) {
         // advance this lane to its next sample to composite; a lane that has skipped
         // SKIP_PER_STEP clear cells sits this step out (idle), so that long clear runs of
@@ -174,6 +176,34 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
         if (__all_sync(0xffffffffu, done)) break;
         // a first phase that hands every ray over at its first sample composites nothing
         if constexpr (SPLIT && SPLIT_J0 == 0) continue;
+        if constexpr (MODE == MODE_PREINT) {
+            // slab between the previous sample and this one, through the pre-integration
+            // table (no skipping in this mode: every sample of the ray is visited)
+            if (!done) {
+                const float u = fminf(fmaxf((tricubic_rep(rep, ip, f) - tfv.lo) * tfv.du, 0.0f),
+                                      255.0f);
+                if (have_prev) {
+                    float4 e = preint_lookup(L.preint, u_prev, u);
+                    const float len = 0.5f * (dl_prev + delta);  // distance between the samples
+                    if (len != step && e.w > 0.0f) {
+                        const float a2 = segment_alpha(e.w, len / step);
+                        const float sc = a2 / e.w;
+                        e = make_float4(e.x * sc, e.y * sc, e.z * sc, a2);
+                    }
+                    C0 = fmaf(Tr, e.x, C0);
+                    C1 = fmaf(Tr, e.y, C1);
+                    C2 = fmaf(Tr, e.z, C2);
+                    Tr = Tr - Tr * e.w;
+                    if (1.0f - Tr > thr) done = true;
+                }
+                u_prev = u;
+                dl_prev = delta;
+                have_prev = true;
+                ++executed;
+                ++j;
+            }
+            continue;
+        }
         if (!done && !idle) {
             // resampling and classification (post: u = (s - lo) * du on [0, 255], linear
             // between entries; or the variant MODE selects)

@@ -27,6 +27,7 @@ cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st) {
     case MODE_CUBIC_PRE: launch_mode<MODE_CUBIC_PRE>(L, grid, st); break;
     case MODE_LINEAR_PRE: launch_mode<MODE_LINEAR_PRE>(L, grid, st); break;
     case MODE_CUBIC_PHONG: launch_mode<MODE_CUBIC_PHONG>(L, grid, st); break;
+    case MODE_PREINT: launch_mode<MODE_PREINT>(L, grid, st); break;
     default: launch_mode<MODE_CUBIC_POST>(L, grid, st);
     }
     return cudaGetLastError();

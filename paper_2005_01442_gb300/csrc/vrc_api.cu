@@ -54,6 +54,9 @@ struct Tf {
     int *prefix = nullptr;    // 257
     uint8_t *zrun = nullptr;  // 256: run id of each zero-opacity entry (0: non-zero entry)
     unsigned version = 0;
+    float4 *preint = nullptr;    // 256 x 256 pre-integration table, built on first use
+    float preint_step = -1.0f;   // the step it was built for
+    unsigned preint_version = 0; // the table version it was built from
 };
 
 int slot_of(int B) { return B == 16 ? 1 : 0; }
@@ -143,6 +146,7 @@ void free_tf(Tf &t) {
     cudaFree(t.drgba);
     cudaFree(t.prefix);
     cudaFree(t.zrun);
+    cudaFree(t.preint);
 }
 
 bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
@@ -353,6 +357,11 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     }
     if ((p->interp || p->preclass || p->shade) && p->kernel >= 2 && p->kernel <= 5)
         return fail(ctx, VRC_ERR_ARG, "the lane-group kernels render the default variant only");
+    if (p->preint != 0 && p->preint != 1) return fail(ctx, VRC_ERR_ARG, "preint must be 0 or 1");
+    if (p->preint && (p->interp || p->preclass || p->shade || p->brick != 0 || p->kernel > 1))
+        return fail(ctx, VRC_ERR_ARG,
+                    "pre-integration needs cubic post-classification, no shading, brick 0 and "
+                    "kernel 0 or 1");
     memset(&L, 0, sizeof(L));
     vrc_status s = build_camera(ctx, cam, L.cam);
     if (s != VRC_OK) return s;
@@ -366,7 +375,16 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     for (int k = 0; k < 3; ++k) L.grid.n[k] = v->n[k];
     L.grid.step = p->step;
     L.grid.ert = p->ert_threshold;
-    L.mode = p->shade ? MODE_CUBIC_PHONG : p->interp + 2 * p->preclass;
+    L.mode = p->preint ? MODE_PREINT : p->shade ? MODE_CUBIC_PHONG : p->interp + 2 * p->preclass;
+    if (p->preint) {
+        if (!t->preint) CK(cudaMalloc(&t->preint, 256 * 256 * sizeof(float4)), "cudaMalloc(preint)");
+        if (t->preint_step != p->step || t->preint_version != t->version) {
+            CK(launch_preint_table(t->rgba, p->step, t->preint, st), "pre-integration launch");
+            t->preint_step = p->step;
+            t->preint_version = t->version;
+        }
+        L.preint = t->preint;
+    }
     L.phong.ka = p->ka;
     L.phong.kd = p->kd;
     L.phong.ks = p->ks;
@@ -413,6 +431,10 @@ vrc_status split_queue(vrc_ctx *ctx, cudaStream_t st, size_t need, RaySplit &q) 
 vrc_status launch_render(vrc_ctx *ctx, const vrc_params *params, RenderLaunch &L,
                          cudaStream_t st, bool queue_ok = true) {
     const int k = params->kernel;
+    if (params->preint) {
+        CK(launch_render_ray(L, st), "render launch");  // the per-ray kernel only
+        return VRC_OK;
+    }
     if (k == 6 || (k == 0 && queue_ok)) {
         vrc_status s = split_queue(ctx, st, (size_t)L.cam.width * L.cam.height, L.split);
         if (s != VRC_OK) return s;
@@ -795,7 +817,7 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
         return fail(ctx, VRC_ERR_ARG, "gradient buffers must be 4-byte aligned");
     const int seg = params->seg_len == 0 ? 64 : params->seg_len;
     if (seg < 1 || seg > ADJ_MAX_SEG) return fail(ctx, VRC_ERR_ARG, "seg_len must be 0..128");
-    if (params->interp || params->preclass || params->shade)
+    if (params->interp || params->preclass || params->shade || params->preint)
         return fail(ctx, VRC_ERR_ARG, "the adjoint differentiates the default variant only");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -884,6 +906,9 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
         return fail(ctx, VRC_ERR_ARG, "counters_dev must be 8-byte aligned");
     const int B = params->brick;
     if (B != 0 && B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick must be 0, 8 or 16");
+    if (params->preint)
+        return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not pre-integrate (the table "
+                                      "would need memory)");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     Volume *v = get_vol(ctx, vol_id);
@@ -1053,7 +1078,7 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
         return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be a 16-byte aligned device pointer");
     if (params && params->kernel >= 2)
         return fail(ctx, VRC_ERR_ARG, "the server renders with the per-ray kernel (kernel 0 or 1)");
-    if (params && (params->interp || params->preclass || params->shade))
+    if (params && (params->interp || params->preclass || params->shade || params->preint))
         return fail(ctx, VRC_ERR_ARG, "the server renders the default variant only");
     DeviceGuard g(ctx->device);
     const int slot = (int)(s->next_seq % s->max_slots);

@@ -137,6 +137,31 @@ __device__ __forceinline__ float tricubic_rep(const ReplView &rp, const int ip[3
     return s;
 }
 
+// Pre-integrated classification: 256 x 256 table of slab (associated rgb, opacity), front
+// entry major (preint_table_kernel); PREINT_K sub-steps per entry.
+constexpr int PREINT_K = 32;
+cudaError_t launch_preint_table(const float4 *rgba, float ds, float4 *tab, cudaStream_t st);
+
+// Bilinear lookup at clamped table coordinates (uf, ub) in [0, 255].
+__device__ __forceinline__ float4 preint_lookup(const float4 *__restrict__ tab, float uf,
+                                                float ub) {
+    int i0, k0;
+    floor_small(uf, i0);
+    floor_small(ub, k0);
+    i0 = min(i0, 254);
+    k0 = min(k0, 254);
+    const float fi = uf - (float)i0, fk = ub - (float)k0;
+    const float4 *r0 = tab + i0 * 256 + k0;
+    const float4 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r0 + 256), d = __ldg(r0 + 257);
+    const float gi = 1.0f - fi, gk = 1.0f - fk;
+    float4 o;
+    o.x = fmaf(fi, fmaf(fk, d.x, gk * c.x), gi * fmaf(fk, b.x, gk * a.x));
+    o.y = fmaf(fi, fmaf(fk, d.y, gk * c.y), gi * fmaf(fk, b.y, gk * a.y));
+    o.z = fmaf(fi, fmaf(fk, d.z, gk * c.z), gi * fmaf(fk, b.z, gk * a.z));
+    o.w = fmaf(fi, fmaf(fk, d.w, gk * c.w), gi * fmaf(fk, b.w, gk * a.w));
+    return o;
+}
+
 // Trilinear sample at integer base ip (taps ip .. ip+1, clamped) with fractions f, from the
 // x-replicated float4 volume: entry (ip0 + 1, ip1 + 1 + b, ip2 + 1 + c) for b, c in {1, 2},
 // components y and z (voxels ip0 and ip0 + 1).
@@ -223,7 +248,8 @@ enum {
     MODE_LINEAR_POST = 1,
     MODE_CUBIC_PRE = 2,
     MODE_LINEAR_PRE = 3,
-    MODE_CUBIC_PHONG = 4
+    MODE_CUBIC_PHONG = 4,
+    MODE_PREINT = 5  // slabs through the pre-integration table (per-ray kernel, no skipping)
 };
 
 template <int MODE>
@@ -377,6 +403,7 @@ struct RenderLaunch {
     int cwx;                       // mask words per row of cells along x
     int mode;                      // interpolation / classification variant (MODE_*)
     Phong phong;                   // MODE_CUBIC_PHONG only
+    const float4 *preint;          // MODE_PREINT only: the table for slabs of length step
 };
 
 // Bit of the cell holding sample base ip (ip in [-1, n-1]); 0: the sample's opacity is zero.

@@ -168,7 +168,7 @@ class Renderer:
     # -- rendering ----------------------------------------------------------------------------
     def render(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
                brick: int = 0, out=None, counters=None, stream=None, kernel: int = 0,
-               interp: int = 0, preclass: int = 0, phong=None):
+               interp: int = 0, preclass: int = 0, phong=None, preint: int = 0):
         """Renders into a (H, W, 4) float32 CUDA tensor (allocated when `out` is None).
         `counters`: optional int64 CUDA tensor of 2 elements incremented by (nominal,
         executed) samples."""
@@ -183,21 +183,21 @@ class Renderer:
             assert counters.is_cuda and counters.dtype == torch.int64 and counters.numel() == 2
             cptr = C.c_void_p(counters.data_ptr())
         cs = native.camera_struct(cam)
-        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong)
+        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, preint)
         self._ck(self.lib.vrc_render(self.ctx, int(vol_id), int(tf_id), C.byref(cs), C.byref(ps),
                                      C.c_void_p(out.data_ptr()), cptr, _stream_ptr(stream)))
         return out
 
     def render_host(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
                     brick: int = 0, out=None, stream=None, kernel: int = 0,
-                    interp: int = 0, preclass: int = 0, phong=None):
+                    interp: int = 0, preclass: int = 0, phong=None, preint: int = 0):
         """End-to-end render into host memory (pinned torch tensor or numpy array)."""
         torch = _torch()
         if out is None:
             out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32, pin_memory=True)
         ptr = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
         cs = native.camera_struct(cam)
-        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong)
+        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, preint)
         self._ck(self.lib.vrc_render_host(self.ctx, int(vol_id), int(tf_id), C.byref(cs),
                                           C.byref(ps), C.c_void_p(ptr), _stream_ptr(stream)))
         return out

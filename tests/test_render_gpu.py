@@ -559,3 +559,51 @@ def test_phong_argument_checks(R, torch):
             R.render(vid, tid, cam, **kw)
     R.free_tf(tid)
     R.free_volume(vid)
+
+
+# ------------------------------------- pre-integrated classification (the next row 3)
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("step,ert", [(0.5, 0.999), (0.37, 1.0)])
+def test_preint_parity(R, orc, torch, kernel, step, ert):
+    """Slabs through the pre-integration table against the oracle (table built on the GPU
+    in double, looked up bilinearly in float)."""
+    vol = _ct_small(seed=20, shape=(40, 48, 56))
+    tf = synth.tf_ct(3)
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    for cam in synth.orbit_cameras(48, 2, synth.dims_of(vol), 64, 56):
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        img = R.render(vid, tid, cam, step=step, ert=ert, kernel=kernel, preint=1,
+                       counters=cnt).cpu().numpy()
+        ref, margin, (nom, ex) = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, step,
+                                            ert=ert, return_margin=True, return_counts=True,
+                                            preint=1)
+        _check(img, ref, margin if ert < 1 else None)
+        if ert >= 1.0:
+            assert cnt.tolist() == [nom, ex]
+    R.free_tf(tid)
+    R.free_volume(vid)
+
+
+def test_preint_table_follows_step_and_table_and_rejects(R, orc, torch):
+    from paper_2005_01442_gb300 import native
+    vol = _ct_small(seed=21, shape=(30, 34, 38))
+    tf = synth.tf_ct()
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(49, 1, synth.dims_of(vol), 40, 40)[0]
+    for step in (0.5, 0.3, 0.5):
+        img = R.render(vid, tid, cam, step=step, preint=1).cpu().numpy()
+        _check(img, orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, step, preint=1))
+    tf2 = synth.tf_ct(4)
+    R.update_tf(tid, tf2, synth.CT_LO, synth.CT_HI)
+    img = R.render(vid, tid, cam, step=0.5, preint=1).cpu().numpy()
+    _check(img, orc.render(vol, tf2, synth.CT_LO, synth.CT_HI, cam, 0.5, preint=1))
+    for kw in (dict(brick=8), dict(interp=1), dict(phong=(0.3, 0.7, 0.2, 8.0)), dict(kernel=6),
+               dict(kernel=2)):
+        with pytest.raises(native.VrcError):
+            R.render(vid, tid, cam, preint=1, **kw)
+    R.free_tf(tid)
+    R.free_volume(vid)
