@@ -80,6 +80,7 @@ def lib():
         L.orc_bricks.argtypes = [vp, ip, ip, ip, ip, ip, vp, vp]
         L.orc_occupancy.argtypes = [vp, vp, ip, C.c_long, vp, C.c_float, C.c_float, vp]
         L.orc_cellmask.argtypes = [vp, ip, ip, ip, ip, vp, C.c_float, C.c_float, vp]
+        L.orc_brick_aabbs.argtypes = [vp, ip, ip, ip, ip, vp, vp]
         L.orc_render.argtypes = [vp, ip, ip, ip, ip, vp, C.c_double, C.c_double,
                                  C.POINTER(Camera), C.POINTER(Params), vp, C.POINTER(Ball), vp,
                                  C.c_long, vp, vp, vp, vp]
@@ -242,19 +243,21 @@ def _pix(pixels):
 
 def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
            return_margin=False, return_counts=False, return_executed=False, interp=0,
-           preclass=0, phong=None, preint=0):
+           preclass=0, phong=None, preint=0, occ=None):
     """FP64 render. Returns float64 (H, W, 4) (or (npix, 4) for a pixel list), plus the ERT
     margins, the (nominal, executed) sample counts and the per-pixel executed samples when
     asked. interp / preclass select the variant; phong = (ka, kd, ks, shininess) turns on
     headlight Blinn-Phong shading (cubic post-classification); preint 1 composites slabs
-    between consecutive samples through the pre-integrated table (no skipping)."""
+    between consecutive samples through the pre-integrated table (no skipping). occ replaces
+    the brick occupancy of `brick` (a piece render passes the occupancy of its piece)."""
     vol = np.ascontiguousarray(vol)
     tf = np.ascontiguousarray(tf, np.float32)
     nz, ny, nx = vol.shape
-    occ = None
-    if brick:
+    if brick and occ is None:
         mn, mx = bricks(vol, brick)
         occ = occupancy(mn, mx, tf, lo, hi)
+    if occ is not None:
+        occ = np.ascontiguousarray(occ, np.uint8)
     pix, npix = _pix(pixels)
     n = npix if pix is not None else cam.width * cam.height
     out = np.zeros((n, 4), np.float64)
@@ -306,3 +309,106 @@ def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, wa
     if rc != 0:
         raise ValueError(f"orc_render_grad failed ({rc})")
     return gtf, gvol
+
+
+# ------------------------------------------------------------------------------------------
+# Object-order rendering with sort-last compositing (see "pieces" in vrc_oracle.c)
+
+
+def brick_aabbs(vol: np.ndarray, tf: np.ndarray, lo: float, hi: float, B: int) -> np.ndarray:
+    """Tight visible box of every brick, int16 (nbz, nby, nbx, 6): (lo_x, lo_y, lo_z, hi_x,
+    hi_y, hi_z), half-open in cell coordinates (cell c holds the points with floor(p) = c);
+    zeros for a brick with no open cell or an empty brick (see orc_brick_aabbs)."""
+    vol = np.ascontiguousarray(vol)
+    tf = np.ascontiguousarray(tf, np.float32)
+    nz, ny, nx = vol.shape
+    cm = cellmask(vol, tf, lo, hi)
+    mn, mx = bricks(vol, B)
+    occ = occupancy(mn, mx, tf, lo, hi)
+    out = np.empty(occ.shape + (6,), np.int16)
+    rc = lib().orc_brick_aabbs(_ptr(cm), nx, ny, nz, int(B), _ptr(occ), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_brick_aabbs failed ({rc})")
+    return out
+
+
+def piece_grid(dims, B: int, grid):
+    """Pieces of a (gx, gy, gz) grid over the bricks of a volume of size dims = (nx, ny, nz):
+    a list, piece index (sz * gy + sy) * gx + sx, of brick boxes (lo, hi), half-open, piece s
+    of g along an axis holding bricks [floor(s nb / g), floor((s + 1) nb / g))."""
+    nb = [(int(n) + B - 1) // B for n in dims]
+    out = []
+    for sz in range(grid[2]):
+        for sy in range(grid[1]):
+            for sx in range(grid[0]):
+                s = (sx, sy, sz)
+                out.append((tuple(s[k] * nb[k] // grid[k] for k in range(3)),
+                            tuple((s[k] + 1) * nb[k] // grid[k] for k in range(3))))
+    return out
+
+
+def piece_cells(dims, B: int, blo, bhi):
+    """Cell range [lo, hi) per axis of the bricks [blo, bhi): brick b holds the cells
+    [bB, bB + B), brick 0 also cell -1, the last brick the cells up to n - 1."""
+    nb = [(int(n) + B - 1) // B for n in dims]
+    lo = tuple(-1 if blo[k] == 0 else blo[k] * B for k in range(3))
+    hi = tuple(int(dims[k]) if bhi[k] == nb[k] else bhi[k] * B for k in range(3))
+    return lo, hi
+
+
+def piece_occupancy(occ: np.ndarray, blo, bhi) -> np.ndarray:
+    """The brick occupancy (nbz, nby, nbx) with every brick outside [blo, bhi) set to 0."""
+    m = np.zeros_like(occ)
+    m[blo[2]:bhi[2], blo[1]:bhi[1], blo[0]:bhi[0]] = occ[blo[2]:bhi[2], blo[1]:bhi[1],
+                                                         blo[0]:bhi[0]]
+    return m
+
+
+def render_piece(vol, tf, lo, hi, cam, step, brick, blo, bhi, ert=1.0, pixels=None):
+    """Partial image (C, 1 - T) of the piece of bricks [blo, bhi): the samples whose brick lies
+    in the piece, composited from T = 1 with their own early termination."""
+    mn, mx = bricks(vol, brick)
+    occ = piece_occupancy(occupancy(mn, mx, tf, lo, hi), blo, bhi)
+    return render(vol, tf, lo, hi, cam, step, ert=ert, brick=brick, pixels=pixels, occ=occ)
+
+
+def pixel_piece_order(cam, dims, cell_boxes, pixels) -> np.ndarray:
+    """Per pixel, the piece indices in the order in which its ray enters the pieces' boxes
+    (point sets floor(p) in [lo, hi), clipped to the volume box [-0.5, n - 0.5]), pieces the
+    ray does not meet last in index order. int (npix, K)."""
+    pix, npix = _pix(pixels)
+    K = len(cell_boxes)
+    order = np.empty((npix, K), np.int64)
+    for i in range(npix):
+        o, d, t_in, t_out, hit = ray(cam, dims, int(pix[i, 0]), int(pix[i, 1]))
+        ent = []
+        for k, (clo, chi) in enumerate(cell_boxes):
+            t0, t1 = t_in, t_out
+            for a in range(3):
+                lo_a = max(float(clo[a]), -0.5)
+                hi_a = min(float(chi[a]), float(dims[a]) - 0.5)
+                if d[a] != 0.0:
+                    ta, tb = (lo_a - o[a]) / d[a], (hi_a - o[a]) / d[a]
+                    t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+                elif not (lo_a <= o[a] < hi_a):
+                    t0, t1 = 1.0, 0.0
+            ent.append((0, t0, k) if (hit and t0 < t1) else (1, 0.0, k))
+        order[i] = [k for _, _, k in sorted(ent)]
+    return order
+
+
+def composite(partials: np.ndarray, order: np.ndarray) -> np.ndarray:
+    """Over-composition of partial images (K, npix, 4) per pixel in the given order (npix, K):
+    C += T C_k, T *= 1 - A_k from C = 0, T = 1; returns (C, 1 - T), float64 (npix, 4)."""
+    partials = np.asarray(partials, np.float64)
+    K, npix, _ = partials.shape
+    out = np.zeros((npix, 4), np.float64)
+    for i in range(npix):
+        C = np.zeros(3)
+        T = 1.0
+        for k in order[i]:
+            C += T * partials[k, i, :3]
+            T *= 1.0 - partials[k, i, 3]
+        out[i, :3] = C
+        out[i, 3] = 1.0 - T
+    return out

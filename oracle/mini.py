@@ -147,12 +147,14 @@ def preint_table(tf, ds, k=32):
     return np.concatenate([col, (1.0 - trans)[..., None]], -1)
 
 
-def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0, phong=None, preint=0):
+def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0, phong=None, preint=0,
+           keep=None):
     """(H, W, 4) float64 image: front-to-back compositing over segment midpoints.
     interp 0/1: cubic B-spline / trilinear kernel; preclass 1: classify every voxel, then
     interpolate the rgba; phong (ka, kd, ks, shininess): headlight shading by the gradient of
     the cubic field, softened by eps = 0.01 (hi - lo); preint: slabs between consecutive
-    samples through the pre-integration table, looked up bilinearly."""
+    samples through the pre-integration table, looked up bilinearly. keep(p) -> bool, when
+    given, drops every sample point it rejects (a partial image of part of the volume)."""
     nz, ny, nx = vol.shape
     dims = (nx, ny, nz)
     kernel = "cubic" if interp == 0 else "linear"
@@ -208,6 +210,8 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, interp=0, preclass=0, phong=None
                 continue
             for a, b in zip(edges[:-1], edges[1:]):
                 p = o + 0.5 * (a + b) * d
+                if keep is not None and not keep(p):
+                    continue
                 rgba = sample(p)
                 if phong is not None:
                     ka, kd, ks, shin = phong

@@ -60,11 +60,22 @@
  *              takes alpha' = 1 - (1 - alpha)^(d/ds) and colour C alpha'/alpha. Cubic post-
  *              classification without shading; no skipping (a skipped sample's value would
  *              be needed by its two slabs).
+ *   pieces     (object-order rendering with sort-last compositing; the paper's blocks and its
+ *              distribution of the volume over processors, Sec. "Analysis") the brick grid
+ *              is cut into a grid of pieces of whole bricks, piece s of g along an axis
+ *              holding bricks [floor(s nb / g), floor((s+1) nb / g)). A piece's partial
+ *              image composites front to back, from T = 1 and with its own ERT, exactly the
+ *              samples whose brick (the brick holding floor(p)) lies in the piece: the ESL
+ *              render with every brick outside the piece marked empty. The image is the
+ *              over-composition (C += T C_k, T *= 1 - A_k) of the partials of each pixel in
+ *              the order in which its ray meets the pieces. Without ERT it equals the
+ *              one-pass render up to rounding (the over operator is associative).
  *   gradient   reverse mode through compositing, opacity, classification and resampling,
  *              w.r.t. the TF entries and the voxel values (see orc_render_grad). At the kinks
  *              of the opacity clamp (a = 0, a = 1-2^-24) and of the index clamp (u = 0, 255)
  *              the derivative is taken on the clamped side (0).
  */
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -533,6 +544,54 @@ int orc_cellmask(const void *data, int dtype, int nx, int ny, int nz, const floa
             if (tf[4 * k + 3] > 0.0f) { o = 1; break; }
         out[idx] = o;
     }
+    return ORC_OK;
+}
+
+/* Tight visible box of every brick (object-order rendering, Sec. "Analysis": blocks and the
+ * auxiliary structures that let rays skip space). A cell c (per axis -1 .. n-1, the sample
+ * points with floor(p) = c) belongs to the brick holding floor(p) as the renderer assigns it:
+ * b = c / B for c >= 0 and b = 0 for c = -1. The box of brick b is the bounding box of the
+ * cells of b that are open in the cell mask (byte 1), when b is occupied; it is written as
+ * six int16 (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z), half-open in cell coordinates, and as six
+ * zeros when no such cell exists. Every sample of b with alpha > 0 lies in a cell of the box.
+ * cellmask: (nz+1, ny+1, nx+1) bytes from orc_cellmask; occ: (nbz, nby, nbx) bytes. */
+int orc_brick_aabbs(const uint8_t *cellmask, int nx, int ny, int nz, int B, const uint8_t *occ,
+                    int16_t *out) {
+    if (B <= 0 || nx <= 0 || ny <= 0 || nz <= 0) return ORC_EARG;
+    const long n[3] = {nx, ny, nz};
+    const long nb[3] = {nbricks_axis(nx, B), nbricks_axis(ny, B), nbricks_axis(nz, B)};
+    const long total = nb[0] * nb[1] * nb[2];
+    long *box = (long *)malloc(sizeof(long) * 6 * (size_t)total);
+    if (!box) return ORC_ENOMEM;
+    for (long i = 0; i < total; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            box[6 * i + k] = LONG_MAX;      /* smallest open cell */
+            box[6 * i + 3 + k] = LONG_MIN;  /* largest open cell */
+        }
+    }
+    for (long c2 = -1; c2 < n[2]; ++c2)
+        for (long c1 = -1; c1 < n[1]; ++c1)
+            for (long c0 = -1; c0 < n[0]; ++c0) {
+                const long idx = ((c2 + 1) * (n[1] + 1) + (c1 + 1)) * (n[0] + 1) + (c0 + 1);
+                if (!cellmask[idx]) continue;
+                const long c[3] = {c0, c1, c2};
+                long b[3];
+                for (int k = 0; k < 3; ++k) b[k] = c[k] >= 0 ? c[k] / B : 0;
+                const long lin = (b[2] * nb[1] + b[1]) * nb[0] + b[0];
+                if (!occ[lin]) continue;
+                for (int k = 0; k < 3; ++k) {
+                    if (c[k] < box[6 * lin + k]) box[6 * lin + k] = c[k];
+                    if (c[k] > box[6 * lin + 3 + k]) box[6 * lin + 3 + k] = c[k];
+                }
+            }
+    for (long i = 0; i < total; ++i) {
+        const int empty = box[6 * i] == LONG_MAX;
+        for (int k = 0; k < 3; ++k) {
+            out[6 * i + k] = empty ? 0 : (int16_t)box[6 * i + k];
+            out[6 * i + 3 + k] = empty ? 0 : (int16_t)(box[6 * i + 3 + k] + 1);
+        }
+    }
+    free(box);
     return ORC_OK;
 }
 

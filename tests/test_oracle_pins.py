@@ -710,3 +710,136 @@ def test_gradient_matches_central_differences(orc):
         if checked >= 25:
             break
     assert checked >= 10
+
+
+# ----------------------------------- object-order pieces and sort-last compositing (next 4)
+
+def _cell_range_of_brick(b, B, n):
+    return (-1 if b == 0 else b * B), min(b * B + B, n)
+
+
+@pytest.mark.parametrize("v", [(6, 5, 4), (0, 0, 0), (12, 10, 8), (7, 3, 8)])
+@pytest.mark.parametrize("B", [4, 8])
+def test_brick_aabbs_single_voxel_closed_form(orc, v, B):
+    # An isolated opaque voxel v in air opens exactly the cells c with max(v-2, -1) <= c <=
+    # min(v+1, n-1) per axis (the cells whose clamped taps c-1 .. c+2 reach v); a brick's box
+    # is that range cut to the brick's own cells, and every other brick's box is empty.
+    nx, ny, nz = 13, 11, 9
+    vol = np.full((nz, ny, nx), -1000, np.int16)
+    vol[v[2], v[1], v[0]] = 1200
+    box = orc.brick_aabbs(vol, synth.tf_ct(), synth.CT_LO, synth.CT_HI, B)
+    n = (nx, ny, nz)
+    nb = [(k + B - 1) // B for k in n]
+    assert box.shape == (nb[2], nb[1], nb[0], 6) and box.dtype == np.int16
+    for bz in range(nb[2]):
+        for by in range(nb[1]):
+            for bx in range(nb[0]):
+                b = (bx, by, bz)
+                lo, hi = [], []
+                for k in range(3):
+                    c0, c1 = _cell_range_of_brick(b[k], B, n[k])
+                    lo.append(max(c0, v[k] - 2, -1))
+                    hi.append(min(c1, v[k] + 2, n[k]))
+                if all(hi[k] > lo[k] for k in range(3)):
+                    assert box[bz, by, bx].tolist() == lo + hi, b
+                else:
+                    assert not box[bz, by, bx].any(), b
+
+
+def test_brick_aabbs_are_the_bounding_boxes_of_open_cells(orc):
+    # Brute force with NumPy on a small CT-like volume: each occupied brick's box is the
+    # bounding box of its open cells; boxes of bricks without open cells (and of empty
+    # bricks) are zero.
+    rng = np.random.default_rng(31)
+    vol = np.full((20, 18, 22), -1000, np.int16)                 # air
+    vol[3:11, 2:12, 4:17] = rng.normal(40, 10, (8, 10, 13))       # soft tissue
+    vol[14, 13, 18] = 1200                                        # bone voxel
+    tf, lo, hi = synth.tf_ct(), synth.CT_LO, synth.CT_HI
+    m = orc.cellmask(vol, tf, lo, hi)
+    nz, ny, nx = vol.shape
+    for B in (4, 8):
+        occ = orc.occupancy(*orc.bricks(vol, B), tf, lo, hi)
+        box = orc.brick_aabbs(vol, tf, lo, hi, B)
+        cells = np.argwhere(m == 1) - 1  # (cz, cy, cx) cell coordinates
+        bidx = np.maximum(cells, 0) // B
+        seen = tighter = 0
+        for bz, by, bx in np.ndindex(occ.shape):
+            sel = cells[(bidx[:, 0] == bz) & (bidx[:, 1] == by) & (bidx[:, 2] == bx)]
+            if occ[bz, by, bx] == 0 or len(sel) == 0:
+                assert not box[bz, by, bx].any()
+                continue
+            seen += 1
+            mn, mx = sel.min(axis=0)[::-1], sel.max(axis=0)[::-1] + 1  # to (x, y, z)
+            assert box[bz, by, bx].tolist() == mn.tolist() + mx.tolist()
+            c0 = [_cell_range_of_brick(b, B, n)[0] for b, n in zip((bx, by, bz), (nx, ny, nz))]
+            c1 = [_cell_range_of_brick(b, B, n)[1] for b, n in zip((bx, by, bz), (nx, ny, nz))]
+            tighter += mn.tolist() != c0 or mx.tolist() != c1
+        assert 0 < seen < occ.size and tighter > 0
+
+
+@pytest.mark.parametrize("grid", [(1, 1, 1), (2, 2, 2), (3, 1, 2), (4, 3, 1)])
+def test_piece_grid_tiles_bricks_and_cells_once(orc, grid):
+    # The pieces of a grid cover every brick once, and their cell ranges cover the cells
+    # -1 .. n-1 of each axis once (the decomposition neither drops nor repeats a sample).
+    dims, B = (37, 29, 20), 4
+    nb = [(n + B - 1) // B for n in dims]
+    pieces = orc.piece_grid(dims, B, grid)
+    assert len(pieces) == grid[0] * grid[1] * grid[2]
+    count = np.zeros(nb[::-1], np.int32)
+    ccount = np.zeros([n + 1 for n in dims[::-1]], np.int32)
+    for blo, bhi in pieces:
+        assert all(bhi[k] > blo[k] for k in range(3))
+        count[blo[2]:bhi[2], blo[1]:bhi[1], blo[0]:bhi[0]] += 1
+        clo, chi = orc.piece_cells(dims, B, blo, bhi)
+        ccount[clo[2] + 1:chi[2] + 1, clo[1] + 1:chi[1] + 1, clo[0] + 1:chi[0] + 1] += 1
+    assert (count == 1).all() and (ccount == 1).all()
+
+
+def _tiny_piece_scene():
+    vol = synth.ct_volume((12, 14, 16), seed=33)
+    tf = synth.tf_ct().copy()
+    tf[:, 3] = np.minimum(tf[:, 3] * 4.0, 0.9)
+    return vol, tf, synth.CT_LO, synth.CT_HI
+
+
+@pytest.mark.parametrize("ert", [1.0, 0.9])
+def test_piece_partial_matches_brute_force(orc, ert):
+    # A piece's partial image is the brute-force caster with every sample outside the
+    # piece's bricks dropped (NumPy rays, segments and kernel sum), its own early termination
+    # included.
+    vol, tf, lo, hi = _tiny_piece_scene()
+    dims = synth.dims_of(vol)
+    B = 4
+    cam = synth.orbit_cameras(1, 9, dims, 10, 8)[0]
+    for blo, bhi in orc.piece_grid(dims, B, (2, 2, 1))[1:3]:
+        def keep(p, blo=blo, bhi=bhi):
+            b = [max(int(math.floor(p[k])), 0) // B for k in range(3)]
+            return all(blo[k] <= b[k] < bhi[k] for k in range(3))
+        ref = mini.render(vol, tf, lo, hi, cam, 0.7, ert=ert, keep=keep)
+        got = orc.render_piece(vol, tf, lo, hi, cam, 0.7, B, blo, bhi, ert=ert)
+        assert np.abs(got - ref).max() < 1e-9
+        assert ref[..., 3].max() > 0.05
+
+
+@pytest.mark.parametrize("grid", [(2, 2, 2), (3, 1, 2)])
+def test_sort_last_composite_equals_one_pass_render(orc, grid):
+    # The over operator is associative: composited in the order each ray meets the pieces,
+    # the partial images of all pieces give the one-pass render (no early termination) to
+    # rounding, for perspective and orthographic views. Reversed, they do not.
+    vol, tf, lo, hi = _ct_small()
+    dims = synth.dims_of(vol)
+    B = 8
+    cams = list(synth.orbit_cameras(2, 5, dims, 24, 20)) + [synth.ortho_z_camera(dims, 24, 20)]
+    pieces = orc.piece_grid(dims, B, grid)
+    boxes = [orc.piece_cells(dims, B, blo, bhi) for blo, bhi in pieces]
+    for cam in cams:
+        pix = [(x, y) for y in range(cam.height) for x in range(cam.width)]
+        full = orc.render(vol, tf, lo, hi, cam, 0.5, brick=B).reshape(-1, 4)
+        parts = np.stack([orc.render_piece(vol, tf, lo, hi, cam, 0.5, B, blo, bhi).reshape(-1, 4)
+                          for blo, bhi in pieces])
+        order = orc.pixel_piece_order(cam, dims, boxes, pix)
+        comp = orc.composite(parts, order)
+        assert np.abs(comp - full).max() < 1e-12
+        assert full[:, 3].max() > 0.5
+        wrong = orc.composite(parts, order[:, ::-1])
+        assert np.abs(wrong - full).max() > 1e-3
