@@ -285,6 +285,100 @@ vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_cam
                               const vrc_params *params, float *out_rgba_dev,
                               unsigned long long *counters_dev, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Object-order pieces and sort-last compositing. The paper splits the volume into blocks
+ * with auxiliary structures (Sec. "Methodology", Fig. 3; Sec. "Analysis", Pros (b)) and
+ * spreads them over processors that each render a part (Sec. "Analysis"); these calls render
+ * a volume as a grid of pieces of whole bricks, each into a partial image, and blend the
+ * partials in visibility order. A piece render is the ESL render with every brick outside
+ * the piece marked empty, so it composites exactly the piece's samples (those whose brick,
+ * the brick holding floor(p), lies in the piece), from T = 1 and with its own early
+ * termination. Without early termination the blended image equals vrc_render's up to
+ * rounding (the over operator is associative); with it, each piece stops on its own. */
+
+/* A piece of a plan. Bricks [brick_lo, brick_hi) per axis; cells (floor of sample points,
+ * -1 .. n-1) [cell_lo, cell_hi): piece s of g along an axis with nb bricks holds the bricks
+ * [floor(s nb / g), floor((s + 1) nb / g)), the first piece also cell -1, the last the cells
+ * up to n-1. vis_lo, vis_hi: the piece's tight visible box in cells (the union of the boxes
+ * of vrc_aabbs_get over its bricks), all zeros when no sample of the piece can be visible. */
+typedef struct {
+    int brick_lo[3], brick_hi[3];
+    int cell_lo[3], cell_hi[3];
+    int vis_lo[3], vis_hi[3];
+} vrc_piece;
+
+/* Copies the tight visible box of every brick of (volume, B, TF) to boxes_host: nbricks x 6
+ * int16 (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z), half-open in cell coordinates, bricks in the
+ * order of vrc_bricks_get. The box is the bounding box of the cells of an occupied brick that
+ * are open in the cell mask (vrc_cellmask_get; brick of cell c: c / B, cell -1 in brick 0),
+ * all zeros when there is none, so every sample of the brick with opacity > 0 lies in it.
+ * nbricks must equal nbx*nby*nbz (VRC_ERR_ARG); B is 8 or 16 with its brick table built
+ * (VRC_ERR_STATE). Builds the occupancy, mask and boxes if needed; synchronises `stream`. */
+vrc_status vrc_aabbs_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, int16_t *boxes_host,
+                         long nbricks, void *stream);
+
+/* Cuts the brick grid of a volume (brick size B, table built) into grid[0] x grid[1] x
+ * grid[2] pieces (1 <= grid[a] <= bricks along axis a; at most 64 pieces) for transfer
+ * function tf_id, and builds each piece's leaping fields (8 bytes per brick per piece, owned
+ * by the plan) and visible box. Piece index (sz * grid[1] + sy) * grid[0] + sx. The plan
+ * stays bound to the volume's brick table and the table's contents at build time: after
+ * either changes, calls that render with it return VRC_ERR_STATE. Synchronises `stream`. */
+vrc_status vrc_pieces_build(vrc_ctx *ctx, int vol_id, int tf_id, int B, const int grid[3],
+                            int *plan_id, void *stream);
+
+/* Piece count (count, may be NULL), the pieces (pieces_host, count entries, may be NULL) and
+ * the interior cut planes (cuts_host, (grid[0]-1) + (grid[1]-1) + (grid[2]-1) floats, x then
+ * y then z, in voxel coordinates: piece s >= 1 of an axis holds the points p >= cut s-1;
+ * may be NULL) of a plan. */
+vrc_status vrc_pieces_get(vrc_ctx *ctx, int plan_id, int *count, vrc_piece *pieces_host,
+                          float *cuts_host);
+
+/* Frees a plan (synchronises the device). */
+vrc_status vrc_pieces_free(vrc_ctx *ctx, int plan_id);
+
+/* Host only, no context: a visibility order (order: grid[0]*grid[1]*grid[2] piece indices,
+ * front first) of the pieces of a rectilinear grid with interior cut planes `cuts` (as
+ * vrc_pieces_get returns them; strictly increasing per axis) for every ray of `cam`: along a
+ * ray from the eye each axis's slab index moves away from the eye's slab, so the order sorts
+ * by the summed slab distance from the eye (for orthographic rays, by the slab index in the
+ * direction's sense). Ties keep index order. VRC_ERR_ARG on a bad camera or cuts. */
+vrc_status vrc_grid_order(const vrc_camera *cam, const int grid[3], const float *cuts,
+                          int *order);
+
+/* Host only, no context: the pixel rectangle rect = (x0, y0, w, h) of `cam` outside of which
+ * no pixel's ray meets the box [lo, hi] (voxel coordinates): the bounding rectangle of the
+ * projected corners widened by one pixel and cut to the image; the whole image when a corner
+ * is not in front of a perspective eye; (0, 0, 0, 0) for an empty box or rectangle. */
+vrc_status vrc_box_rect(const vrc_camera *cam, const float lo[3], const float hi[3],
+                        int rect[4]);
+
+/* Renders piece `piece` of a plan for the pixels rect = (x0, y0, w, h) of `cam` (inside the
+ * image) into out_dev: h x w x 4 floats, pixel (x0 + i, y0 + j) at row j, column i, in the
+ * format of vrc_render. params as for vrc_render, with params->brick equal to the plan's B
+ * and no pre-integration (its slabs span pieces). A rect with w or h 0 renders nothing.
+ * Pixels whose rays miss the piece's visible box get (0, 0, 0, 0), so a rect from
+ * vrc_box_rect of that box loses nothing. Asynchronous on `stream`. */
+vrc_status vrc_render_piece(vrc_ctx *ctx, int plan_id, int piece, const vrc_camera *cam,
+                            const vrc_params *params, const int rect[4], float *out_dev,
+                            void *stream);
+
+/* Blends K (<= 64) partial images into out_dev (height x width x 4 floats): per pixel, from
+ * C = 0, T = 1, for k = order[0], order[1], ... (front to back): when the pixel lies in
+ * rects[4k .. 4k+3] = (x0, y0, w, h), with (c, a) the partial's value there
+ * (partials_dev[k], h x w x 4 floats), C += T c and T *= 1 - a; the result is (C, 1 - T).
+ * order must be a permutation of 0 .. K-1; partials with an empty rect are not read.
+ * Asynchronous on `stream`. */
+vrc_status vrc_composite(vrc_ctx *ctx, int K, const float *const *partials_dev,
+                         const int *rects, const int *order, int width, int height,
+                         float *out_dev, void *stream);
+
+/* The whole sort-last path for one camera: the visibility order of the plan's pieces, each
+ * visible piece rendered into the rectangle of its visible box (partial images in memory the
+ * plan owns, grown on demand), then vrc_composite into out_dev (height x width x 4 floats,
+ * the format of vrc_render). Asynchronous on `stream` unless the partial buffer grows. */
+vrc_status vrc_render_sortlast(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
+                               const vrc_params *params, float *out_dev, void *stream);
+
 /* Reads and clears the device error word shared by the context's kernels: 0 when no kernel
  * check has fired, else a VRC_ERR_* code. Synchronises `stream`. */
 vrc_status vrc_last_device_error(vrc_ctx *ctx, int *code, void *stream);

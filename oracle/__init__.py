@@ -364,12 +364,14 @@ def piece_occupancy(occ: np.ndarray, blo, bhi) -> np.ndarray:
     return m
 
 
-def render_piece(vol, tf, lo, hi, cam, step, brick, blo, bhi, ert=1.0, pixels=None):
+def render_piece(vol, tf, lo, hi, cam, step, brick, blo, bhi, ert=1.0, pixels=None, **kw):
     """Partial image (C, 1 - T) of the piece of bricks [blo, bhi): the samples whose brick lies
-    in the piece, composited from T = 1 with their own early termination."""
+    in the piece, composited from T = 1 with their own early termination. Further keywords
+    (the variant, return_margin) go to render()."""
     mn, mx = bricks(vol, brick)
     occ = piece_occupancy(occupancy(mn, mx, tf, lo, hi), blo, bhi)
-    return render(vol, tf, lo, hi, cam, step, ert=ert, brick=brick, pixels=pixels, occ=occ)
+    return render(vol, tf, lo, hi, cam, step, ert=ert, brick=brick, pixels=pixels, occ=occ,
+                  **kw)
 
 
 def pixel_piece_order(cam, dims, cell_boxes, pixels) -> np.ndarray:

@@ -1,0 +1,196 @@
+// Object-order decomposition and sort-last compositing (the paper's blocks with their
+// auxiliary structures, Sec. "Methodology" and Sec. "Analysis", Pros (b), and its
+// distribution of the volume over several processors that each render a part).
+//
+//   brick_aabb_kernel   tight visible box of every brick: the bounding box of the cells of
+//                       an occupied brick that are open in the cell mask (a sample of the
+//                       brick with opacity > 0 lies in one of them).
+//   piece_mask_kernel   the occupancy of one piece: bricks outside the piece marked empty, so
+//                       that the ESL render composites exactly the samples of the piece.
+//   piece_box_kernel    the union of the brick boxes of each piece (its visible box).
+//   composite_kernel    the over operator across the partial images of the pieces, per pixel,
+//                       in a visibility order (C += T C_k, T *= 1 - A_k).
+#include <limits.h>
+
+#include "vrc_internal.h"
+
+namespace vrc {
+
+namespace {
+
+// One warp per brick. Cell c (per axis -1 .. n-1) sits at mask index c + 1; brick b holds the
+// cells [bB, bB + B) cut to n - 1, brick 0 also the cell -1. Each lane takes whole rows (y, z)
+// of the brick's cells and extracts their x bits (at most B + 1 bits, two words at most).
+__global__ void __launch_bounds__(256) brick_aabb_kernel(const uint32_t *__restrict__ cells,
+                                                         int cwx, int nx, int ny, int nz,
+                                                         int B, int nbx, int nby, int nbz,
+                                                         const uint8_t *__restrict__ occ,
+                                                         int16_t *__restrict__ out) {
+    const long nbricks = (long)nbx * nby * nbz;
+    const long lin = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (lin >= nbricks) return;  // whole warps leave together
+    const int bx = (int)(lin % nbx), by = (int)((lin / nbx) % nby), bz = (int)(lin / ((long)nbx * nby));
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    if (occ[lin]) {
+        const int n[3] = {nx, ny, nz};
+        const int b[3] = {bx, by, bz};
+        int c0[3], c1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c0[k] = b[k] == 0 ? -1 : b[k] * B;
+            c1[k] = min(b[k] * B + B, n[k]);
+        }
+        const int ry = c1[1] - c0[1], rows = ry * (c1[2] - c0[2]);
+        const int x0 = c0[0] + 1, w = c1[0] - c0[0];  // mask index of the first cell, width
+        const int wd = x0 >> 5, sh = x0 & 31;
+        const unsigned long long keep = (w >= 64) ? ~0ull : ((1ull << w) - 1ull);
+        for (int r = lane; r < rows; r += 32) {
+            const int cy = c0[1] + r % ry, cz = c0[2] + r / ry;
+            const uint32_t *row = cells + ((long)(cz + 1) * (ny + 1) + (cy + 1)) * cwx;
+            unsigned long long bits = row[wd];
+            if (wd + 1 < cwx) bits |= (unsigned long long)row[wd + 1] << 32;
+            bits = (bits >> sh) & keep;
+            if (bits) {
+                lo[0] = min(lo[0], c0[0] + __ffsll((long long)bits) - 1);
+                hi[0] = max(hi[0], c0[0] + 63 - __clzll((long long)bits));
+                lo[1] = min(lo[1], cy);
+                hi[1] = max(hi[1], cy);
+                lo[2] = min(lo[2], cz);
+                hi[2] = max(hi[2], cz);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+        hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+    }
+    if (lane < 6) {
+        const bool empty = lo[0] == INT_MAX;
+        const int v = lane == 0 ? lo[0] : lane == 1 ? lo[1] : lane == 2 ? lo[2]
+                    : lane == 3 ? hi[0] + 1 : lane == 4 ? hi[1] + 1 : hi[2] + 1;
+        out[lin * 6 + lane] = empty ? (int16_t)0 : (int16_t)v;
+    }
+}
+
+__global__ void piece_mask_kernel(const uint8_t *__restrict__ occ, int nbx, int nby, int nbz,
+                                  int x0, int y0, int z0, int x1, int y1, int z1,
+                                  uint8_t *__restrict__ out) {
+    const long nbricks = (long)nbx * nby * nbz;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nbricks;
+         i += (long)gridDim.x * blockDim.x) {
+        const int bx = (int)(i % nbx), by = (int)((i / nbx) % nby), bz = (int)(i / ((long)nbx * nby));
+        const bool in = bx >= x0 && bx < x1 && by >= y0 && by < y1 && bz >= z0 && bz < z1;
+        out[i] = in ? occ[i] : (uint8_t)0;
+    }
+}
+
+// One block per piece: min/max of the non-empty brick boxes inside the piece's brick range.
+__global__ void __launch_bounds__(256) piece_box_kernel(const int16_t *__restrict__ aabb,
+                                                        int nbx, int nby,
+                                                        const int *__restrict__ bricks_k,
+                                                        int *__restrict__ out) {
+    const int *pb = bricks_k + 6 * blockIdx.x;  // brick lo[3], hi[3]
+    const int ex = pb[3] - pb[0], ey = pb[4] - pb[1], ez = pb[5] - pb[2];
+    const long count = (long)ex * ey * ez;
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (long i = threadIdx.x; i < count; i += blockDim.x) {
+        const int bx = pb[0] + (int)(i % ex), by = pb[1] + (int)((i / ex) % ey),
+                  bz = pb[2] + (int)(i / ((long)ex * ey));
+        const int16_t *a = aabb + (((long)bz * nby + by) * nbx + bx) * 6;
+        if (a[3] > a[0]) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = min(lo[k], (int)a[k]);
+                hi[k] = max(hi[k], (int)a[3 + k]);
+            }
+        }
+    }
+    __shared__ int red[8][6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+        hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            red[wid][k] = lo[k];
+            red[wid][3 + k] = hi[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        int v = red[0][k], any = red[0][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            v = k < 3 ? min(v, red[w][k]) : max(v, red[w][k]);
+            any = min(any, red[w][0]);
+        }
+        out[6 * blockIdx.x + k] = any == INT_MAX ? 0 : v;  // no open cell in the piece: zeros
+    }
+}
+
+// One thread per output pixel; the partials are listed front to back.
+__global__ void __launch_bounds__(256) composite_kernel(const CompositeArgs a,
+                                                        float4 *__restrict__ out) {
+    const long npix = (long)a.width * a.height;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < npix;
+         i += (long)gridDim.x * blockDim.x) {
+        const int px = (int)(i % a.width), py = (int)(i / a.width);
+        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+        for (int k = 0; k < a.K; ++k) {
+            const int x = px - a.rect[k][0], y = py - a.rect[k][1];
+            if ((unsigned)x < (unsigned)a.rect[k][2] && (unsigned)y < (unsigned)a.rect[k][3]) {
+                const float4 p = __ldg(a.part[k] + (long)y * a.rect[k][2] + x);
+                c0 = fmaf(T, p.x, c0);
+                c1 = fmaf(T, p.y, c1);
+                c2 = fmaf(T, p.z, c2);
+                T = T * (1.0f - p.w);
+            }
+        }
+        out[i] = make_float4(c0, c1, c2, 1.0f - T);
+    }
+}
+
+int grid_for(long n, int per_block) {
+    long g = (n + per_block - 1) / per_block;
+    return (int)(g < 1 ? 1 : (g > (1L << 20) ? (1L << 20) : g));
+}
+
+}  // namespace
+
+cudaError_t launch_brick_aabbs(const uint32_t *cells, int cwx, const int n[3], int B,
+                               const int nb[3], const uint8_t *occ, int16_t *out,
+                               cudaStream_t st) {
+    const long nbricks = (long)nb[0] * nb[1] * nb[2];
+    const long blocks = (nbricks + 7) / 8;
+    if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
+    brick_aabb_kernel<<<(unsigned)blocks, 256, 0, st>>>(cells, cwx, n[0], n[1], n[2], B, nb[0],
+                                                       nb[1], nb[2], occ, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_piece_mask(const uint8_t *occ, const int nb[3], const int blo[3],
+                              const int bhi[3], uint8_t *out, cudaStream_t st) {
+    const long nbricks = (long)nb[0] * nb[1] * nb[2];
+    piece_mask_kernel<<<grid_for(nbricks, 256), 256, 0, st>>>(
+        occ, nb[0], nb[1], nb[2], blo[0], blo[1], blo[2], bhi[0], bhi[1], bhi[2], out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_piece_boxes(const int16_t *aabb, const int nb[3], const int *bricks_k, int K,
+                               int *out, cudaStream_t st) {
+    piece_box_kernel<<<K, 256, 0, st>>>(aabb, nb[0], nb[1], bricks_k, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite(const CompositeArgs &a, float4 *out, cudaStream_t st) {
+    const long npix = (long)a.width * a.height;
+    composite_kernel<<<grid_for(npix, 256), 256, 0, st>>>(a, out);
+    return cudaGetLastError();
+}
+
+}  // namespace vrc

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -34,6 +35,8 @@ struct Occ {
     uint32_t *cells = nullptr;  // cell transparency mask (cellmask_words words)
     long n = 0;
     unsigned brick_version = 0, tf_version = 0;
+    int16_t *aabb = nullptr;    // tight visible box per brick (6 int16), built on first use
+    unsigned aabb_brick_version = 0, aabb_tf_version = 0;
 };
 
 struct Volume {
@@ -72,6 +75,23 @@ struct SplitBuf {
     size_t cap = 0;
 };
 
+// Object-order decomposition of a volume into a grid of pieces of whole bricks, for one
+// transfer function and brick size.
+struct Piece {
+    vrc_piece info;
+    uint8_t *dist = nullptr;  // 8 forward-box distance fields of the piece's occupancy
+};
+
+struct Plan {
+    int vol_id = 0, tf_id = 0, B = 0;
+    int grid[3] = {1, 1, 1};
+    unsigned brick_version = 0, tf_version = 0;
+    std::vector<Piece> pieces;
+    std::vector<float> cuts;        // interior cut planes, x then y then z
+    float4 *partials = nullptr;     // partial images of vrc_render_sortlast
+    size_t partial_cap = 0;         // in pixels
+};
+
 }  // namespace
 
 struct vrc_ctx {
@@ -84,6 +104,7 @@ struct vrc_ctx {
     float4 *host_img = nullptr;  // device image for vrc_render_host
     size_t host_img_bytes = 0;
     std::map<cudaStream_t, SplitBuf> split;  // split-render queues by stream
+    std::map<int, Plan> plans;               // piece grids (vrc_pieces_build)
     unsigned tf_version_counter = 0;
 };
 
@@ -137,6 +158,7 @@ void free_volume(Volume &v) {
         cudaFree(kv.second.dist);
         cudaFree(kv.second.scratch);
         cudaFree(kv.second.cells);
+        cudaFree(kv.second.aabb);
     }
     v.occ.clear();
 }
@@ -149,6 +171,14 @@ void free_tf(Tf &t) {
     cudaFree(t.preint);
 }
 
+void free_plan(Plan &p) {
+    for (auto &pc : p.pieces) cudaFree(pc.dist);
+    p.pieces.clear();
+    cudaFree(p.partials);
+    p.partials = nullptr;
+    p.partial_cap = 0;
+}
+
 bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
 
 // Camera record -> per-pixel affine maps in double, split into double-float.
@@ -158,13 +188,16 @@ ff split(double v) {
     return {hi, lo};
 }
 
-vrc_status build_camera(vrc_ctx *ctx, const vrc_camera *c, CamDev &cd) {
+// Validates a camera record and returns its orthonormal frame in double: f the view
+// direction, r the image's right and u its up axis.
+vrc_status camera_frame(vrc_ctx *ctx, const vrc_camera *c, double f[3], double r[3],
+                        double u[3]) {
     if (!c) return fail(ctx, VRC_ERR_ARG, "camera is NULL");
     if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768)
         return fail(ctx, VRC_ERR_ARG, "image size %dx%d out of range", c->width, c->height);
     if (!finite3(c->eye) || !finite3(c->center) || !finite3(c->up))
         return fail(ctx, VRC_ERR_ARG, "camera has non-finite values");
-    double f[3], up[3], r[3], u[3];
+    double up[3];
     double fl = 0, rl = 0;
     for (int k = 0; k < 3; ++k) {
         f[k] = (double)c->center[k] - (double)c->eye[k];
@@ -183,6 +216,20 @@ vrc_status build_camera(vrc_ctx *ctx, const vrc_camera *c, CamDev &cd) {
     u[0] = r[1] * f[2] - r[2] * f[1];
     u[1] = r[2] * f[0] - r[0] * f[2];
     u[2] = r[0] * f[1] - r[1] * f[0];
+    if (c->ortho) {
+        const double hx = 0.5 * c->ortho_extent[0], hy = 0.5 * c->ortho_extent[1];
+        if (!(hx > 0) || !(hy > 0) || !isfinite(hx) || !isfinite(hy))
+            return fail(ctx, VRC_ERR_ARG, "orthographic extent must be positive");
+    } else if (!(c->fovy_deg > 0.0f && c->fovy_deg < 179.0f)) {
+        return fail(ctx, VRC_ERR_ARG, "fovy_deg must be in (0, 179)");
+    }
+    return VRC_OK;
+}
+
+vrc_status build_camera(vrc_ctx *ctx, const vrc_camera *c, CamDev &cd) {
+    double f[3], r[3], u[3];
+    vrc_status s = camera_frame(ctx, c, f, r, u);
+    if (s != VRC_OK) return s;
     const double W = c->width, H = c->height;
     memset(&cd, 0, sizeof(cd));
     cd.ortho = c->ortho ? 1 : 0;
@@ -190,8 +237,6 @@ vrc_status build_camera(vrc_ctx *ctx, const vrc_camera *c, CamDev &cd) {
     cd.height = c->height;
     if (c->ortho) {
         const double hx = 0.5 * c->ortho_extent[0], hy = 0.5 * c->ortho_extent[1];
-        if (!(hx > 0) || !(hy > 0) || !isfinite(hx) || !isfinite(hy))
-            return fail(ctx, VRC_ERR_ARG, "orthographic extent must be positive");
         for (int k = 0; k < 3; ++k) {
             cd.A[k] = split((double)c->eye[k] - hx * r[k] + hy * u[k]);
             cd.Bx[k] = split(hx / W * r[k]);
@@ -200,8 +245,6 @@ vrc_status build_camera(vrc_ctx *ctx, const vrc_camera *c, CamDev &cd) {
             cd.eye[k] = split(c->eye[k]);
         }
     } else {
-        if (!(c->fovy_deg > 0.0f && c->fovy_deg < 179.0f))
-            return fail(ctx, VRC_ERR_ARG, "fovy_deg must be in (0, 179)");
         const double th = tan(0.5 * (double)c->fovy_deg * M_PI / 180.0);
         const double kx = th * W / H, ky = th;
         for (int k = 0; k < 3; ++k) {
@@ -292,9 +335,12 @@ vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStre
         cudaFree(o.dist);
         cudaFree(o.scratch);
         cudaFree(o.cells);
+        cudaFree(o.aabb);
         o.dev = o.dist = nullptr;
         o.scratch = nullptr;
         o.cells = nullptr;
+        o.aabb = nullptr;
+        o.aabb_brick_version = o.aabb_tf_version = 0;
         o.n = 0;
         CK(cudaMalloc(&o.dev, (size_t)b.count()), "cudaMalloc(occupancy)");
         CK(cudaMalloc(&o.dist, 8 * (size_t)b.count()), "cudaMalloc(occupancy)");
@@ -319,6 +365,121 @@ vrc_status ensure_occ(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStre
     *out = o.dev;
     if (dist_out) *dist_out = o.dist;
     if (cells_out) *cells_out = o.cells;
+    return VRC_OK;
+}
+
+// Tight visible boxes of (volume, B, tf), rebuilt with the occupancy and cell mask.
+vrc_status ensure_aabb(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStream_t st,
+                       const int16_t **out, const uint8_t **occ_out = nullptr) {
+    const uint8_t *occ = nullptr;
+    const uint32_t *cells = nullptr;
+    vrc_status s = ensure_occ(ctx, v, tf_id, t, B, st, &occ, nullptr, &cells);
+    if (s != VRC_OK) return s;
+    Bricks &b = v.bricks[slot_of(B)];
+    Occ &o = v.occ[(long)tf_id * 2 + slot_of(B)];
+    if (!o.aabb) {
+        CK(cudaMalloc(&o.aabb, 6 * sizeof(int16_t) * (size_t)b.count()), "cudaMalloc(boxes)");
+        o.aabb_brick_version = o.aabb_tf_version = 0;
+    }
+    if (o.aabb_brick_version != o.brick_version || o.aabb_tf_version != o.tf_version) {
+        CK(launch_brick_aabbs(cells, (v.n[0] + 1 + 31) / 32, v.n, B, b.nb, occ, o.aabb, st),
+           "box launch");
+        o.aabb_brick_version = o.brick_version;
+        o.aabb_tf_version = o.tf_version;
+    }
+    *out = o.aabb;
+    if (occ_out) *occ_out = occ;
+    return VRC_OK;
+}
+
+// Visibility order of the pieces of a grid (cuts: the interior cut planes, x then y then z).
+// Along any ray from a point the piece index of each axis moves monotonically away from the
+// slab of the point, so sorting by the summed slab distance |s - s_eye| orders every pair of
+// pieces one ray can meet (the later one is farther on some axis and no nearer on any). For
+// parallel rays the slab index only grows (or only falls) with the direction's sign.
+vrc_status grid_order(vrc_ctx *ctx, const vrc_camera *cam, const int grid[3], const float *cuts,
+                      int *order) {
+    double f[3], r[3], u[3];
+    vrc_status s = camera_frame(ctx, cam, f, r, u);
+    if (s != VRC_OK) return s;
+    const int K = grid[0] * grid[1] * grid[2];
+    std::vector<std::pair<long, int>> key((size_t)K);
+    int seye[3];
+    const float *c = cuts;
+    for (int a = 0; a < 3; ++a) {
+        seye[a] = 0;
+        for (int i = 0; i + 1 < grid[a]; ++i)
+            if ((double)c[i] <= (double)cam->eye[a]) seye[a] = i + 1;
+        c += grid[a] - 1;
+    }
+    for (int k = 0; k < K; ++k) {
+        const int sl[3] = {k % grid[0], (k / grid[0]) % grid[1], k / (grid[0] * grid[1])};
+        long d = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (cam->ortho)
+                d += f[a] > 0 ? sl[a] : (f[a] < 0 ? grid[a] - 1 - sl[a] : 0);
+            else
+                d += sl[a] > seye[a] ? sl[a] - seye[a] : seye[a] - sl[a];
+        }
+        key[(size_t)k] = {d, k};
+    }
+    std::stable_sort(key.begin(), key.end());
+    for (int k = 0; k < K; ++k) order[k] = key[(size_t)k].second;
+    return VRC_OK;
+}
+
+// Pixel rectangle (x0, y0, w, h) outside of which no pixel's ray meets the box [lo, hi]: the
+// bounding rectangle of the projected corners, widened by one pixel; the whole image when a
+// corner is not in front of a perspective eye, (0, 0, 0, 0) for an empty box or rectangle.
+vrc_status box_rect(vrc_ctx *ctx, const vrc_camera *cam, const float lo[3], const float hi[3],
+                    int rect[4]) {
+    double f[3], r[3], u[3];
+    vrc_status s = camera_frame(ctx, cam, f, r, u);
+    if (s != VRC_OK) return s;
+    rect[0] = rect[1] = rect[2] = rect[3] = 0;
+    for (int a = 0; a < 3; ++a)
+        if (!(hi[a] > lo[a])) return VRC_OK;  // empty (or NaN) box
+    const double W = cam->width, H = cam->height;
+    double xs = INFINITY, xe = -INFINITY, ys = INFINITY, ye = -INFINITY;
+    bool full = false;
+    for (int corner = 0; corner < 8; ++corner) {
+        double v[3];
+        for (int a = 0; a < 3; ++a)
+            v[a] = (double)((corner >> a) & 1 ? hi[a] : lo[a]) - (double)cam->eye[a];
+        const double vr = v[0] * r[0] + v[1] * r[1] + v[2] * r[2];
+        const double vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+        double X, Y;  // image coordinates: pixel px has its centre at X = 2 px + 1
+        if (cam->ortho) {
+            X = W * (1.0 + vr / (0.5 * cam->ortho_extent[0]));
+            Y = H * (1.0 - vu / (0.5 * cam->ortho_extent[1]));
+        } else {
+            const double z = v[0] * f[0] + v[1] * f[1] + v[2] * f[2];
+            const double vl = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (!(z > 1e-6 * vl)) {
+                full = true;
+                break;
+            }
+            const double th = tan(0.5 * (double)cam->fovy_deg * M_PI / 180.0);
+            X = W * (1.0 + vr / (z * th * W / H));
+            Y = H * (1.0 - vu / (z * th));
+        }
+        xs = fmin(xs, X);
+        xe = fmax(xe, X);
+        ys = fmin(ys, Y);
+        ye = fmax(ye, Y);
+    }
+    double x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
+    if (!full) {
+        x0 = fmax(x0, ceil((xs - 1.0) * 0.5) - 1.0);
+        x1 = fmin(x1, floor((xe - 1.0) * 0.5) + 1.0);
+        y0 = fmax(y0, ceil((ys - 1.0) * 0.5) - 1.0);
+        y1 = fmin(y1, floor((ye - 1.0) * 0.5) + 1.0);
+        if (!(x1 >= x0 && y1 >= y0)) return VRC_OK;
+    }
+    rect[0] = (int)x0;
+    rect[1] = (int)y0;
+    rect[2] = (int)(x1 - x0) + 1;
+    rect[3] = (int)(y1 - y0) + 1;
     return VRC_OK;
 }
 
@@ -500,6 +661,7 @@ vrc_status vrc_destroy(vrc_ctx *ctx) {
     cudaFree(ctx->err_word);
     cudaFree(ctx->host_img);
     for (auto &kv : ctx->split) cudaFree(kv.second.base);
+    for (auto &kv : ctx->plans) free_plan(kv.second);
     delete ctx;
     return VRC_OK;
 }
@@ -1170,3 +1332,320 @@ extern "C" vrc_status vrc_server_destroy(vrc_server *s) {
     server_free(s);
     return VRC_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+// Object-order pieces and sort-last compositing
+
+namespace {
+
+Plan *get_plan(vrc_ctx *ctx, int id) {
+    auto it = ctx->plans.find(id);
+    return it == ctx->plans.end() ? nullptr : &it->second;
+}
+
+// The plan's volume and table exist and are the versions the plan was built from.
+vrc_status plan_fresh(vrc_ctx *ctx, const Plan &p) {
+    Volume *v = get_vol(ctx, p.vol_id);
+    Tf *t = get_tf(ctx, p.tf_id);
+    if (!v || !t) return fail(ctx, VRC_ERR_STATE, "the plan's volume or transfer function is gone");
+    if (v->bricks[slot_of(p.B)].version != p.brick_version || t->version != p.tf_version)
+        return fail(ctx, VRC_ERR_STATE, "the volume or transfer function changed; rebuild the plan");
+    return VRC_OK;
+}
+
+vrc_status check_rect(vrc_ctx *ctx, const int rect[4], int width, int height) {
+    if (!rect) return fail(ctx, VRC_ERR_ARG, "rect is NULL");
+    if (rect[0] < 0 || rect[1] < 0 || rect[2] < 0 || rect[3] < 0 ||
+        (long)rect[0] + rect[2] > width || (long)rect[1] + rect[3] > height)
+        return fail(ctx, VRC_ERR_ARG, "rect (%d, %d, %d, %d) is not inside the %dx%d image",
+                    rect[0], rect[1], rect[2], rect[3], width, height);
+    return VRC_OK;
+}
+
+vrc_status render_piece(vrc_ctx *ctx, Plan &p, int piece, const vrc_camera *cam,
+                        const vrc_params *params, const int rect[4], float *out_dev,
+                        cudaStream_t st) {
+    if (!params) return fail(ctx, VRC_ERR_ARG, "params is NULL");
+    if (params->brick != p.B)
+        return fail(ctx, VRC_ERR_ARG, "params.brick (%d) must be the plan's brick size %d",
+                    params->brick, p.B);
+    if (params->preint)
+        return fail(ctx, VRC_ERR_ARG, "pre-integrated slabs span pieces: not with pieces");
+    RenderLaunch L;
+    vrc_status s = prepare_render(ctx, p.vol_id, p.tf_id, cam, params, st, L);
+    if (s != VRC_OK) return s;
+    if ((s = check_rect(ctx, rect, cam->width, cam->height)) != VRC_OK) return s;
+    if (rect[2] == 0 || rect[3] == 0) return VRC_OK;
+    if (!out_dev || ((uintptr_t)out_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_dev must be non-NULL and 16-byte aligned");
+    L.dist = p.pieces[(size_t)piece].dist;
+    L.cam.ox = rect[0];
+    L.cam.oy = rect[1];
+    L.cam.width = rect[2];
+    L.cam.height = rect[3];
+    L.out = (float4 *)out_dev;
+    return launch_render(ctx, params, L, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+vrc_status vrc_aabbs_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, int16_t *boxes_host,
+                         long nbricks, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!boxes_host) return fail(ctx, VRC_ERR_ARG, "boxes_host is NULL");
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick must be 8 or 16");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int16_t *aabb = nullptr;
+    vrc_status s = ensure_aabb(ctx, *v, tf_id, *t, B, st, &aabb);
+    if (s != VRC_OK) return s;
+    const long count = v->bricks[slot_of(B)].count();
+    if (nbricks != count) return fail(ctx, VRC_ERR_ARG, "nbricks must be %ld", count);
+    CK(cudaMemcpyAsync(boxes_host, aabb, 6 * sizeof(int16_t) * (size_t)count,
+                       cudaMemcpyDeviceToHost, st), "box copy");
+    CK(cudaStreamSynchronize(st), "box copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_pieces_build(vrc_ctx *ctx, int vol_id, int tf_id, int B, const int grid[3],
+                            int *plan_id, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!grid || !plan_id) return fail(ctx, VRC_ERR_ARG, "grid and plan_id must be non-NULL");
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    Tf *t = get_tf(ctx, tf_id);
+    if (!t) return fail(ctx, VRC_ERR_ARG, "unknown transfer function id %d", tf_id);
+    if (B != 8 && B != 16) return fail(ctx, VRC_ERR_ARG, "brick must be 8 or 16");
+    Bricks &b = v->bricks[slot_of(B)];
+    if (!b.mn || b.B != B) return fail(ctx, VRC_ERR_STATE, "brick table B=%d not built", B);
+    for (int a = 0; a < 3; ++a)
+        if (grid[a] < 1 || grid[a] > b.nb[a])
+            return fail(ctx, VRC_ERR_ARG, "grid[%d] = %d must be in 1..%d (bricks on that axis)",
+                        a, grid[a], b.nb[a]);
+    const int K = grid[0] * grid[1] * grid[2];
+    if (K > MAX_PIECES) return fail(ctx, VRC_ERR_ARG, "at most %d pieces", MAX_PIECES);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int16_t *aabb = nullptr;
+    const uint8_t *occ = nullptr;
+    vrc_status s = ensure_aabb(ctx, *v, tf_id, *t, B, st, &aabb, &occ);
+    if (s != VRC_OK) return s;
+
+    Plan p;
+    p.vol_id = vol_id;
+    p.tf_id = tf_id;
+    p.B = B;
+    for (int a = 0; a < 3; ++a) p.grid[a] = grid[a];
+    p.brick_version = b.version;
+    p.tf_version = t->version;
+    std::vector<int> bricks_k((size_t)6 * K);
+    p.pieces.resize((size_t)K);
+    for (int k = 0; k < K; ++k) {
+        const int sl[3] = {k % grid[0], (k / grid[0]) % grid[1], k / (grid[0] * grid[1])};
+        vrc_piece &pi = p.pieces[(size_t)k].info;
+        memset(&pi, 0, sizeof(pi));
+        for (int a = 0; a < 3; ++a) {
+            pi.brick_lo[a] = (int)((long)sl[a] * b.nb[a] / grid[a]);
+            pi.brick_hi[a] = (int)((long)(sl[a] + 1) * b.nb[a] / grid[a]);
+            pi.cell_lo[a] = pi.brick_lo[a] == 0 ? -1 : pi.brick_lo[a] * B;
+            pi.cell_hi[a] = pi.brick_hi[a] == b.nb[a] ? v->n[a] : pi.brick_hi[a] * B;
+            bricks_k[(size_t)6 * k + a] = pi.brick_lo[a];
+            bricks_k[(size_t)6 * k + 3 + a] = pi.brick_hi[a];
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int i = 1; i < grid[a]; ++i)
+            p.cuts.push_back((float)((long)i * b.nb[a] / grid[a] * B));
+
+    // device work: per piece the masked occupancy and its distance fields, then the boxes
+    uint8_t *mask = nullptr;
+    int *scratch = nullptr, *dk = nullptr;
+    std::vector<int> boxes((size_t)6 * K);
+    cudaError_t e = cudaMalloc(&mask, (size_t)b.count());
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, box_dist_scratch_bytes(b.nb));
+    if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(int) * 12 * (size_t)K);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        Piece &pc = p.pieces[(size_t)k];
+        e = cudaMalloc(&pc.dist, 8 * (size_t)b.count());
+        if (e == cudaSuccess)
+            e = launch_piece_mask(occ, b.nb, pc.info.brick_lo, pc.info.brick_hi, mask, st);
+        if (e == cudaSuccess) e = launch_box_dist(mask, b.nb, scratch, pc.dist, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dk, bricks_k.data(), sizeof(int) * 6 * (size_t)K,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_piece_boxes(aabb, b.nb, dk, K, dk + 6 * K, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(boxes.data(), dk + 6 * K, sizeof(int) * 6 * (size_t)K,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(mask);
+    cudaFree(scratch);
+    cudaFree(dk);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(ctx, e, "piece build");
+    }
+    for (int k = 0; k < K; ++k)
+        for (int a = 0; a < 3; ++a) {
+            p.pieces[(size_t)k].info.vis_lo[a] = boxes[(size_t)6 * k + a];
+            p.pieces[(size_t)k].info.vis_hi[a] = boxes[(size_t)6 * k + 3 + a];
+        }
+    const int id = ctx->next_id++;
+    ctx->plans[id] = std::move(p);
+    *plan_id = id;
+    return VRC_OK;
+}
+
+vrc_status vrc_pieces_get(vrc_ctx *ctx, int plan_id, int *count, vrc_piece *pieces_host,
+                          float *cuts_host) {
+    if (!ctx) return VRC_ERR_ARG;
+    Plan *p = get_plan(ctx, plan_id);
+    if (!p) return fail(ctx, VRC_ERR_ARG, "unknown plan id %d", plan_id);
+    if (count) *count = (int)p->pieces.size();
+    if (pieces_host)
+        for (size_t k = 0; k < p->pieces.size(); ++k) pieces_host[k] = p->pieces[k].info;
+    if (cuts_host)
+        for (size_t i = 0; i < p->cuts.size(); ++i) cuts_host[i] = p->cuts[i];
+    return VRC_OK;
+}
+
+vrc_status vrc_pieces_free(vrc_ctx *ctx, int plan_id) {
+    if (!ctx) return VRC_ERR_ARG;
+    Plan *p = get_plan(ctx, plan_id);
+    if (!p) return fail(ctx, VRC_ERR_ARG, "unknown plan id %d", plan_id);
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    free_plan(*p);
+    ctx->plans.erase(plan_id);
+    return VRC_OK;
+}
+
+vrc_status vrc_grid_order(const vrc_camera *cam, const int grid[3], const float *cuts,
+                          int *order) {
+    if (!cam || !grid || !order) return VRC_ERR_ARG;
+    long K = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (grid[a] < 1 || grid[a] > 4096) return VRC_ERR_ARG;
+        K *= grid[a];
+    }
+    if (K > 1L << 20) return VRC_ERR_ARG;
+    if (K > 1 && !cuts && (grid[0] > 1 || grid[1] > 1 || grid[2] > 1)) return VRC_ERR_ARG;
+    const float *c = cuts;
+    for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i + 1 < grid[a]; ++i)
+            if (!isfinite(c[i]) || (i > 0 && !(c[i] > c[i - 1]))) return VRC_ERR_ARG;
+        c += grid[a] - 1;
+    }
+    return grid_order(nullptr, cam, grid, cuts, order);
+}
+
+vrc_status vrc_box_rect(const vrc_camera *cam, const float lo[3], const float hi[3],
+                        int rect[4]) {
+    if (!cam || !lo || !hi || !rect) return VRC_ERR_ARG;
+    if (!finite3(lo) || !finite3(hi)) return VRC_ERR_ARG;
+    return box_rect(nullptr, cam, lo, hi, rect);
+}
+
+vrc_status vrc_render_piece(vrc_ctx *ctx, int plan_id, int piece, const vrc_camera *cam,
+                            const vrc_params *params, const int rect[4], float *out_dev,
+                            void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Plan *p = get_plan(ctx, plan_id);
+    if (!p) return fail(ctx, VRC_ERR_ARG, "unknown plan id %d", plan_id);
+    if (piece < 0 || piece >= (int)p->pieces.size())
+        return fail(ctx, VRC_ERR_ARG, "piece %d out of range", piece);
+    vrc_status s = plan_fresh(ctx, *p);
+    if (s != VRC_OK) return s;
+    DeviceGuard g(ctx->device);
+    return render_piece(ctx, *p, piece, cam, params, rect, out_dev, (cudaStream_t)stream);
+}
+
+vrc_status vrc_composite(vrc_ctx *ctx, int K, const float *const *partials_dev, const int *rects,
+                         const int *order, int width, int height, float *out_dev, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (K < 0 || K > MAX_PIECES) return fail(ctx, VRC_ERR_ARG, "K must be in 0..%d", MAX_PIECES);
+    if (K > 0 && (!partials_dev || !rects || !order))
+        return fail(ctx, VRC_ERR_ARG, "partials_dev, rects and order must be non-NULL");
+    if (width < 1 || height < 1 || width > 32768 || height > 32768)
+        return fail(ctx, VRC_ERR_ARG, "image size %dx%d out of range", width, height);
+    if (!out_dev || ((uintptr_t)out_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_dev must be non-NULL and 16-byte aligned");
+    CompositeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.width = width;
+    a.height = height;
+    bool seen[MAX_PIECES] = {false};
+    for (int i = 0; i < K; ++i) {
+        const int k = order[i];
+        if (k < 0 || k >= K || seen[k]) return fail(ctx, VRC_ERR_ARG, "order is not a permutation");
+        seen[k] = true;
+        vrc_status s = check_rect(ctx, rects + 4 * k, width, height);
+        if (s != VRC_OK) return s;
+        if (rects[4 * k + 2] == 0 || rects[4 * k + 3] == 0) continue;  // nothing to blend
+        if (!partials_dev[k] || ((uintptr_t)partials_dev[k] & 15) != 0)
+            return fail(ctx, VRC_ERR_ARG, "partial %d must be non-NULL and 16-byte aligned", k);
+        a.part[a.K] = (const float4 *)partials_dev[k];
+        for (int q = 0; q < 4; ++q) a.rect[a.K][q] = rects[4 * k + q];
+        ++a.K;
+    }
+    DeviceGuard g(ctx->device);
+    CK(launch_composite(a, (float4 *)out_dev, (cudaStream_t)stream), "composite launch");
+    return VRC_OK;
+}
+
+vrc_status vrc_render_sortlast(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
+                               const vrc_params *params, float *out_dev, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Plan *p = get_plan(ctx, plan_id);
+    if (!p) return fail(ctx, VRC_ERR_ARG, "unknown plan id %d", plan_id);
+    vrc_status s = plan_fresh(ctx, *p);
+    if (s != VRC_OK) return s;
+    if (!out_dev || ((uintptr_t)out_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_dev must be non-NULL and 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = (int)p->pieces.size();
+    std::vector<int> order((size_t)K), rects((size_t)4 * K);
+    if ((s = grid_order(ctx, cam, p->grid, p->cuts.data(), order.data())) != VRC_OK) return s;
+    Volume *v = get_vol(ctx, p->vol_id);
+    size_t total = 0;
+    for (int k = 0; k < K; ++k) {
+        const vrc_piece &pi = p->pieces[(size_t)k].info;
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {  // the points with floor(p) in [vis_lo, vis_hi)
+            lo[a] = fmaxf((float)pi.vis_lo[a], -0.5f);
+            hi[a] = fminf((float)pi.vis_hi[a], (float)v->n[a] - 0.5f);
+        }
+        if ((s = box_rect(ctx, cam, lo, hi, &rects[(size_t)4 * k])) != VRC_OK) return s;
+        total += (size_t)rects[(size_t)4 * k + 2] * rects[(size_t)4 * k + 3];
+    }
+    if (p->partial_cap < total) {
+        CK(cudaStreamSynchronize(st), "sync before partial realloc");
+        cudaFree(p->partials);
+        p->partials = nullptr;
+        p->partial_cap = 0;
+        CK(cudaMalloc(&p->partials, total * sizeof(float4)), "cudaMalloc(partials)");
+        p->partial_cap = total;
+    }
+    std::vector<const float *> parts((size_t)K, nullptr);
+    size_t off = 0;
+    for (int k = 0; k < K; ++k) {
+        const int *r = &rects[(size_t)4 * k];
+        if (r[2] == 0 || r[3] == 0) continue;
+        parts[(size_t)k] = (const float *)(p->partials + off);
+        s = render_piece(ctx, *p, k, cam, params, r, (float *)(p->partials + off), st);
+        if (s != VRC_OK) return s;
+        off += (size_t)r[2] * r[3];
+    }
+    return vrc_composite(ctx, K, parts.data(), rects.data(), order.data(), cam->width,
+                         cam->height, out_dev, stream);
+}
+
+}  // extern "C"

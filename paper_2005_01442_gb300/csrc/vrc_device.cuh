@@ -105,7 +105,8 @@ struct CamDev {
     ff eye[3];
     ff dir[3];
     int ortho;
-    int width, height;
+    int width, height;  // pixels rendered (a sub-rectangle of the image for a piece)
+    int ox, oy;         // image pixel of rendered pixel (0, 0)
 };
 
 // Box and sampling parameters of one render.
@@ -160,7 +161,7 @@ __device__ __forceinline__ bool ray_clearly_misses(const CamDev &cam, const RayG
 
 __device__ __forceinline__ void ray_setup(const CamDev &cam, const RayGrid &g, int px, int py,
                                           RaySetup &r) {
-    const float X = (float)(2 * px + 1), Y = (float)(2 * py + 1);
+    const float X = (float)(2 * (px + cam.ox) + 1), Y = (float)(2 * (py + cam.oy) + 1);
     r.nseg = 0;
     if (ray_clearly_misses(cam, g, X, Y)) return;
     ff o[3], d[3];

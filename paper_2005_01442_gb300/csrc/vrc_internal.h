@@ -469,6 +469,25 @@ size_t box_dist_scratch_bytes(const int nb[3]);
 // dist: 8 x nbricks bytes (one forward-box distance field per direction octant)
 cudaError_t launch_box_dist(const uint8_t *occ, const int nb[3], int *scratch, uint8_t *dist,
                              cudaStream_t st);
+// Object-order pieces and sort-last compositing (k_pieces.cu).
+constexpr int MAX_PIECES = 64;
+// Partials listed front to back; partial k covers the image pixels [rect[k][0], +rect[k][2])
+// x [rect[k][1], +rect[k][3]), rect[k][2] pixels per row.
+struct CompositeArgs {
+    int K, width, height;
+    const float4 *part[MAX_PIECES];
+    int rect[MAX_PIECES][4];
+};
+// out: 6 int16 per brick (tight visible box, half-open cell coordinates, zeros when empty)
+cudaError_t launch_brick_aabbs(const uint32_t *cells, int cwx, const int n[3], int B,
+                               const int nb[3], const uint8_t *occ, int16_t *out,
+                               cudaStream_t st);
+cudaError_t launch_piece_mask(const uint8_t *occ, const int nb[3], const int blo[3],
+                              const int bhi[3], uint8_t *out, cudaStream_t st);
+// bricks_k: K x 6 ints (device; brick lo, hi of each piece); out: K x 6 ints (device)
+cudaError_t launch_piece_boxes(const int16_t *aabb, const int nb[3], const int *bricks_k, int K,
+                               int *out, cudaStream_t st);
+cudaError_t launch_composite(const CompositeArgs &a, float4 *out, cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
 cudaError_t launch_render_warp(const RenderLaunch &L, int lanes_per_ray, cudaStream_t st);
 // Both phases of the split render; L.split.head must be zero (it is left nonzero).

@@ -26,7 +26,9 @@ EXPORTS = [
     "vrc_occupancy_build", "vrc_occupancy_get", "vrc_cellmask_get", "vrc_render", "vrc_render_host",
     "vrc_render_noalloc", "vrc_render_backward", "vrc_server_create", "vrc_server_submit",
     "vrc_server_pump", "vrc_server_poll", "vrc_server_destroy", "vrc_last_device_error",
-    "vrc_last_error_message", "vrc_status_str", "vrc_version",
+    "vrc_last_error_message", "vrc_status_str", "vrc_version", "vrc_aabbs_get",
+    "vrc_pieces_build", "vrc_pieces_get", "vrc_pieces_free", "vrc_grid_order", "vrc_box_rect",
+    "vrc_render_piece", "vrc_composite", "vrc_render_sortlast",
 ]
 
 
@@ -48,6 +50,11 @@ class vrc_params(C.Structure):
                 ("preclass", C.c_int), ("shade", C.c_int), ("ka", C.c_float),
                 ("kd", C.c_float), ("ks", C.c_float), ("shininess", C.c_float),
                 ("preint", C.c_int)]
+
+
+class vrc_piece(C.Structure):
+    _fields_ = [("brick_lo", C.c_int * 3), ("brick_hi", C.c_int * 3), ("cell_lo", C.c_int * 3),
+                ("cell_hi", C.c_int * 3), ("vis_lo", C.c_int * 3), ("vis_hi", C.c_int * 3)]
 
 
 _lib = None
@@ -98,6 +105,18 @@ def load(build_if_missing: bool = False):
     L.vrc_server_pump.argtypes = [vp, C.c_longlong, C.c_longlong, pint]
     L.vrc_server_poll.argtypes = [vp, C.c_longlong, pint]
     L.vrc_server_destroy.argtypes = [vp]
+    L.vrc_aabbs_get.argtypes = [vp, ip, ip, ip, vp, C.c_long, vp]
+    L.vrc_pieces_build.argtypes = [vp, ip, ip, ip, pint, pint, vp]
+    L.vrc_pieces_get.argtypes = [vp, ip, pint, C.POINTER(vrc_piece), C.POINTER(C.c_float)]
+    L.vrc_pieces_free.argtypes = [vp, ip]
+    L.vrc_grid_order.argtypes = [C.POINTER(vrc_camera), pint, C.POINTER(C.c_float), pint]
+    L.vrc_box_rect.argtypes = [C.POINTER(vrc_camera), C.POINTER(C.c_float),
+                               C.POINTER(C.c_float), pint]
+    L.vrc_render_piece.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params),
+                                   pint, vp, vp]
+    L.vrc_composite.argtypes = [vp, ip, C.POINTER(vp), pint, pint, ip, ip, vp, vp]
+    L.vrc_render_sortlast.argtypes = [vp, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
+                                      vp]
     L.vrc_last_device_error.argtypes = [vp, pint, vp]
     L.vrc_last_error_message.argtypes = [vp]
     L.vrc_last_error_message.restype = C.c_char_p
@@ -136,3 +155,31 @@ def params_struct(step=0.5, ert=1.0, brick=0, seg_len=64, kernel=0, interp=0,
     return vrc_params(float(step), float(ert), int(brick), int(seg_len), int(kernel),
                       int(interp), int(preclass), int(phong is not None), float(ka), float(kd),
                       float(ks), float(shin), int(preint))
+
+
+def grid_order(cam, grid, cuts) -> list:
+    """vrc_grid_order (host only): visibility order of the pieces of a grid with interior cut
+    planes `cuts` (x then y then z) for every ray of `cam`."""
+    L = load()
+    K = int(grid[0]) * int(grid[1]) * int(grid[2])
+    g = (C.c_int * 3)(*[int(x) for x in grid])
+    cu = (C.c_float * max(len(cuts), 1))(*[float(x) for x in cuts])
+    order = (C.c_int * K)()
+    cs = camera_struct(cam)
+    st = L.vrc_grid_order(C.byref(cs), g, cu, order)
+    if st != 0:
+        raise VrcError(st, "vrc_grid_order")
+    return list(order)
+
+
+def box_rect(cam, lo, hi) -> tuple:
+    """vrc_box_rect (host only): (x0, y0, w, h) of the pixels whose rays may meet [lo, hi]."""
+    L = load()
+    a = (C.c_float * 3)(*[float(x) for x in lo])
+    b = (C.c_float * 3)(*[float(x) for x in hi])
+    r = (C.c_int * 4)()
+    cs = camera_struct(cam)
+    st = L.vrc_box_rect(C.byref(cs), a, b, r)
+    if st != 0:
+        raise VrcError(st, "vrc_box_rect")
+    return tuple(r)

@@ -216,6 +216,93 @@ class Renderer:
             C.c_void_p(grad_vol.data_ptr()) if grad_vol is not None else None,
             _stream_ptr(stream)))
 
+    # -- object-order pieces and sort-last compositing ----------------------------------------
+    def aabbs(self, vol_id: int, tf_id: int, B: int, stream=None) -> np.ndarray:
+        """Tight visible box of every brick, int16 (nbz, nby, nbx, 6): (lo_x, lo_y, lo_z,
+        hi_x, hi_y, hi_z) in cell coordinates, zeros when nothing in the brick is visible."""
+        _, (nx, ny, nz) = self.volume_info(vol_id)
+        nb = [(n + B - 1) // B for n in (nz, ny, nx)]
+        out = np.empty(nb + [6], np.int16)
+        self._ck(self.lib.vrc_aabbs_get(self.ctx, int(vol_id), int(tf_id), int(B),
+                                        out.ctypes.data_as(C.c_void_p), nb[0] * nb[1] * nb[2],
+                                        _stream_ptr(stream)))
+        return out
+
+    def build_pieces(self, vol_id: int, tf_id: int, B: int, grid, stream=None) -> int:
+        """Plan of grid = (gx, gy, gz) pieces of whole bricks; returns its id."""
+        g = (C.c_int * 3)(*[int(x) for x in grid])
+        pid = C.c_int()
+        self._ck(self.lib.vrc_pieces_build(self.ctx, int(vol_id), int(tf_id), int(B), g,
+                                           C.byref(pid), _stream_ptr(stream)))
+        return pid.value
+
+    def pieces(self, plan_id: int):
+        """(pieces, cuts): one dict per piece (brick_lo/hi, cell_lo/hi, vis_lo/hi, each a
+        3-tuple) and the interior cut planes (x then y then z)."""
+        n = C.c_int()
+        self._ck(self.lib.vrc_pieces_get(self.ctx, int(plan_id), C.byref(n), None, None))
+        arr = (native.vrc_piece * n.value)()
+        ncut = 64 * 3
+        cuts = (C.c_float * ncut)(*([float("nan")] * ncut))
+        self._ck(self.lib.vrc_pieces_get(self.ctx, int(plan_id), None, arr, cuts))
+        out = [{f: tuple(getattr(p, f)) for f, _ in native.vrc_piece._fields_} for p in arr]
+        return out, [c for c in cuts if c == c]
+
+    def free_pieces(self, plan_id: int):
+        self._ck(self.lib.vrc_pieces_free(self.ctx, int(plan_id)))
+
+    def render_piece(self, plan_id: int, piece: int, cam, rect, step: float = 0.5,
+                     ert: float = 1.0, brick: int = 8, out=None, stream=None, kernel: int = 0,
+                     interp: int = 0, preclass: int = 0, phong=None):
+        """Partial image of one piece for the pixels rect = (x0, y0, w, h): a (h, w, 4)
+        float32 CUDA tensor (allocated when `out` is None)."""
+        torch = _torch()
+        x0, y0, w, h = [int(v) for v in rect]
+        if out is None:
+            out = torch.empty((h, w, 4), dtype=torch.float32, device=f"cuda:{self.device}")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == h * w * 4
+        r = (C.c_int * 4)(x0, y0, w, h)
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, 0)
+        self._ck(self.lib.vrc_render_piece(self.ctx, int(plan_id), int(piece), C.byref(cs),
+                                           C.byref(ps), r, C.c_void_p(out.data_ptr()),
+                                           _stream_ptr(stream)))
+        return out
+
+    def composite(self, partials, rects, order, width: int, height: int, out=None,
+                  stream=None):
+        """Blends partial images (CUDA tensors, (h_k, w_k, 4) for rects[k] = (x0, y0, w, h))
+        front to back in `order` into a (height, width, 4) float32 CUDA tensor."""
+        torch = _torch()
+        K = len(partials)
+        if out is None:
+            out = torch.empty((height, width, 4), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        ptrs = (C.c_void_p * max(K, 1))(*[p.data_ptr() if p is not None else None
+                                          for p in partials])
+        rc = (C.c_int * max(4 * K, 1))(*[int(v) for r in rects for v in r])
+        od = (C.c_int * max(K, 1))(*[int(k) for k in order])
+        self._ck(self.lib.vrc_composite(self.ctx, K, ptrs, rc, od, int(width), int(height),
+                                        C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def render_sortlast(self, plan_id: int, cam, step: float = 0.5, ert: float = 1.0,
+                        brick: int = 8, out=None, stream=None, kernel: int = 0, interp: int = 0,
+                        preclass: int = 0, phong=None):
+        """The image of `cam` rendered piece by piece and blended in visibility order."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == cam.height * cam.width * 4
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, 0)
+        self._ck(self.lib.vrc_render_sortlast(self.ctx, int(plan_id), C.byref(cs), C.byref(ps),
+                                              C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
     def last_device_error(self, stream=None) -> int:
         code = C.c_int()
         self._ck(self.lib.vrc_last_device_error(self.ctx, C.byref(code), _stream_ptr(stream)))
