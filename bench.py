@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--mode", default="render",
                    choices=["render", "serve", "adjoint", "large", "variants", "sortlast"])
     p.add_argument("--serve-seconds", type=float, default=8.0)
+    p.add_argument("--grid", default="1,1,1;2,2,2;3,3,3;4,4,4",
+                   help="--mode sortlast: piece grids gx,gy,gz separated by ';'")
     return p.parse_args()
 
 
@@ -607,7 +609,7 @@ def run_mode(args, torch, R, synth):
             one_pass()
         base_ms = _timed(torch, one_pass, args.steps) / len(cams)
         rows = []
-        for grid in [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 4, 4)]:
+        for grid in [tuple(int(x) for x in g.split(",")) for g in args.grid.split(";")]:
             plan = R.build_pieces(vid, tid, args.brick, grid)
             pieces, _ = R.pieces(plan)
 
@@ -617,6 +619,13 @@ def run_mode(args, torch, R, synth):
             for _ in range(args.warmup):
                 frames()
             ms = _timed(torch, frames, args.steps) / len(cams)
+
+            def ordered():
+                for c in cams:
+                    R.render_ordered(plan, c, ert=0.999, brick=args.brick, out=out)
+            for _ in range(args.warmup):
+                ordered()
+            ord_ms = _timed(torch, ordered, args.steps) / len(cams)
             # the blend alone, on the partials of the first camera
             cam = cams[0]
             order = native.grid_order(cam, grid, R.pieces(plan)[1])
@@ -628,13 +637,21 @@ def run_mode(args, torch, R, synth):
                 rects.append(r)
                 parts.append(R.render_piece(plan, k, cam, r, ert=0.999, brick=args.brick)
                              if r[2] and r[3] else None)
-            blend = lambda: R.composite(parts, rects, order, 1024, 1024, out=out)  # noqa: E731
-            for _ in range(3):
-                blend()
-            c_ms = _timed(torch, blend, 20)
+            flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
+            c_ms = 0.0
+            for rep in range(23):  # 3 warm-up launches, then 20 timed, L2 flushed before each
+                flush.fill_(float(rep))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                R.composite(parts, rects, order, 1024, 1024, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep >= 3:
+                    c_ms += e0.elapsed_time(e1) / 20
+            del flush
             nbytes = 16 * (sum(r[2] * r[3] for r in rects) + 1024 * 1024)
             # agreement with the one-pass render on the first four cameras
-            d_off = d_on = 0.0
+            d_off = d_on = d_ord = 0.0
             for c in cams[:4]:
                 R.render(vid, tid, c, ert=1.0, brick=args.brick, out=ref)
                 R.render_sortlast(plan, c, ert=1.0, brick=args.brick, out=out)
@@ -642,18 +659,23 @@ def run_mode(args, torch, R, synth):
                 R.render(vid, tid, c, ert=0.999, brick=args.brick, out=ref)
                 R.render_sortlast(plan, c, ert=0.999, brick=args.brick, out=out)
                 d_on = max(d_on, float((out - ref).abs().max()))
+                R.render_ordered(plan, c, ert=0.999, brick=args.brick, out=out)
+                d_ord = max(d_ord, float((out - ref).abs().max()))
             rows.append({
                 "grid": list(grid), "pieces": len(pieces),
                 "visible_pieces": sum(p["vis_hi"] != (0, 0, 0) for p in pieces),
-                "ms_per_frame": ms, "vs_one_pass": ms / base_ms,
+                "sortlast_ms_per_frame": ms, "sortlast_vs_one_pass": ms / base_ms,
+                "ordered_ms_per_frame": ord_ms, "ordered_vs_one_pass": ord_ms / base_ms,
                 "partial_pixels_first_camera": sum(r[2] * r[3] for r in rects),
                 "composite_us": c_ms * 1e3, "composite_gbs": nbytes / (c_ms / 1e3) / 1e9,
                 "composite_frac_of_hbm": nbytes / (c_ms / 1e3) / 1e9 / hbm,
                 "max_abs_diff_vs_one_pass_no_ert": d_off,
-                "max_abs_diff_vs_one_pass_ert": d_on})
+                "max_abs_diff_vs_one_pass_ert": d_on,
+                "max_abs_diff_ordered_vs_one_pass_ert": d_ord})
             R.free_pieces(plan)
         print(json.dumps({
-            "mode": "sortlast", "metric": "ms per frame (pieces + blend) vs the one-pass render",
+            "mode": "sortlast", "metric": "ms per frame of the object-order paths (sort-last: "
+            "pieces + blend; ordered: pieces front to back) vs the one-pass render",
             "data": "synthetic", "config": workload_config(args),
             "one_pass_ms_per_frame": base_ms, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
             "grids": rows}), flush=True)

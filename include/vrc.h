@@ -379,6 +379,17 @@ vrc_status vrc_composite(vrc_ctx *ctx, int K, const float *const *partials_dev,
 vrc_status vrc_render_sortlast(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
                                const vrc_params *params, float *out_dev, void *stream);
 
+/* The object-order pass of one process (the paper's blocks drawn front to back from the
+ * observer, Sec. "Analysis"): the plan's visible pieces are rendered in visibility order into
+ * one running image of (C, T), each ray continuing the colour and transmittance the pieces in
+ * front left and stopping (skipping later pieces) once 1 - T passes params->ert_threshold, as
+ * in the one-pass render; then out_dev (height x width x 4 floats, the format of vrc_render)
+ * gets (C, 1 - T). Equals vrc_render up to float rounding where a ray crosses a piece face.
+ * params->kernel 2..5 is rejected (VRC_ERR_ARG). The running image (16 bytes per pixel) is
+ * owned by the plan. Asynchronous on `stream` unless that image grows. */
+vrc_status vrc_render_ordered(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
+                              const vrc_params *params, float *out_dev, void *stream);
+
 /* Reads and clears the device error word shared by the context's kernels: 0 when no kernel
  * check has fired, else a VRC_ERR_* code. Synchronises `stream`. */
 vrc_status vrc_last_device_error(vrc_ctx *ctx, int *code, void *stream);

@@ -10,6 +10,9 @@
 //   piece_box_kernel    the union of the brick boxes of each piece (its visible box).
 //   composite_kernel    the over operator across the partial images of the pieces, per pixel,
 //                       in a visibility order (C += T C_k, T *= 1 - A_k).
+//   accum_*_kernel      set-up and read-out of the running (C, T) image of an ordered pass,
+//                       in which the pieces are rendered front to back and each ray continues
+//                       (and terminates) across them as in the one-pass render.
 #include <limits.h>
 
 #include "vrc_internal.h"
@@ -133,25 +136,66 @@ __global__ void __launch_bounds__(256) piece_box_kernel(const int16_t *__restric
     }
 }
 
-// One thread per output pixel; the partials are listed front to back.
+// One warp per run of 32 pixels of a row, one thread per pixel. Each warp first marks, with
+// two ballots, the partials whose rectangle meets its run (so a pixel visits only those, front
+// to back in list order), then keeps up to four partial loads in flight per thread; a warp
+// reads 32 consecutive pixels of a partial's row (coalesced). No shared memory, no barrier.
+constexpr int CT_W = 32, CT_H = 8;
 __global__ void __launch_bounds__(256) composite_kernel(const CompositeArgs a,
                                                         float4 *__restrict__ out) {
-    const long npix = (long)a.width * a.height;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < npix;
-         i += (long)gridDim.x * blockDim.x) {
-        const int px = (int)(i % a.width), py = (int)(i / a.width);
-        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
-        for (int k = 0; k < a.K; ++k) {
-            const int x = px - a.rect[k][0], y = py - a.rect[k][1];
-            if ((unsigned)x < (unsigned)a.rect[k][2] && (unsigned)y < (unsigned)a.rect[k][3]) {
-                const float4 p = __ldg(a.part[k] + (long)y * a.rect[k][2] + x);
-                c0 = fmaf(T, p.x, c0);
-                c1 = fmaf(T, p.y, c1);
-                c2 = fmaf(T, p.z, c2);
-                T = T * (1.0f - p.w);
+    const int lane = threadIdx.x & 31;
+    const int px0 = blockIdx.x * CT_W, py = blockIdx.y * CT_H + (threadIdx.x >> 5);
+    if (py >= a.height) return;  // whole warps leave together
+    unsigned long long hits = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = h * 32 + lane;
+        bool hit = false;
+        if (k < a.K) {
+            const int *r = a.rect[k];
+            hit = r[1] <= py && py < r[1] + r[3] && r[0] < px0 + CT_W && px0 < r[0] + r[2];
+        }
+        hits |= (unsigned long long)__ballot_sync(0xffffffffu, hit) << (32 * h);
+    }
+    const int px = px0 + lane;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+    constexpr int U = 4;  // partial loads in flight per thread
+    while (hits) {
+        float4 p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {  // an identity past the last hit and outside a rectangle
+            p[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (hits) {
+                const int k = __ffsll((long long)hits) - 1;
+                hits &= hits - 1ull;
+                const int x = px - a.rect[k][0], y = py - a.rect[k][1];
+                if ((unsigned)x < (unsigned)a.rect[k][2] && px < a.width)
+                    p[u] = __ldg(a.part[k] + (long)y * a.rect[k][2] + x);
             }
         }
-        out[i] = make_float4(c0, c1, c2, 1.0f - T);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c0 = fmaf(T, p[u].x, c0);
+            c1 = fmaf(T, p[u].y, c1);
+            c2 = fmaf(T, p[u].z, c2);
+            T = T * (1.0f - p[u].w);
+        }
+    }
+    if (px < a.width) out[(long)py * a.width + px] = make_float4(c0, c1, c2, 1.0f - T);
+}
+
+__global__ void accum_init_kernel(float4 *__restrict__ a, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x)
+        a[i] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+}
+
+__global__ void accum_finish_kernel(const float4 *__restrict__ a, float4 *__restrict__ out,
+                                    long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x) {
+        const float4 v = a[i];
+        out[i] = make_float4(v.x, v.y, v.z, 1.0f - v.w);
     }
 }
 
@@ -188,8 +232,18 @@ cudaError_t launch_piece_boxes(const int16_t *aabb, const int nb[3], const int *
 }
 
 cudaError_t launch_composite(const CompositeArgs &a, float4 *out, cudaStream_t st) {
-    const long npix = (long)a.width * a.height;
-    composite_kernel<<<grid_for(npix, 256), 256, 0, st>>>(a, out);
+    const dim3 grid((a.width + CT_W - 1) / CT_W, (a.height + CT_H - 1) / CT_H);
+    composite_kernel<<<grid, CT_W * CT_H, 0, st>>>(a, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum_init(float4 *accum, long n, cudaStream_t st) {
+    accum_init_kernel<<<grid_for(n, 256), 256, 0, st>>>(accum, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum_finish(const float4 *accum, float4 *out, long n, cudaStream_t st) {
+    accum_finish_kernel<<<grid_for(n, 256), 256, 0, st>>>(accum, out, n);
     return cudaGetLastError();
 }
 

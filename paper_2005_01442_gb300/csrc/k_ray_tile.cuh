@@ -49,9 +49,22 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     const uint32_t *cells = L.cells;
     const int cwx = L.cwx;
 
+    // output pixel; in an ordered pass over pieces (L.accum) the ray continues the colour and
+    // transmittance the pieces in front left there (full-image pixels, T itself), and a ray
+    // already past the termination threshold casts nothing
+    const long oidx = L.accum ? (long)(py + L.cam.oy) * L.accum_pitch + (px + L.cam.ox)
+                              : (long)py * L.cam.width + px;
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Tr = 1.0f;
+    if (L.accum && valid) {
+        const float4 s = L.accum[oidx];
+        C0 = s.x;
+        C1 = s.y;
+        C2 = s.z;
+        Tr = s.w;
+    }
     RaySetup ray;
     ray.nseg = 0;
-    if (valid) ray_setup(L.cam, L.grid, px, py, ray);
+    if (valid && !(1.0f - Tr > L.grid.ert)) ray_setup(L.cam, L.grid, px, py, ray);
 
     const float step = L.grid.step, thr = L.grid.ert;
     const float inv_step = 1.0f / step;
@@ -59,7 +72,6 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     ray_pos_init(ray, step, rp);
     float Pf[3], df[3], inv_df[3];
     ray_float(rp, Pf, df, inv_df);
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Tr = 1.0f;
     int executed = 0;
     const uint8_t *dist = nullptr;
     if (ESL) {
@@ -163,8 +175,8 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                     // at most one record per pixel, so the two ends never meet: always true
                     if (k < L.split.cap) {
                         const unsigned idx = lng ? k : L.split.cap - 1u - k;
-                        split_store(L.split.rec + (long)idx * SPLIT_REC, rp, j,
-                                    py * L.cam.width + px, C0, C1, C2, Tr);
+                        split_store(L.split.rec + (long)idx * SPLIT_REC, rp, j, (int)oidx,
+                                    C0, C1, C2, Tr);
                         done = true;
                         queued = true;
                     } else {
@@ -219,7 +231,16 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             ++j;
         }
     }
-    if (valid && !queued) L.out[(long)py * L.cam.width + px] = make_float4(C0, C1, C2, 1.0f - Tr);
+    if (valid && !queued) {
+        // in an ordered pass a ray writes back only when it met a sample of this piece:
+        // pieces rendered concurrently are never met by the same ray, so no write of one can
+        // be overwritten by a stale value from another
+        if (L.accum) {
+            if (executed > 0) L.accum[oidx] = make_float4(C0, C1, C2, Tr);
+        } else {
+            L.out[oidx] = make_float4(C0, C1, C2, 1.0f - Tr);
+        }
+    }
 
     if (L.counters) {
         unsigned int nom = (unsigned)ray.nseg, ex = (unsigned)executed;

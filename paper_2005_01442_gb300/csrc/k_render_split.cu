@@ -68,7 +68,12 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 3) split_tail_kernel(RenderL
         if (ESL) dist = L.dist + octant_of(df) * nbricks;
         group_march<ESL, G, MODE>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q,
                                   gbase, RC0, RC1, RC2, RT, executed);
-        if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
+        if (q == 0) {
+            if (L.accum)  // ordered pass: T itself (a queued ray met a sample of the piece)
+                L.accum[pix] = make_float4(RC0, RC1, RC2, RT);
+            else
+                L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
+        }
     }
     if (L.counters) {
         unsigned ex = q == 0 ? (unsigned)executed : 0u;

@@ -90,7 +90,16 @@ struct Plan {
     std::vector<float> cuts;        // interior cut planes, x then y then z
     float4 *partials = nullptr;     // partial images of vrc_render_sortlast
     size_t partial_cap = 0;         // in pixels
+    float4 *accum = nullptr;        // running (C, T) image of vrc_render_ordered
+    size_t accum_cap = 0;           // in pixels
+    // worker streams that render independent pieces concurrently (created on first use),
+    // one completion event each and the caller stream's fork event
+    std::vector<cudaStream_t> workers;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
 };
+
+constexpr int PIECE_WORKERS = 4;
 
 }  // namespace
 
@@ -177,6 +186,15 @@ void free_plan(Plan &p) {
     cudaFree(p.partials);
     p.partials = nullptr;
     p.partial_cap = 0;
+    cudaFree(p.accum);
+    p.accum = nullptr;
+    p.accum_cap = 0;
+    for (auto w : p.workers) cudaStreamDestroy(w);
+    for (auto e : p.done) cudaEventDestroy(e);
+    if (p.fork) cudaEventDestroy(p.fork);
+    p.workers.clear();
+    p.done.clear();
+    p.fork = nullptr;
 }
 
 bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
@@ -398,7 +416,7 @@ vrc_status ensure_aabb(vrc_ctx *ctx, Volume &v, int tf_id, Tf &t, int B, cudaStr
 // pieces one ray can meet (the later one is farther on some axis and no nearer on any). For
 // parallel rays the slab index only grows (or only falls) with the direction's sign.
 vrc_status grid_order(vrc_ctx *ctx, const vrc_camera *cam, const int grid[3], const float *cuts,
-                      int *order) {
+                      int *order, long *keys = nullptr) {
     double f[3], r[3], u[3];
     vrc_status s = camera_frame(ctx, cam, f, r, u);
     if (s != VRC_OK) return s;
@@ -424,7 +442,10 @@ vrc_status grid_order(vrc_ctx *ctx, const vrc_camera *cam, const int grid[3], co
         key[(size_t)k] = {d, k};
     }
     std::stable_sort(key.begin(), key.end());
-    for (int k = 0; k < K; ++k) order[k] = key[(size_t)k].second;
+    for (int k = 0; k < K; ++k) {
+        order[k] = key[(size_t)k].second;
+        if (keys) keys[k] = key[(size_t)k].first;
+    }
     return VRC_OK;
 }
 
@@ -1362,9 +1383,11 @@ vrc_status check_rect(vrc_ctx *ctx, const int rect[4], int width, int height) {
     return VRC_OK;
 }
 
+// Renders a piece for the pixels `rect`: into out_dev (rect-sized), or, with accum set,
+// continuing the running (C, T) image accum (full-image pixels) of an ordered pass.
 vrc_status render_piece(vrc_ctx *ctx, Plan &p, int piece, const vrc_camera *cam,
                         const vrc_params *params, const int rect[4], float *out_dev,
-                        cudaStream_t st) {
+                        cudaStream_t st, float4 *accum = nullptr) {
     if (!params) return fail(ctx, VRC_ERR_ARG, "params is NULL");
     if (params->brick != p.B)
         return fail(ctx, VRC_ERR_ARG, "params.brick (%d) must be the plan's brick size %d",
@@ -1376,15 +1399,70 @@ vrc_status render_piece(vrc_ctx *ctx, Plan &p, int piece, const vrc_camera *cam,
     if (s != VRC_OK) return s;
     if ((s = check_rect(ctx, rect, cam->width, cam->height)) != VRC_OK) return s;
     if (rect[2] == 0 || rect[3] == 0) return VRC_OK;
-    if (!out_dev || ((uintptr_t)out_dev & 15) != 0)
+    if (!accum && (!out_dev || ((uintptr_t)out_dev & 15) != 0))
         return fail(ctx, VRC_ERR_ARG, "out_dev must be non-NULL and 16-byte aligned");
     L.dist = p.pieces[(size_t)piece].dist;
+    L.accum = accum;
+    L.accum_pitch = cam->width;
     L.cam.ox = rect[0];
     L.cam.oy = rect[1];
     L.cam.width = rect[2];
     L.cam.height = rect[3];
     L.out = (float4 *)out_dev;
     return launch_render(ctx, params, L, st);
+}
+
+// Creates the plan's worker streams and events on first use.
+vrc_status plan_workers(vrc_ctx *ctx, Plan &p) {
+    if (!p.workers.empty()) return VRC_OK;
+    CK(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming), "cudaEventCreate");
+    for (int i = 0; i < PIECE_WORKERS; ++i) {
+        cudaStream_t w;
+        cudaEvent_t e;
+        CK(cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking), "cudaStreamCreate");
+        p.workers.push_back(w);
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        p.done.push_back(e);
+    }
+    return VRC_OK;
+}
+
+// Makes every worker stream wait for the work queued on st so far.
+vrc_status fork_workers(vrc_ctx *ctx, Plan &p, cudaStream_t st) {
+    CK(cudaEventRecord(p.fork, st), "fork record");
+    for (auto w : p.workers) CK(cudaStreamWaitEvent(w, p.fork, 0), "fork wait");
+    return VRC_OK;
+}
+
+// Makes st wait for everything queued on the worker streams.
+vrc_status join_workers(vrc_ctx *ctx, Plan &p, cudaStream_t st) {
+    for (size_t i = 0; i < p.workers.size(); ++i) {
+        CK(cudaEventRecord(p.done[i], p.workers[i]), "join record");
+        CK(cudaStreamWaitEvent(st, p.done[i], 0), "join wait");
+    }
+    return VRC_OK;
+}
+
+// The visibility order, per-piece rectangles and keys of a plan for one camera.
+vrc_status plan_view(vrc_ctx *ctx, Plan &p, const vrc_camera *cam, std::vector<int> &order,
+                     std::vector<int> &rects, std::vector<long> &keys) {
+    const int K = (int)p.pieces.size();
+    order.assign((size_t)K, 0);
+    rects.assign((size_t)4 * K, 0);
+    keys.assign((size_t)K, 0);
+    vrc_status s = grid_order(ctx, cam, p.grid, p.cuts.data(), order.data(), keys.data());
+    if (s != VRC_OK) return s;
+    Volume *v = get_vol(ctx, p.vol_id);
+    for (int k = 0; k < K; ++k) {
+        const vrc_piece &pi = p.pieces[(size_t)k].info;
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {  // the points with floor(p) in [vis_lo, vis_hi)
+            lo[a] = fmaxf((float)pi.vis_lo[a], -0.5f);
+            hi[a] = fminf((float)pi.vis_hi[a], (float)v->n[a] - 0.5f);
+        }
+        if ((s = box_rect(ctx, cam, lo, hi, &rects[(size_t)4 * k])) != VRC_OK) return s;
+    }
+    return VRC_OK;
 }
 
 }  // namespace
@@ -1612,20 +1690,11 @@ vrc_status vrc_render_sortlast(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int K = (int)p->pieces.size();
-    std::vector<int> order((size_t)K), rects((size_t)4 * K);
-    if ((s = grid_order(ctx, cam, p->grid, p->cuts.data(), order.data())) != VRC_OK) return s;
-    Volume *v = get_vol(ctx, p->vol_id);
+    std::vector<int> order, rects;
+    std::vector<long> keys;
+    if ((s = plan_view(ctx, *p, cam, order, rects, keys)) != VRC_OK) return s;
     size_t total = 0;
-    for (int k = 0; k < K; ++k) {
-        const vrc_piece &pi = p->pieces[(size_t)k].info;
-        float lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {  // the points with floor(p) in [vis_lo, vis_hi)
-            lo[a] = fmaxf((float)pi.vis_lo[a], -0.5f);
-            hi[a] = fminf((float)pi.vis_hi[a], (float)v->n[a] - 0.5f);
-        }
-        if ((s = box_rect(ctx, cam, lo, hi, &rects[(size_t)4 * k])) != VRC_OK) return s;
-        total += (size_t)rects[(size_t)4 * k + 2] * rects[(size_t)4 * k + 3];
-    }
+    for (int k = 0; k < K; ++k) total += (size_t)rects[(size_t)4 * k + 2] * rects[(size_t)4 * k + 3];
     if (p->partial_cap < total) {
         CK(cudaStreamSynchronize(st), "sync before partial realloc");
         cudaFree(p->partials);
@@ -1634,18 +1703,80 @@ vrc_status vrc_render_sortlast(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
         CK(cudaMalloc(&p->partials, total * sizeof(float4)), "cudaMalloc(partials)");
         p->partial_cap = total;
     }
+    if ((s = plan_workers(ctx, *p)) != VRC_OK) return s;
+    if ((s = fork_workers(ctx, *p, st)) != VRC_OK) return s;
+    // the partials are independent: visible pieces go round-robin to the worker streams
     std::vector<const float *> parts((size_t)K, nullptr);
     size_t off = 0;
+    int n = 0;
     for (int k = 0; k < K; ++k) {
         const int *r = &rects[(size_t)4 * k];
         if (r[2] == 0 || r[3] == 0) continue;
         parts[(size_t)k] = (const float *)(p->partials + off);
-        s = render_piece(ctx, *p, k, cam, params, r, (float *)(p->partials + off), st);
-        if (s != VRC_OK) return s;
+        s = render_piece(ctx, *p, k, cam, params, r, (float *)(p->partials + off),
+                         p->workers[(size_t)(n++ % PIECE_WORKERS)]);
+        if (s != VRC_OK) {
+            join_workers(ctx, *p, st);
+            return s;
+        }
         off += (size_t)r[2] * r[3];
     }
+    if ((s = join_workers(ctx, *p, st)) != VRC_OK) return s;
     return vrc_composite(ctx, K, parts.data(), rects.data(), order.data(), cam->width,
                          cam->height, out_dev, stream);
+}
+
+vrc_status vrc_render_ordered(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
+                              const vrc_params *params, float *out_dev, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    Plan *p = get_plan(ctx, plan_id);
+    if (!p) return fail(ctx, VRC_ERR_ARG, "unknown plan id %d", plan_id);
+    vrc_status s = plan_fresh(ctx, *p);
+    if (s != VRC_OK) return s;
+    if (!out_dev || ((uintptr_t)out_dev & 15) != 0)
+        return fail(ctx, VRC_ERR_ARG, "out_dev must be non-NULL and 16-byte aligned");
+    if (params && params->kernel >= 2 && params->kernel <= 5)
+        return fail(ctx, VRC_ERR_ARG, "an ordered pass runs the split or per-ray kernel only");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = (int)p->pieces.size();
+    std::vector<int> order, rects;
+    std::vector<long> keys;
+    if ((s = plan_view(ctx, *p, cam, order, rects, keys)) != VRC_OK) return s;
+    const size_t npix = (size_t)cam->width * cam->height;
+    if (p->accum_cap < npix) {
+        CK(cudaStreamSynchronize(st), "sync before running image realloc");
+        cudaFree(p->accum);
+        p->accum = nullptr;
+        p->accum_cap = 0;
+        CK(cudaMalloc(&p->accum, npix * sizeof(float4)), "cudaMalloc(running image)");
+        p->accum_cap = npix;
+    }
+    if ((s = plan_workers(ctx, *p)) != VRC_OK) return s;
+    CK(launch_accum_init(p->accum, (long)npix, st), "running image launch");
+    // front to back by levels of the order's key: no ray meets two pieces of one level, so
+    // a level's pieces run concurrently on the worker streams; levels run in order
+    for (int i = 0; i < K;) {
+        int e = i;
+        while (e < K && keys[(size_t)e] == keys[(size_t)i]) ++e;
+        if ((s = fork_workers(ctx, *p, st)) != VRC_OK) return s;
+        int n = 0;
+        for (int j = i; j < e; ++j) {
+            const int k = order[(size_t)j];
+            const int *r = &rects[(size_t)4 * k];
+            if (r[2] == 0 || r[3] == 0) continue;
+            s = render_piece(ctx, *p, k, cam, params, r, nullptr,
+                             p->workers[(size_t)(n++ % PIECE_WORKERS)], p->accum);
+            if (s != VRC_OK) {
+                join_workers(ctx, *p, st);
+                return s;
+            }
+        }
+        if ((s = join_workers(ctx, *p, st)) != VRC_OK) return s;
+        i = e;
+    }
+    CK(launch_accum_finish(p->accum, (float4 *)out_dev, (long)npix, st), "running image launch");
+    return VRC_OK;
 }
 
 }  // extern "C"

@@ -404,6 +404,8 @@ struct RenderLaunch {
     int mode;                      // interpolation / classification variant (MODE_*)
     Phong phong;                   // MODE_CUBIC_PHONG only
     const float4 *preint;          // MODE_PREINT only: the table for slabs of length step
+    float4 *accum;                 // NULL, or the running (C, T) image of an ordered pass
+    int accum_pitch;               // its pixels per row (the full image's width)
 };
 
 // Bit of the cell holding sample base ip (ip in [-1, n-1]); 0: the sample's opacity is zero.
@@ -488,6 +490,9 @@ cudaError_t launch_piece_mask(const uint8_t *occ, const int nb[3], const int blo
 cudaError_t launch_piece_boxes(const int16_t *aabb, const int nb[3], const int *bricks_k, int K,
                                int *out, cudaStream_t st);
 cudaError_t launch_composite(const CompositeArgs &a, float4 *out, cudaStream_t st);
+// ordered pass: accum = (0, 0, 0, 1) everywhere; out = (C, 1 - T) of accum
+cudaError_t launch_accum_init(float4 *accum, long n, cudaStream_t st);
+cudaError_t launch_accum_finish(const float4 *accum, float4 *out, long n, cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
 cudaError_t launch_render_warp(const RenderLaunch &L, int lanes_per_ray, cudaStream_t st);
 // Both phases of the split render; L.split.head must be zero (it is left nonzero).

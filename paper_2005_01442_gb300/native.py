@@ -28,7 +28,7 @@ EXPORTS = [
     "vrc_server_pump", "vrc_server_poll", "vrc_server_destroy", "vrc_last_device_error",
     "vrc_last_error_message", "vrc_status_str", "vrc_version", "vrc_aabbs_get",
     "vrc_pieces_build", "vrc_pieces_get", "vrc_pieces_free", "vrc_grid_order", "vrc_box_rect",
-    "vrc_render_piece", "vrc_composite", "vrc_render_sortlast",
+    "vrc_render_piece", "vrc_composite", "vrc_render_sortlast", "vrc_render_ordered",
 ]
 
 
@@ -117,6 +117,8 @@ def load(build_if_missing: bool = False):
     L.vrc_composite.argtypes = [vp, ip, C.POINTER(vp), pint, pint, ip, ip, vp, vp]
     L.vrc_render_sortlast.argtypes = [vp, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                       vp]
+    L.vrc_render_ordered.argtypes = [vp, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
+                                     vp]
     L.vrc_last_device_error.argtypes = [vp, pint, vp]
     L.vrc_last_error_message.argtypes = [vp]
     L.vrc_last_error_message.restype = C.c_char_p

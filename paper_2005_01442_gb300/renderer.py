@@ -303,6 +303,23 @@ class Renderer:
                                               C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
+    def render_ordered(self, plan_id: int, cam, step: float = 0.5, ert: float = 1.0,
+                       brick: int = 8, out=None, stream=None, kernel: int = 0, interp: int = 0,
+                       preclass: int = 0, phong=None):
+        """The image of `cam` rendered piece by piece front to back through one running
+        image, rays terminating across pieces."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == cam.height * cam.width * 4
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, 0)
+        self._ck(self.lib.vrc_render_ordered(self.ctx, int(plan_id), C.byref(cs), C.byref(ps),
+                                             C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
     def last_device_error(self, stream=None) -> int:
         code = C.c_int()
         self._ck(self.lib.vrc_last_device_error(self.ctx, C.byref(code), _stream_ptr(stream)))

@@ -260,6 +260,60 @@ def test_invisible_pieces_are_skipped(R, orc, torch):
     R.free_tf(tid)
 
 
+# ------------------------------------------------------- ordered pass (front to back, ERT)
+
+@pytest.mark.parametrize("grid", [(2, 2, 2), (3, 1, 2), (4, 4, 2)])
+@pytest.mark.parametrize("ert", [1.0, 0.999])
+def test_ordered_pass_matches_oracle_one_pass_render(R, orc, torch, grid, ert):
+    # Pieces drawn front to back through one running image, rays terminating across them:
+    # the one-pass image of the oracle, early termination included.
+    vol = synth.ct_volume((48, 64, 72), seed=28)
+    B = 8
+    tf = synth.tf_ct().copy()
+    tf[:, 3] = np.minimum(tf[:, 3] * 3.0, 0.95)
+    vid, tid, _ = _scene(R, vol, B, tf)
+    dims = _dims(vol)
+    plan = R.build_pieces(vid, tid, B, grid)
+    cams = list(synth.orbit_cameras(14, 2, dims, 48, 40)) + [synth.ortho_z_camera(dims, 48, 40)]
+    for cam in cams:
+        img = R.render_ordered(plan, cam, 0.5, ert, B).cpu().numpy().astype(np.float64)
+        ref, mg = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=ert, brick=B,
+                             return_margin=True)
+        d = np.abs(img - ref).max(axis=-1)
+        flagged = mg < ERT_MARGIN
+        assert d[~flagged].max(initial=0.0) <= TOL, d.max()
+        assert d[flagged].max(initial=0.0) <= 1e-3
+        assert ref[..., 3].max() > 0.9
+    R.free_pieces(plan)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+@pytest.mark.parametrize("variant", [{}, {"interp": 1}, {"preclass": 1},
+                                     {"phong": (0.3, 0.6, 0.2, 16.0)}, {"kernel": 1}])
+def test_ordered_pass_equals_one_pass_render(R, torch, variant):
+    vol = synth.ct_volume((64, 80, 96), seed=29)
+    B = 8
+    vid, tid, _ = _scene(R, vol, B)
+    dims = _dims(vol)
+    plan = R.build_pieces(vid, tid, B, (3, 2, 2))
+    one_plan = R.build_pieces(vid, tid, B, (1, 1, 1))
+    for cam in list(synth.orbit_cameras(15, 3, dims, 96, 80)) + [synth.ortho_z_camera(dims, 96, 80)]:
+        for ert in (1.0, 0.999):
+            one = R.render(vid, tid, cam, 0.5, ert, B, **variant).cpu().numpy()
+            od = R.render_ordered(plan, cam, 0.5, ert, B, **variant).cpu().numpy()
+            d = np.abs(od - one).max(axis=-1)
+            # a ray whose opacity crosses the threshold within float rounding may stop one
+            # sample apart (at most the termination bound)
+            assert (d > 2e-5).mean() <= 1e-3 and d.max() <= 1e-3, d.max()
+            single = R.render_ordered(one_plan, cam, 0.5, ert, B, **variant).cpu().numpy()
+            assert np.array_equal(single, one)  # one piece: the one-pass render bit for bit
+    R.free_pieces(plan)
+    R.free_pieces(one_plan)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
 # --------------------------------------------------------------------------- rejections
 
 def test_piece_calls_reject_bad_arguments(R, torch):
@@ -284,6 +338,8 @@ def test_piece_calls_reject_bad_arguments(R, torch):
         R.render_piece(plan, 0, cam, (0, 0, 32, 24), 0.5, 1.0, 16)  # brick size differs
     with pytest.raises(VrcError):
         R.render_sortlast(plan, cam, 0.5, 1.0, 0)
+    with pytest.raises(VrcError):
+        R.render_ordered(plan, cam, 0.5, 1.0, B, kernel=3)  # lane-group kernels
     a = torch.zeros((24, 32, 4), device="cuda")
     with pytest.raises(VrcError):
         R.composite([a, a], [(0, 0, 32, 24)] * 2, [0, 0], 32, 24)  # not a permutation
