@@ -13,7 +13,8 @@ and nominal Gsamples/s ride along. `roofline` reports one render call (the split
 kernels) against the FP32 issue roof (152 SMs x 128 lanes x 2 flop x 2.07 GHz), using the
 algorithmic flop count per executed sample. `cpu_baseline` times the FP64 oracle on host cores on a
 bounded sample of the same workload. `e2e` repeats the measurement through
-vrc_render_host (image read back to pinned host memory inside the timed region).
+vrc_render_host_batch (each step's images read back to pinned host memory inside the timed
+region, each frame's copy overlapping the next frame's render).
 
 `--impl reference` times the FP64 CPU oracle itself on the same workload (bounded samples).
 """
@@ -348,22 +349,22 @@ def main():
         host = torch.empty((args.cameras, 1024, 1024, 4), dtype=torch.float32, pin_memory=True)
         for _ in range(2):
             R.build_bricks(vid, B)
-            for i, cam in enumerate(cams):
-                R.render_host(vid, tid, cam, ert=0.999, brick=B, out=host[i], kernel=args.kernel)
+            R.render_host_batch(vid, tid, cams, out=host, ert=0.999, brick=B, kernel=args.kernel)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             R.build_bricks(vid, B)
-            for i, cam in enumerate(cams):
-                R.render_host(vid, tid, cam, ert=0.999, brick=B, out=host[i], kernel=args.kernel)
+            R.render_host_batch(vid, tid, cams, out=host, ert=0.999, brick=B, kernel=args.kernel)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": world * executed * args.steps / e2e_s / 1e9, "unit": "Gsamples/s",
                "h2d_bytes_per_step": args.cameras * 60,  # vrc_camera records passed by value
                "d2h_bytes_per_step": args.cameras * 1024 * 1024 * 16,
-               "api": "vrc_render_host (pinned host image, copy inside the timed region)"}
+               "api": "vrc_render_host_batch (the step's cameras in one call; pinned host "
+                      "images, each read back while the next frame renders, inside the timed "
+                      "region)"}
 
     clocks = sampler.summary()
     sampler.stop()

@@ -215,6 +215,18 @@ vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam
 vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                            const vrc_params *params, float *out_rgba_host, void *stream);
 
+/* vrc_render_host for n cameras in one call (a client's sequence of frames): out_rgba_host[i]
+ * receives the image of cams[i] (height x width x 4 floats each; page-locked memory lets
+ * the copies run asynchronously). The device renders frame i + 1 while a copy stream owned by
+ * the context reads frame i back, through two device images the context owns (grown to the
+ * largest frame), so the image transfers overlap the renders. Images equal vrc_render's bit
+ * for bit. Synchronises `stream`; n = 0 does nothing. Image sizes and pointers are checked
+ * before anything is launched; a failure while rendering camera i returns its status after
+ * the frames before it have been copied. */
+vrc_status vrc_render_host_batch(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cams,
+                                 int n, const vrc_params *params, float *const *out_rgba_host,
+                                 void *stream);
+
 /* Reverse mode of vrc_render (same volume, transfer function, camera and parameters):
  * given grad_out_dev = dL/d(image) (height x width x 4 floats, 16-byte aligned), ADDS
  * dL/d(table) to grad_tf_dev (256 x 4 floats) and, when grad_vol_dev is not NULL,

@@ -114,6 +114,11 @@ struct vrc_ctx {
     size_t host_img_bytes = 0;
     std::map<cudaStream_t, SplitBuf> split;  // split-render queues by stream
     std::map<int, Plan> plans;               // piece grids (vrc_pieces_build)
+    // vrc_render_host_batch: two device images, a copy stream and their events
+    float4 *batch_img[2] = {nullptr, nullptr};
+    size_t batch_bytes = 0;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
     unsigned tf_version_counter = 0;
 };
 
@@ -683,6 +688,12 @@ vrc_status vrc_destroy(vrc_ctx *ctx) {
     cudaFree(ctx->host_img);
     for (auto &kv : ctx->split) cudaFree(kv.second.base);
     for (auto &kv : ctx->plans) free_plan(kv.second);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(ctx->batch_img[b]);
+        if (ctx->ev_rendered[b]) cudaEventDestroy(ctx->ev_rendered[b]);
+        if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
+    }
+    if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
     delete ctx;
     return VRC_OK;
 }
@@ -984,6 +995,70 @@ vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera
     CK(cudaMemcpyAsync(out_rgba_host, ctx->host_img, bytes, cudaMemcpyDeviceToHost, st),
        "image copy");
     CK(cudaStreamSynchronize(st), "image copy sync");
+    return VRC_OK;
+}
+
+vrc_status vrc_render_host_batch(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cams,
+                                 int n, const vrc_params *params, float *const *out_rgba_host,
+                                 void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (n < 0) return fail(ctx, VRC_ERR_ARG, "n must be >= 0");
+    if (n == 0) return VRC_OK;
+    if (!cams || !out_rgba_host) return fail(ctx, VRC_ERR_ARG, "cams and out_rgba_host must be non-NULL");
+    size_t bytes = 0;
+    for (int i = 0; i < n; ++i) {
+        const vrc_camera *c = &cams[i];
+        if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768)
+            return fail(ctx, VRC_ERR_ARG, "image size of camera %d out of range", i);
+        if (!out_rgba_host[i]) return fail(ctx, VRC_ERR_ARG, "out_rgba_host[%d] is NULL", i);
+        bytes = std::max(bytes, (size_t)c->width * c->height * sizeof(float4));
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->copy_st) {
+        CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaEventCreateWithFlags(&ctx->ev_rendered[b], cudaEventDisableTiming), "cudaEventCreate");
+            CK(cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    if (ctx->batch_bytes < bytes) {
+        CK(cudaStreamSynchronize(ctx->copy_st), "sync before image realloc");
+        CK(cudaStreamSynchronize(st), "sync before image realloc");
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(ctx->batch_img[b]);
+            ctx->batch_img[b] = nullptr;
+        }
+        ctx->batch_bytes = 0;
+        for (int b = 0; b < 2; ++b) CK(cudaMalloc(&ctx->batch_img[b], bytes), "cudaMalloc(image)");
+        ctx->batch_bytes = bytes;
+    }
+    // frame i renders into image i % 2 on `stream` once the copy of frame i - 2 has left it;
+    // the copy stream reads frame i back while frame i + 1 renders
+    vrc_status s = VRC_OK;
+    for (int i = 0; i < n && s == VRC_OK; ++i) {
+        const int b = i & 1;
+        if (i >= 2) CK(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0), "batch wait");
+        RenderLaunch L;
+        s = prepare_render(ctx, vol_id, tf_id, &cams[i], params, st, L);
+        if (s != VRC_OK) break;
+        L.out = ctx->batch_img[b];
+        L.counters = nullptr;
+        s = launch_render(ctx, params, L, st);
+        if (s != VRC_OK) break;
+        CK(cudaEventRecord(ctx->ev_rendered[b], st), "batch record");
+        CK(cudaStreamWaitEvent(ctx->copy_st, ctx->ev_rendered[b], 0), "batch wait");
+        CK(cudaMemcpyAsync(out_rgba_host[i], ctx->batch_img[b],
+                           (size_t)cams[i].width * cams[i].height * sizeof(float4),
+                           cudaMemcpyDeviceToHost, ctx->copy_st),
+           "image copy");
+        CK(cudaEventRecord(ctx->ev_copied[b], ctx->copy_st), "batch record");
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(ctx->copy_st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s != VRC_OK) return s;
+    if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "image copy sync");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "render sync");
     return VRC_OK;
 }
 

@@ -29,6 +29,7 @@ EXPORTS = [
     "vrc_last_error_message", "vrc_status_str", "vrc_version", "vrc_aabbs_get",
     "vrc_pieces_build", "vrc_pieces_get", "vrc_pieces_free", "vrc_grid_order", "vrc_box_rect",
     "vrc_render_piece", "vrc_composite", "vrc_render_sortlast", "vrc_render_ordered",
+    "vrc_render_host_batch",
 ]
 
 
@@ -117,6 +118,8 @@ def load(build_if_missing: bool = False):
     L.vrc_composite.argtypes = [vp, ip, C.POINTER(vp), pint, pint, ip, ip, vp, vp]
     L.vrc_render_sortlast.argtypes = [vp, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                       vp]
+    L.vrc_render_host_batch.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), ip,
+                                        C.POINTER(vrc_params), C.POINTER(vp), vp]
     L.vrc_render_ordered.argtypes = [vp, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                      vp]
     L.vrc_last_device_error.argtypes = [vp, pint, vp]

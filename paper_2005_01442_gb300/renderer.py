@@ -202,6 +202,27 @@ class Renderer:
                                           C.byref(ps), C.c_void_p(ptr), _stream_ptr(stream)))
         return out
 
+    def render_host_batch(self, vol_id: int, tid: int, cams, out=None, step: float = 0.5,
+                          ert: float = 1.0, brick: int = 0, stream=None, kernel: int = 0,
+                          interp: int = 0, preclass: int = 0, phong=None, preint: int = 0):
+        """End-to-end renders of several cameras into host memory, the read-back of each frame
+        overlapping the render of the next. `out`: a list of host tensors/arrays (one per
+        camera, (H, W, 4) float32) or one (n, H, W, 4) pinned tensor for equal-size cameras;
+        allocated (pinned) when None."""
+        torch = _torch()
+        n = len(cams)
+        if out is None:
+            out = [torch.empty((c.height, c.width, 4), dtype=torch.float32, pin_memory=True)
+                   for c in cams]
+        items = [out[i] for i in range(n)]
+        ptrs = (C.c_void_p * max(n, 1))(*[(t.data_ptr() if isinstance(t, torch.Tensor)
+                                           else t.ctypes.data) for t in items])
+        cs = (native.vrc_camera * max(n, 1))(*[native.camera_struct(c) for c in cams])
+        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, preint)
+        self._ck(self.lib.vrc_render_host_batch(self.ctx, int(vol_id), int(tid), cs, n,
+                                                C.byref(ps), ptrs, _stream_ptr(stream)))
+        return out
+
     def render_backward(self, vol_id: int, tf_id: int, cam, grad_out, grad_tf, grad_vol=None,
                         step: float = 0.5, ert: float = 1.0, brick: int = 0, seg_len: int = 64,
                         stream=None):

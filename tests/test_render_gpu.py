@@ -247,6 +247,28 @@ def test_render_host_matches_device(R, torch):
     R.free_volume(vid)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_render_host_batch_matches_device(R, torch, kernel):
+    # double-buffered read-back: every frame equals its device render bit for bit, for mixed
+    # image sizes (the buffers grow mid-way), one camera, and no camera
+    import numpy as np
+    vol = _ct_small(seed=9)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    dims = synth.dims_of(vol)
+    cams = (list(synth.orbit_cameras(45, 3, dims, 40, 32)) + list(synth.orbit_cameras(46, 2, dims, 72, 56))
+            + [synth.ortho_z_camera(dims, 33, 17)])
+    outs = R.render_host_batch(vid, tid, cams, ert=0.999, brick=8, kernel=kernel)
+    for c, h in zip(cams, outs):
+        assert torch.equal(R.render(vid, tid, c, ert=0.999, brick=8, kernel=kernel).cpu(), h)
+    one = [np.zeros((cams[0].height, cams[0].width, 4), np.float32)]
+    R.render_host_batch(vid, tid, cams[:1], out=one, ert=0.999, brick=8, kernel=kernel)
+    assert np.array_equal(one[0], R.render(vid, tid, cams[0], ert=0.999, brick=8).cpu().numpy())
+    assert R.render_host_batch(vid, tid, [], ert=0.999, brick=8) == []
+    R.free_volume(vid)
+
+
 # --------------------------------------------------------- full-size CT, sampled pixels
 
 @pytest.fixture(scope="module")
