@@ -264,7 +264,8 @@ def test_render_host_batch_matches_device(R, torch, kernel):
         assert torch.equal(R.render(vid, tid, c, ert=0.999, brick=8, kernel=kernel).cpu(), h)
     one = [np.zeros((cams[0].height, cams[0].width, 4), np.float32)]
     R.render_host_batch(vid, tid, cams[:1], out=one, ert=0.999, brick=8, kernel=kernel)
-    assert np.array_equal(one[0], R.render(vid, tid, cams[0], ert=0.999, brick=8).cpu().numpy())
+    assert np.array_equal(one[0], R.render(vid, tid, cams[0], ert=0.999, brick=8,
+                                           kernel=kernel).cpu().numpy())
     assert R.render_host_batch(vid, tid, [], ert=0.999, brick=8) == []
     R.free_volume(vid)
 
