@@ -37,7 +37,7 @@ FLOPS_PER_SAMPLE = 230      # algorithmic FP32 flops per executed sample (FMA = 
 # DRAM bytes (read + write) of one default render call (both split-render kernels) on this
 # workload with 8^3 bricks, from the ncu capture summarised in
 # profiles/split_render_ct512x400_1024sq_B8.md; None for any other kernel or brick size.
-TRAFFIC_PER_RENDER_B8 = 70.50e6
+TRAFFIC_PER_RENDER_B8 = 73.0e6
 SM_COUNT_NOMINAL = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
