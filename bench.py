@@ -375,6 +375,7 @@ def main():
     peak = sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     line = None
     if rank == 0:
+        sgemm = fp32_sgemm_tflops(torch, dev)  # after the timed region
         cpu = None
         if not args.no_cpu_baseline:
             # a bounded sample of the step (~10 s of host work): whole frames, cameras in
@@ -407,7 +408,9 @@ def main():
                          "kernel": ("one render call: split_head_kernel + split_tail_kernel"
                                     if args.kernel in (0, 6) else f"render kernel {args.kernel}"),
                          "basis": f"{FLOPS_PER_SAMPLE} flop/executed sample; peak = {sms} SMs x "
-                                  f"{FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
+                                  f"{FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
+                         "fp32_sgemm_tflops_measured": sgemm,
+                         "frac_of_sgemm": (achieved / sgemm) if sgemm else None},
             "cpu_baseline": cpu, "e2e": e2e,
             # bricks, occupancy, 3 summed-volume passes, distance, cell mask; per frame the
             # split render's two kernels (one for the per-ray kernel)
@@ -460,6 +463,23 @@ def image_quality(img, ref):
         m = ((2 * ma * mb + c1) * (2 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2))
         ss.append(float(m.mean()))
     return psnr, float(np.mean(ss))
+
+
+def fp32_sgemm_tflops(torch, dev, n=8192, reps=5):
+    """Measured FP32 FMA rate of the CUDA cores: a cuBLAS SGEMM with TF32 off (context for the
+    ALU roof, which stays the unit-count figure)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        for _ in range(2):
+            a @ b
+        ms = _timed(torch, lambda: a @ b, reps)
+        del a, b
+        return 2.0 * n ** 3 / (ms / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def _timed(torch, fn, reps):
