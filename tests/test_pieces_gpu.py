@@ -352,3 +352,51 @@ def test_piece_calls_reject_bad_arguments(R, torch):
         R.render_sortlast(plan, cam, 0.5, 1.0, B)
     R.free_volume(vid)
     R.free_tf(tid)
+
+
+# ------------------------------------------------------------- full-size CT, sampled pixels
+
+def test_full_size_pieces_match_oracle_on_sampled_pixels(R, orc, torch):
+    # 512 x 512 x 400 CT at 1024^2, 2 x 2 x 2 pieces of 8^3 bricks: the blended image equals
+    # the one-pass render to float32 rounding without termination (a property at any size),
+    # and on 192 seeded pixels the sort-last and ordered images match the oracle's per-pixel
+    # blend of its piece partials (sort-last) and its one-pass render (ordered), with
+    # termination.
+    vol = synth.ct_volume()
+    dims = _dims(vol)
+    B = 8
+    vid, tid, tf = _scene(R, vol, B)
+    plan = R.build_pieces(vid, tid, B, (2, 2, 2))
+    pieces, _ = R.pieces(plan)
+    cam = synth.orbit_cameras(4, 1, dims, 1024, 1024)[0]
+    one = R.render(vid, tid, cam, 0.5, 1.0, B).cpu().numpy()
+    sl = R.render_sortlast(plan, cam, 0.5, 1.0, B).cpu().numpy()
+    assert np.abs(sl - one).max() <= 2e-5
+    rng = np.random.default_rng(47)
+    a = one[..., 3]
+    cand = np.argwhere(a > 0.05)
+    pix = [(int(x), int(y)) for y, x in cand[rng.choice(len(cand), 160, replace=False)]]
+    pix += [(int(x), int(y)) for x, y in zip(rng.integers(0, 1024, 32), rng.integers(0, 1024, 32))]
+    sl = R.render_sortlast(plan, cam, 0.5, 0.999, B).cpu().numpy()
+    od = R.render_ordered(plan, cam, 0.5, 0.999, B).cpu().numpy()
+    parts, flagged = [], np.zeros(len(pix), bool)
+    for p in pieces:
+        part, mg = orc.render_piece(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, B,
+                                    p["brick_lo"], p["brick_hi"], ert=0.999, pixels=pix,
+                                    return_margin=True)
+        parts.append(part)
+        flagged |= mg < ERT_MARGIN
+    boxes = [(p["cell_lo"], p["cell_hi"]) for p in pieces]
+    ref = orc.composite(np.stack(parts), orc.pixel_piece_order(cam, dims, boxes, pix))
+    got = np.array([sl[y, x] for x, y in pix], np.float64)
+    d = np.abs(got - ref).max(axis=-1)
+    assert d[~flagged].max(initial=0.0) <= TOL and d[flagged].max(initial=0.0) <= 2e-3
+    ref1, mg1 = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=0.999, brick=B,
+                           pixels=pix, return_margin=True)
+    got1 = np.array([od[y, x] for x, y in pix], np.float64)
+    d1 = np.abs(got1 - ref1).max(axis=-1)
+    f1 = mg1 < ERT_MARGIN
+    assert d1[~f1].max(initial=0.0) <= TOL and d1[f1].max(initial=0.0) <= 1e-3
+    R.free_pieces(plan)
+    R.free_volume(vid)
+    R.free_tf(tid)
