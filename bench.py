@@ -10,11 +10,15 @@ L2 is flushed (a 256 MB write) before every step, outside the step's events.
 Printed: one JSON line on rank 0. `value` is executed samples per second (Gsamples/s, all
 ranks; executed = samples in occupied bricks up to termination, the oracle's count); Mrays/s
 and nominal Gsamples/s ride along. `roofline` reports one render call (the split render's two
-kernels) against the FP32 issue roof (152 SMs x 128 lanes x 2 flop x 2.07 GHz), using the
-algorithmic flop count per executed sample. `cpu_baseline` times the FP64 oracle on host cores on a
-bounded sample of the same workload. `e2e` repeats the measurement through
-vrc_render_host_batch (each step's images read back to pinned host memory inside the timed
-region, each frame's copy overlapping the next frame's render).
+kernels) against the stencil's bound max(N F / P_fp32, N G / BW_L1): F = 230 flop and G = 128
+bytes (64 int16 taps) per sample, P_fp32 and BW_L1 the lower of this device's measured rates
+(vrc_microbench) and its unit counts (152 SMs x 128 lanes x 2 flop, x 128 bytes, at 2.07 GHz);
+`frac` counts executed samples, `frac_resampled` only those resampled. `dense_tf` repeats the
+frames with a transfer function that makes soft tissue semi-transparent (long rays, nearly all
+samples resampled). `cpu_baseline` times the FP64 oracle on host cores on a bounded sample of
+the same workload. `e2e` repeats the measurement through vrc_render_host_batch (each step's
+images read back to pinned host memory inside the timed region, each frame's copy overlapping
+the next frame's render).
 
 `--impl reference` times the FP64 CPU oracle itself on the same workload (bounded samples).
 """
@@ -33,13 +37,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FLOPS_PER_SAMPLE = 230      # algorithmic FP32 flops per executed sample (FMA = 2)
-# DRAM bytes (read + write) of one default render call (both split-render kernels) on this
-# workload with 8^3 bricks, from the ncu capture summarised in
-# profiles/split_render_ct512x400_1024sq_B8.md; None for any other kernel or brick size.
-TRAFFIC_PER_RENDER_B8 = 73.0e6
-SM_COUNT_NOMINAL = 152
+FLOPS_PER_SAMPLE = 230        # algorithmic FP32 flops per sample (FMA = 2)
+GATHER_BYTES_PER_SAMPLE = 128  # 64 int16 taps: the least a sample reads from on-chip memory
 FP32_LANES = 128
+L1_BYTES_PER_CLK = 128
 SM_MAX_MHZ = 2070.0
 METRIC = ("Gsamples/s & Mrays/s (512²×400 CT, 1024² img) vs roofline; "
           "p50/p99 req latency")
@@ -54,6 +55,7 @@ def parse():
     p.add_argument("--brick", type=int, default=8)
     p.add_argument("--cameras", type=int, default=16)
     p.add_argument("--kernel", type=int, default=0)
+    p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
@@ -109,6 +111,10 @@ class ClockSampler:
     def mark(self, on: bool):
         with self.lock:
             self.active = on
+
+    def rows_clear(self):
+        with self.lock:
+            self.rows = []
 
     def stop(self):
         if self.proc:
@@ -213,6 +219,45 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def measure_peaks(R, sms: int) -> dict:
+    """The stencil's two roofs on this device: measured (vrc_microbench) and unit-count figures,
+    and the lower of the two, which the roofline divides by."""
+    spec_fp32 = sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+    spec_l1 = sms * L1_BYTES_PER_CLK * SM_MAX_MHZ * 1e6
+    fma, l1, lds = R.microbench(0), R.microbench(1), R.microbench(2)
+    return {"fp32_tflops": min(fma, spec_fp32) / 1e12, "fp32_tflops_measured": fma / 1e12,
+            "fp32_tflops_spec": spec_fp32 / 1e12,
+            "l1_gbs": min(l1, spec_l1) / 1e9, "l1_gbs_measured": l1 / 1e9,
+            "lds_gbs_measured": lds / 1e9, "l1_gbs_spec": spec_l1 / 1e9,
+            "source": "min(measured vrc_microbench, unit count at 2070 MHz); "
+                      f"{sms} SMs"}
+
+
+def roofline(executed: int, resampled: int, launch_ms: float, peaks: dict, kernel: str) -> dict:
+    """Roofline of one render call: max(N F / P_fp32, N G / BW_L1) over its CUDA-event time,
+    N = executed samples (`frac`) or resampled samples (`frac_resampled`)."""
+    t = launch_ms / 1e3
+    p_alu, p_l1 = peaks["fp32_tflops"] * 1e12, peaks["l1_gbs"] * 1e9
+    alu, gat = FLOPS_PER_SAMPLE * executed / t, GATHER_BYTES_PER_SAMPLE * executed / t
+    alu_r, gat_r = FLOPS_PER_SAMPLE * resampled / t, GATHER_BYTES_PER_SAMPLE * resampled / t
+    l1_binds = gat / p_l1 >= alu / p_alu
+    return {"bound": "l1_gather" if l1_binds else "alu",
+            "achieved": gat / 1e9 if l1_binds else alu / 1e12,
+            "peak": peaks["l1_gbs"] if l1_binds else peaks["fp32_tflops"],
+            "unit": "GB/s" if l1_binds else "TFLOP/s",
+            "frac": max(gat / p_l1, alu / p_alu),
+            "traffic": None,
+            "alu_frac": alu / p_alu, "gather_frac": gat / p_l1,
+            "frac_resampled": max(gat_r / p_l1, alu_r / p_alu),
+            "alu_frac_resampled": alu_r / p_alu, "gather_frac_resampled": gat_r / p_l1,
+            "executed_per_launch": executed, "resampled_per_launch": resampled,
+            "launch_ms": launch_ms, "kernel": kernel,
+            "basis": f"{FLOPS_PER_SAMPLE} flop and {GATHER_BYTES_PER_SAMPLE} B (64 int16 taps) "
+                     "per sample; peaks measured on this device (of measured)",
+            "traffic_note": "DRAM bytes per launch come from ncu captures, not from this run",
+            "peaks": peaks}
+
+
 SERVE_SIZES = [(512, 512), (1024, 1024), (2048, 2048)]
 
 
@@ -275,9 +320,14 @@ def main():
     uuid = getattr(props, "uuid", None)
     gpu_id = f"GPU-{uuid}" if uuid is not None else str(local)
     if args.mode != "render":
+        global _SAMPLER
+        _SAMPLER = ClockSampler(gpu_id)
+        _SAMPLER.start()
+        time.sleep(0.5)
         R = Renderer(local)
         run_mode(args, torch, R, synth)
         R.close()
+        _SAMPLER.stop()
         return
 
     vol = synth.ct_volume()
@@ -294,12 +344,12 @@ def main():
 
     # sample counts (deterministic; measured once, outside the timed region)
     R.build_bricks(vid, B)
-    cnt = torch.zeros((args.cameras, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros((args.cameras, 3), dtype=torch.int64, device=dev)
     for i, cam in enumerate(cams):
         R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], counters=cnt[i],
                  kernel=args.kernel)
     torch.cuda.synchronize()
-    nominal, executed = [int(x) for x in cnt.sum(0).tolist()]
+    nominal, executed, resampled = [int(x) for x in cnt.sum(0).tolist()]
     rays_per_step = args.cameras * 1024 * 1024
 
     def one_step(ev_frames=None):
@@ -367,15 +417,24 @@ def main():
                       "region)"}
 
     clocks = sampler.summary()
-    sampler.stop()
     sms = props.multi_processor_count
     kernel_ms = statistics.mean(frame_ms)
-    flops_per_launch = FLOPS_PER_SAMPLE * executed / args.cameras
-    achieved = flops_per_launch / (kernel_ms / 1e3) / 1e12
-    peak = sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    kname = ("one render call: split_head_kernel + split_tail_kernel" if args.kernel in (0, 6)
+             else f"render kernel {args.kernel}")
+    dense = None
+    if not args.no_dense:
+        dense = dense_tf_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, world,
+                             dev)
+    sampler.stop()
     line = None
     if rank == 0:
-        sgemm = fp32_sgemm_tflops(torch, dev)  # after the timed region
+        peaks = measure_peaks(R, sms)  # after the timed regions
+        roof = roofline(executed // args.cameras, resampled // args.cameras, kernel_ms, peaks,
+                        kname)
+        if dense is not None:
+            dense["roofline"] = roofline(dense.pop("_executed"), dense.pop("_resampled"),
+                                         dense["ms_per_frame"], peaks, kname)
+        sgemm = fp32_sgemm_tflops(torch, dev)
         cpu = None
         if not args.no_cpu_baseline:
             # a bounded sample of the step (~10 s of host work): whole frames, cameras in
@@ -399,27 +458,18 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "mrays_per_s": world * rays_per_step * args.steps / secs / 1e6,
             "gsamples_nominal_per_s": world * nominal * args.steps / secs / 1e9,
-            "samples_per_step": {"nominal": nominal, "executed": executed},
+            "samples_per_step": {"nominal": nominal, "executed": executed,
+                                 "resampled": resampled},
             "render_kernel_ms": kernel_ms,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": (TRAFFIC_PER_RENDER_B8 if args.kernel in (0, 6) and B == 8
-                                     else None),
-                         "kernel": ("one render call: split_head_kernel + split_tail_kernel"
-                                    if args.kernel in (0, 6) else f"render kernel {args.kernel}"),
-                         "basis": f"{FLOPS_PER_SAMPLE} flop/executed sample; peak = {sms} SMs x "
-                                  f"{FP32_LANES} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
-                         "fp32_sgemm_tflops_measured": sgemm,
-                         "frac_of_sgemm": (achieved / sgemm) if sgemm else None},
+            "roofline": roof,
+            "fp32_sgemm_tflops_measured": sgemm,
+            "dense_tf": dense,
             "cpu_baseline": cpu, "e2e": e2e,
             # bricks, occupancy, 3 summed-volume passes, distance, cell mask; per frame the
             # split render's two kernels (one for the per-ray kernel)
             "gpu_launches": args.steps * (7 + args.cameras * (2 if args.kernel in (0, 6) else 1)),
             "clocks": clocks,
         }
-        if clocks.get("sm_mhz"):
-            line["roofline"]["frac_at_measured_clock"] = achieved / (
-                sms * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
         if not args.no_serve:
             small = synth.ct_volume((256, 256, 256), seed=5)
             sid = R.upload_volume(small)
@@ -433,6 +483,54 @@ def main():
     R.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def dense_tf_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, world, dev):
+    """The same volume and cameras with a transfer function that makes soft tissue
+    semi-transparent: frame time of the render call (CUDA events, L2 flushed before each group
+    of frames) and its sample counts, with its own clock record."""
+    B = args.brick
+    tid = R.set_tf(synth.tf_ct_dense(), synth.CT_LO, synth.CT_HI)
+    R.build_occupancy(vid, tid, B)
+    cnt = torch.zeros((len(cams), 3), dtype=torch.int64, device=dev)
+    for i, cam in enumerate(cams):
+        R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], counters=cnt[i],
+                 kernel=args.kernel)
+    torch.cuda.synchronize()
+    nominal, executed, resampled = [int(x) for x in cnt.sum(0).tolist()]
+    steps = max(1, min(args.steps, 5))
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        for i, cam in enumerate(cams):
+            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=args.kernel)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in cams] for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.rows_clear()
+    sampler.mark(True)
+    for s in range(steps):
+        flush.fill_(float(s))
+        for i, cam in enumerate(cams):
+            ev[s][i][0].record(stream)
+            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=args.kernel)
+            ev[s][i][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    ms = statistics.mean(a.elapsed_time(b) for fr in ev for a, b in fr)
+    R.free_tf(tid)
+    nf = len(cams)
+    return {"transfer_function": "soft tissue semi-transparent (about 0.01-0.02 opacity per "
+                                 "voxel), vessels and bone more opaque",
+            "ms_per_frame": ms, "frames_timed": steps * nf,
+            "gsamples_per_s": executed / nf / (ms / 1e3) / 1e9,
+            "gsamples_resampled_per_s": resampled / nf / (ms / 1e3) / 1e9,
+            "mrays_per_s": 1024 * 1024 / (ms / 1e3) / 1e6,
+            "samples_per_frame": {"nominal": nominal // nf, "executed": executed // nf,
+                                  "resampled": resampled // nf},
+            "clocks": sampler.summary(),
+            "_executed": executed // nf, "_resampled": resampled // nf}
 
 
 def _gauss_blur(a, sigma=1.5, radius=5):
@@ -482,14 +580,28 @@ def fp32_sgemm_tflops(torch, dev, n=8192, reps=5):
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+_SAMPLER = None  # clock sampler of the --mode runs (marks the timed regions)
+
+
+def _mark(on: bool):
+    if _SAMPLER is not None:
+        _SAMPLER.mark(on)
+
+
+def _clocks():
+    return _SAMPLER.summary() if _SAMPLER is not None else None
+
+
 def _timed(torch, fn, reps):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    _mark(True)
     e0.record()
     for _ in range(reps):
         fn()
     e1.record()
     torch.cuda.synchronize()
+    _mark(False)
     return e0.elapsed_time(e1) / reps
 
 
@@ -509,11 +621,13 @@ def run_mode(args, torch, R, synth):
             vols[vid] = synth.dims_of(v)
             del v
         tids = [R.set_tf(synth.tf_ct(k), synth.CT_LO, synth.CT_HI) for k in (None, 1, 2, 3)]
+        _mark(True)
         res = serve_bench(R, torch, vols, tids,
                           [(200.0, 60.0), (600.0, 20.0), (900.0, 20.0), (1200.0, 10.0),
                            (3000.0, 3.0)], 5.0, args.brick, seed=5)
+        _mark(False)
         print(json.dumps({"mode": "serve", "metric": "p50/p99 request latency (ms) and images/s",
-                          "data": "synthetic", "serving": res}), flush=True)
+                          "data": "synthetic", "serving": res, "clocks": _clocks()}), flush=True)
         return
     if args.mode == "adjoint":
         vol = synth.ct_float_downsampled(7)
@@ -527,19 +641,23 @@ def run_mode(args, torch, R, synth):
         imgs = [torch.empty((512, 512, 4), device=dev) for _ in cams]
         gtf = torch.zeros((256, 4), device=dev)
         gvol = torch.zeros(vol.shape, device=dev)
-        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
         for c, im in zip(cams, imgs):
             R.render(vid, tid, c, brick=args.brick, out=im, counters=cnt)
         torch.cuda.synchronize()
         executed = int(cnt[1])
 
+        # the forward records each camera's checkpoints; the adjoint reads them
+        cks = [R.ckpt_buffer(vid, c, 0.5, 64) for c in cams]
+
         def fwd():
-            for c, im in zip(cams, imgs):
-                R.render(vid, tid, c, brick=args.brick, out=im)
+            for c, im, ck in zip(cams, imgs, cks):
+                R.render(vid, tid, c, brick=args.brick, out=im, ckpt=ck)
 
         def bwd():
-            for c, im, t in zip(cams, imgs, targets):
-                R.render_backward(vid, tid, c, 2.0 * (im - t), gtf, gvol, brick=args.brick)
+            for c, im, t, ck in zip(cams, imgs, targets, cks):
+                R.render_backward(vid, tid, c, 2.0 * (im - t), gtf, gvol, brick=args.brick,
+                                  ckpt=ck)
 
         for _ in range(args.warmup):
             fwd()
@@ -553,9 +671,11 @@ def run_mode(args, torch, R, synth):
                        "cameras": 8, "image": [512, 512], "step": 0.5, "brick": args.brick,
                        "loss": "L2 vs targets rendered with transfer function seed 8"},
             "forward_ms_per_step": f_ms, "backward_ms_per_step": b_ms,
+            "forward": "split render recording checkpoints (seg_len 64)",
+            "checkpoint_bytes_per_camera": int(cks[0].numel()),
             "executed_samples_per_step": executed, "loss": loss,
             "value": executed / ((f_ms + b_ms) / 1e3) / 1e9, "unit": "Gsamples/s",
-            "gpu_launches": 8 * args.steps * 3}), flush=True)
+            "gpu_launches": 8 * args.steps * 3, "clocks": _clocks()}), flush=True)
         return
     if args.mode == "variants":
         # the paper's Fig. 4 comparison on the headline workload: frame time of each
@@ -600,7 +720,7 @@ def run_mode(args, torch, R, synth):
             "mode": "variants", "metric": "ms per frame; PSNR / SSIM vs tricubic "
             "post-classification (RGBA, peak 1)", "data": "synthetic",
             "config": workload_config(args), "variants": rows,
-            "gpu_launches": 7 * (args.warmup + args.steps) * len(cams) * 2}), flush=True)
+            "gpu_launches": 7 * (args.warmup + args.steps) * len(cams) * 2, "clocks": _clocks()}), flush=True)
         return
     if args.mode == "sortlast":
         # object-order rendering: the headline workload cut into grids of pieces of whole
@@ -699,7 +819,7 @@ def run_mode(args, torch, R, synth):
             "pieces + blend; ordered: pieces front to back) vs the one-pass render",
             "data": "synthetic", "config": workload_config(args),
             "one_pass_ms_per_frame": base_ms, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
-            "grids": rows}), flush=True)
+            "grids": rows, "clocks": _clocks()}), flush=True)
         return
     if args.mode == "large":
         vol = synth.ct_volume((2000, 512, 512), seed=9)
@@ -711,19 +831,24 @@ def run_mode(args, torch, R, synth):
         tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
         cam = synth.orbit_cameras(9, 1, dims, 4096, 4096)[0]
         img = torch.empty((4096, 4096, 4), device=dev)
-        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
         R.render(vid, tid, cam, step=0.25, ert=0.999, brick=B, out=img, counters=cnt)
         torch.cuda.synchronize()
-        nominal, executed = (int(x) for x in cnt.tolist())
+        nominal, executed, resampled = (int(x) for x in cnt.tolist())
         g = torch.rand((4096, 4096, 4), device=dev) - 0.5
         gtf = torch.zeros((256, 4), device=dev)
         gvol = torch.zeros((dims[2], dims[1], dims[0]), device=dev)
-        fwd = lambda: R.render(vid, tid, cam, step=0.25, ert=0.999, brick=B, out=img)  # noqa
+        ck = R.ckpt_buffer(vid, cam, 0.25, 64)  # caller-owned checkpoints (about 9 GB)
+        plain = lambda: R.render(vid, tid, cam, step=0.25, ert=0.999, brick=B, out=img)  # noqa
+        fwd = lambda: R.render(vid, tid, cam, step=0.25, ert=0.999, brick=B, out=img,  # noqa
+                               ckpt=ck, seg_len=64)
         bwd = lambda: R.render_backward(vid, tid, cam, g, gtf, gvol, step=0.25,  # noqa
-                                        ert=0.999, brick=B, seg_len=64)
+                                        ert=0.999, brick=B, seg_len=64, ckpt=ck)
+        plain()
         fwd()
         bwd()
         reps = max(1, min(args.steps, 3))
+        p_ms = _timed(torch, plain, reps)
         f_ms = _timed(torch, fwd, reps)
         b_ms = _timed(torch, bwd, reps)
         print(json.dumps({
@@ -731,9 +856,10 @@ def run_mode(args, torch, R, synth):
             "config": {"volume": [512, 512, 2000], "volume_dtype": "int16", "image": [4096, 4096],
                        "step": 0.25, "brick": B, "ert": 0.999, "seg_len": 64},
             "nominal_samples": nominal, "executed_samples": executed,
-            "forward_ms": f_ms, "backward_ms": b_ms,
-            "forward_gsamples_per_s": executed / (f_ms / 1e3) / 1e9,
-            "mrays_per_s": 4096 * 4096 / (f_ms / 1e3) / 1e6}), flush=True)
+            "resampled_samples": resampled, "checkpoint_bytes": int(ck.numel()),
+            "render_ms": p_ms, "forward_with_checkpoints_ms": f_ms, "backward_ms": b_ms,
+            "forward_gsamples_per_s": executed / (p_ms / 1e3) / 1e9,
+            "mrays_per_s": 4096 * 4096 / (p_ms / 1e3) / 1e6, "clocks": _clocks()}), flush=True)
         return
 
 

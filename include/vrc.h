@@ -86,7 +86,7 @@ typedef struct {
  *                  2..5 = lane groups: one ray per 32 (2), 4 (3), 8 (4) or 16 (5) lanes,
  *                  each group taking that many consecutive samples per step;
  *                  6 = split render: one lane per ray sets the ray up and leaps to its
- *                  first sample that may be non-zero, then groups of 8 lanes drawn from the
+ *                  first sample that may be non-zero, then groups of 16 lanes drawn from the
  *                  whole device finish the queued rays (the context keeps a queue of 112
  *                  bytes per pixel for each stream it renders on).
  *                  All kernels compute the same method; images agree within float
@@ -200,14 +200,32 @@ vrc_status vrc_cellmask_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint32_t
 
 /* Renders `cam` into out_rgba_dev: height x width x 4 floats (RGBA, row py = 0 on top),
  * colour premultiplied by opacity, black background: (C_r, C_g, C_b, 1 - T).
- * counters_dev: NULL, or 2 caller-owned uint64 that the kernel increments by the number of
- * nominal samples (segments inside the box, summed over rays) and executed samples (samples
+ * counters_dev: NULL, or 3 caller-owned uint64 that the kernel increments by the number of
+ * nominal samples (segments inside the box, summed over rays), executed samples (samples
  * up to termination that lie in occupied bricks, or every sample up to termination when
- * params->brick = 0; those in clear cells are counted though not resampled).
+ * params->brick = 0; those in clear cells are counted though not resampled) and resampled
+ * samples (the executed ones that were resampled and composited).
+ * ckpt_dev: NULL, or a caller-owned device buffer of vrc_ckpt_bytes(cam, params, vol_id, ctx)
+ * bytes (256-byte aligned) that the render fills with the checkpoints vrc_render_backward
+ * needs (see there): the ray of every pixel records its first checkpointed segment and its
+ * last composited sample, and the transmittance at the start of each segment of
+ * params->seg_len samples from its first to its last composited sample. With ckpt_dev the
+ * render must be the default variant (interp = preclass = shade = preint = 0) and params->kernel
+ * 0, 1 or 6; the split render (0, 6) needs seg_len a multiple of 16 (VRC_ERR_ARG otherwise).
  * Asynchronous on `stream`. */
 vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                       const vrc_params *params, float *out_rgba_dev,
-                      unsigned long long *counters_dev, void *stream);
+                      unsigned long long *counters_dev, void *ckpt_dev, void *stream);
+
+/* Size in bytes of the checkpoint buffer of a render of `cam` with `params` (step, seg_len)
+ * of resident volume vol_id: an 8-byte record per pixel, then (from a 256-byte boundary) for
+ * every pixel K floats, K = ceil((ceil(d / step) + 2) / seg_len) with d the diagonal of the
+ * volume box -- the segments the longest ray can hold (e.g. 9.0 GB for a 4096^2 image of a
+ * 512 x 512 x 2000 volume at step 0.25 with seg_len 64). Returns 0 on a bad argument (the
+ * message is on the context). The paper has no reverse mode; the segment checkpoints keep
+ * its memory to one float per segment per ray instead of every sample. */
+size_t vrc_ckpt_bytes(const vrc_camera *cam, const vrc_params *params, int vol_id,
+                      vrc_ctx *ctx);
 
 /* The same render end to end for callers holding host memory: renders into a
  * context-owned device image and copies it to out_rgba_host (height x width x 4 floats;
@@ -233,15 +251,19 @@ vrc_status vrc_render_host_batch(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_
  * dL/d(voxel values) to grad_vol_dev (nx*ny*nz floats, x fastest; any voxel dtype, values
  * treated as reals). The forward model is the paper's (Sec. "Methodology": cubic-spline
  * resampling, post-classification, front-to-back accumulation, early termination); its
- * reverse is not in the paper. Each ray replays its forward pass exactly, keeps the
- * transmittance at the start of every params->seg_len samples (1..128, 0 = 64) in
- * per-thread memory, and walks the segments back to front, recomputing each from its
- * checkpoint. Early termination is treated as a fixed decision; the opacity clamp has zero
- * derivative at its ends. Rays may hold at most 256 * seg_len samples (VRC_ERR_ARG
- * otherwise). Gradients are summed with float atomics: the last bits vary between runs. */
+ * reverse is not in the paper. Every ray is walked back to front one segment of
+ * params->seg_len samples (1..128, 0 = 64) at a time, each segment recomputed forward from
+ * its checkpointed transmittance (never dividing by 1 - alpha). ckpt_dev: the buffer a
+ * vrc_render with the same volume, transfer function, camera and parameters filled (the
+ * gradient is then that of the image it rendered, with its early-termination decisions);
+ * NULL: the call first renders the checkpoints itself, one ray per thread, into a buffer the
+ * context owns (grown to vrc_ckpt_bytes). Rays of any length are supported. Early
+ * termination is treated as a fixed decision; the opacity clamp has zero derivative at its
+ * ends. Gradients are summed with float atomics: the last bits vary between runs. */
 vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                                const vrc_params *params, const float *grad_out_dev,
-                               float *grad_tf_dev, float *grad_vol_dev, void *stream);
+                               const void *ckpt_dev, float *grad_tf_dev, float *grad_vol_dev,
+                               void *stream);
 
 /* ---- Batched serving. The paper's cloud server serves several clients from one application
  * (Sec. "Cloud architecture"); here render requests of any resident volume, transfer
@@ -401,6 +423,15 @@ vrc_status vrc_render_sortlast(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
  * owned by the plan. Asynchronous on `stream` unless that image grows. */
 vrc_status vrc_render_ordered(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
                               const vrc_params *params, float *out_dev, void *stream);
+
+/* Measures one roof of the resampling stencil on the context's device (the paper has no
+ * counterpart; used to state the render's roofline against this device's own rates):
+ * kind 0 = FP32 fused multiply-add rate of the CUDA cores (flop/s, FMA = 2 flop), 1 = rate of
+ * 16-byte global loads that hit in L1 (bytes/s), 2 = rate of 16-byte shared-memory loads
+ * (bytes/s). Every SM runs 64 warps; the best of five timed launches after one warm-up is
+ * returned in *rate_out. Synchronises `stream`; allocates a small context-owned buffer on
+ * first use. */
+vrc_status vrc_microbench(vrc_ctx *ctx, int kind, double *rate_out, void *stream);
 
 /* Reads and clears the device error word shared by the context's kernels: 0 when no kernel
  * check has fired, else a VRC_ERR_* code. Synchronises `stream`. */

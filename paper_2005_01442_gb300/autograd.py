@@ -1,6 +1,8 @@
-"""Differentiable rendering through torch.autograd: the forward calls vrc_render, the backward
-vrc_render_backward (the hand-written adjoint kernel); gradients flow to the 256 x 4 transfer
-function and to a float32 volume. Only argument marshalling happens here.
+"""Differentiable rendering through torch.autograd: the forward calls vrc_render (the split
+render, recording the reverse-mode checkpoints into a buffer the autograd graph keeps), the
+backward vrc_render_backward (the hand-written adjoint kernel) with those checkpoints; gradients
+flow to the 256 x 4 transfer function and to a float32 volume. Only argument marshalling
+happens here.
 
     dr = DifferentiableRenderer(Renderer(0), shape=(nz, ny, nx), lo=-1024, hi=3071)
     img = dr(volume, tf, cam, step=0.5, brick=8)       # (H, W, 4) CUDA tensor
@@ -25,10 +27,13 @@ class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, volume, tf, dr, cam, step, ert, brick, seg_len):
         dr._load(volume, tf, brick)
-        # the per-ray kernel: the compositing order the adjoint replays
+        # the split render, recording its checkpoints: the adjoint differentiates exactly the
+        # image it rendered (its transmittances and early-termination decisions)
+        ck = dr.renderer.ckpt_buffer(dr.vol_id, cam, step, seg_len)
         img = dr.renderer.render(dr.vol_id, dr.tf_id, cam, step=step, ert=ert, brick=brick,
-                                 kernel=1)
+                                 ckpt=ck, seg_len=seg_len)
         ctx.save_for_backward(volume, tf)
+        ctx.ck = ck
         ctx.dr, ctx.cam = dr, cam
         ctx.args = (step, ert, brick, seg_len)
         return img
@@ -50,8 +55,9 @@ class _RenderFn(torch.autograd.Function):
         ps = native.params_struct(step, ert, brick, seg_len, 0)
         R._ck(R.lib.vrc_render_backward(
             R.ctx, dr.vol_id, dr.tf_id, C.byref(cs), C.byref(ps), C.c_void_p(g.data_ptr()),
-            C.c_void_p(grad_tf.data_ptr()),
+            C.c_void_p(ctx.ck.data_ptr()), C.c_void_p(grad_tf.data_ptr()),
             C.c_void_p(grad_vol.data_ptr()) if grad_vol is not None else None, _stream_ptr(None)))
+        ctx.ck = None
         gtf = grad_tf.to(tf.device) if ctx.needs_input_grad[1] else None
         return grad_vol, gtf, None, None, None, None, None, None
 

@@ -3,12 +3,11 @@
 // its forward model (cubic B-spline resampling, post-classification, opacity correction,
 // front-to-back compositing, early termination).
 //
-// One thread per ray. Forward pass: the same arithmetic, in the same order, as the per-ray
-// render kernel (so every transmittance and the early-termination decision are reproduced
-// exactly), recording the transmittance T at the start of every segment of `seg` samples
-// (checkpoints in per-thread memory) and which segments hold composited samples. Backward
-// pass, segment by segment from the last: recompute the segment forward from its checkpoint
-// (never dividing by 1 - alpha), then walk its samples back to front keeping
+// One thread per ray, reading the checkpoints of a forward render (RenderLaunch::ckpt): the
+// ray's last composited sample and, for each segment of `seg` samples up to it, the
+// transmittance at the segment's start (-1 for segments without a composited sample). Walking
+// the segments back to front: recompute the segment forward from its checkpoint (never
+// dividing by 1 - alpha), then walk its samples back to front keeping
 //   S = normalised colour behind the sample, U = transmittance behind the sample,
 //   dL/drgb_j   = T_j alpha_j g_rgb
 //   dL/dalpha_j = T_j [ g_rgb . (rgb_j - S) + g_A U ]
@@ -101,8 +100,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
     RaySetup ray;
     ray.nseg = 0;
     if (valid && any_g) ray_setup(L.cam, L.grid, px, py, ray);
-    const float step = L.grid.step, thr = L.grid.ert;
-    const float inv_step = 1.0f / step;
+    const float step = L.grid.step;
     const int seg = A.seg;
     RayPos rp;
     ray_pos_init(ray, step, rp);
@@ -112,68 +110,23 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
     if (ESL)
         dist = L.dist + (long)octant_of(df) * L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
 
-    // ------------------------------------------------------------------ forward pass
-    float ckpt[ADJ_MAX_CKPT];
-    unsigned segmask[ADJ_MAX_CKPT / 32];
-#pragma unroll
-    for (int i = 0; i < ADJ_MAX_CKPT / 32; ++i) segmask[i] = 0u;
-    int filled = 0;  // checkpoints written
-    int jlast = -1;  // last composited sample
-    float Tr = 1.0f;
-    {
-        int leap_lin = -1, leap_r = 0, run_lin = -1, run_empty = 0;
-        bool in_run = !ESL;
-        int j = 0;
-        while (j < ray.nseg) {
-            if (ESL && !in_run) {
-                const int jn = leap_float(L.bricks, dist, Pf, df, inv_df, step, inv_step,
-                                          ray.nseg, j, leap_lin, leap_r);
-                if (jn != j) {
-                    j = jn;
-                    continue;
-                }
-                in_run = true;
-            }
-            int ip[3];
-            float f[3], delta;
-            place(rp, step, L.grid.n, j, ip, f, delta);
-            if (ESL) {
-                const int lin = brick_of(L.bricks, ip);
-                if (lin != run_lin) {
-                    run_lin = lin;
-                    run_empty = dist[lin] != 0;
-                }
-                if (run_empty) {
-                    ++j;
-                    in_run = false;
-                    continue;
-                }
-                if (L.cells && !cell_open(L.cells, L.cwx, L.grid.n, ip)) {  // opacity 0
-                    ++j;
-                    continue;
-                }
-            }
-            const int k = j / seg;
-            while (filled <= k) ckpt[filled++] = Tr;
-            segmask[k >> 5] |= 1u << (k & 31);
-            SampleEval e;
-            eval_sample(L, ip, f, delta, e);
-            const float w = Tr * e.alpha;
-            Tr = Tr - w;
-            jlast = j;
-            if (1.0f - Tr > thr) break;
-            ++j;
-        }
+    // the forward's record of this ray: first checkpointed segment, last composited sample
+    int k0 = 0, jlast = -1;
+    if (valid && any_g) {
+        const int2 h = L.ckpt_head[(long)py * L.cam.width + px];
+        k0 = max(h.x, 0);
+        jlast = min(h.y, rp.nseg - 1);
     }
+    const float *ck_row = L.ckpt + ((long)py * L.cam.width + px) * L.ckpt_K;
 
     // ------------------------------------------------------------------ backward pass
     float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, U = 1.0f;
     float buf_s[ADJ_MAX_SEG], buf_T[ADJ_MAX_SEG];
     int buf_j[ADJ_MAX_SEG];
-    for (int k = filled - 1; k >= 0; --k) {
-        if (!((segmask[k >> 5] >> (k & 31)) & 1u)) continue;
+    for (int k = jlast >= 0 ? min(jlast / seg, L.ckpt_K - 1) : -1; k >= k0; --k) {
         // recompute the segment forward from its checkpoint
-        float T = ckpt[k];
+        float T = ck_row[k];
+        if (!(T >= 0.0f)) continue;  // no composited sample in this segment
         int n = 0;
         const int j1 = min(k * seg + seg, jlast + 1);
         for (int j = k * seg; j < j1; ++j) {

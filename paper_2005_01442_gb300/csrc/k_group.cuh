@@ -47,15 +47,22 @@ __device__ __forceinline__ int advance_to_occupied(const RayPos &rp, const Rende
 // Lane q of a group of G lanes (mask gmask, first lane gbase) marches the ray from sample jlo
 // on, compositing onto (RC, RT); on return RC and RT are the ray's colour and transmittance,
 // equal in every lane of the group. `executed` grows by the samples in occupied bricks up to
-// termination, resampled or skipped as clear cells (counted in every lane; callers count it
-// once per group).
-template <bool ESL, int G, int MODE = MODE_CUBIC_POST>
+// termination, resampled or skipped as clear cells, `resampled` by those resampled (both
+// counted in every lane; callers count them once per group).
+//
+// CKPT (default variant, L.ckpt_seg a multiple of G, so a block lies in one segment): ck
+// records the ray's reverse-mode checkpoints as render_ray_tile does -- the transmittance
+// before the first block with a composited sample in each segment (-1 for segments without
+// one), every segment from the first to the last such one (written by the group's lanes in
+// turn), and the last composited sample.
+template <bool ESL, int G, int MODE = MODE_CUBIC_POST, bool CKPT = false>
 __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos &rp,
                                             const uint8_t *__restrict__ dist, const float Pf[3],
                                             const float df[3], const float inv_df[3],
                                             float inv_step, int jlo, unsigned gmask, int q,
                                             int gbase, float &RC0, float &RC1, float &RC2,
-                                            float &RT, unsigned long long &executed) {
+                                            float &RT, unsigned long long &executed,
+                                            unsigned &resampled, CkState *ck = nullptr) {
     constexpr int SH = G == 32 ? 5 : G == 16 ? 4 : G == 8 ? 3 : 2;
     constexpr unsigned low = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
     const float step = L.grid.step, thr = L.grid.ert;
@@ -91,7 +98,17 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
             }
         }
         const unsigned occ_bits = (__ballot_sync(gmask, in_occ) >> gbase) & low;
-        if (__ballot_sync(gmask, live) & gmask) {
+        const unsigned live_bits = (__ballot_sync(gmask, live) >> gbase) & low;
+        if (live_bits) {
+            if constexpr (CKPT) {
+                const int k = (blk * G) / L.ckpt_seg;
+                if (k != ck->last) {
+                    for (int kk = (ck->first < 0 ? k : ck->last + 1) + q; kk <= k; kk += G)
+                        ck->row[kk] = kk == k ? RT : -1.0f;  // -1: no composited sample
+                    if (ck->first < 0) ck->first = k;
+                    ck->last = k;
+                }
+            }
             // inclusive scan of "over" across the group's block
 #pragma unroll
             for (int o = 1; o < G; o <<= 1) {
@@ -113,10 +130,13 @@ __device__ __forceinline__ void group_march(const RenderLaunch &L, const RayPos 
                 (__ballot_sync(gmask, live && (1.0f - tT > thr)) >> gbase) & low;
             const int last = stop_bits ? __ffs(stop_bits) - 1 : G - 1;
             executed += __popc(occ_bits & (0xffffffffu >> (31 - last)));
+            resampled += __popc(live_bits & (0xffffffffu >> (31 - last)));
             RC0 = __shfl_sync(gmask, t0, last, G);
             RC1 = __shfl_sync(gmask, t1, last, G);
             RC2 = __shfl_sync(gmask, t2, last, G);
             RT = __shfl_sync(gmask, tT, last, G);
+            if constexpr (CKPT)
+                ck->jlast = blk * G + (stop_bits ? last : 31 - __clz(live_bits));
             if (stop_bits) break;
         } else {
             executed += __popc(occ_bits);  // a block of identities: (RC, RT) unchanged

@@ -33,7 +33,13 @@ __device__ __forceinline__ int brick_linear(const BrickView &bv, int bx, int by,
 // with its colour and transmittance so far; the second phase finishes it with SPLIT_G lanes
 // in blocks aligned to SPLIT_G. Samples between SPLIT_J0 and the queued index have opacity
 // zero, so the split image is also identical with and without skipping.
-template <bool ESL, bool SPLIT = false, int MODE = MODE_CUBIC_POST>
+//
+// CKPT: the ray also records its reverse-mode checkpoints (L.ckpt, default variant only): for
+// each segment of L.ckpt_seg samples from the first to the last one holding a composited
+// sample, the transmittance before its first composited sample (skipped samples have opacity
+// zero, so that is the transmittance at the segment's start), or -1 when it holds none; and
+// in L.ckpt_head the first such segment and the last composited sample.
+template <bool ESL, bool SPLIT = false, int MODE = MODE_CUBIC_POST, bool CKPT = false>
 __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile) {
     const int lane = threadIdx.x & 31;
     const int tiles_x = (L.cam.width + 7) >> 3;
@@ -72,7 +78,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     ray_pos_init(ray, step, rp);
     float Pf[3], df[3], inv_df[3];
     ray_float(rp, Pf, df, inv_df);
-    int executed = 0;
+    int executed = 0, resampled = 0;
     const uint8_t *dist = nullptr;
     if (ESL) {
         const int oct = (df[0] < 0.0f) | ((df[1] < 0.0f) << 1) | ((df[2] < 0.0f) << 2);
@@ -88,6 +94,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     const int jsw = SPLIT ? SPLIT_J0 : 0x7fffffff;  // hand-over index (SPLIT)
     float u_prev = 0.0f, dl_prev = 0.0f;  // previous sample (MODE_PREINT)
     bool have_prev = false;
+    int ck_first = -1, ck_last = -1, ck_next = 0, jlast = -1;  // CKPT
     while (true) {
         // advance this lane to its next sample to composite; a lane that has skipped
         // SKIP_PER_STEP clear cells sits this step out (idle), so that long clear runs of
@@ -212,6 +219,7 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
                 dl_prev = delta;
                 have_prev = true;
                 ++executed;
+                ++resampled;
                 ++j;
             }
             continue;
@@ -221,12 +229,26 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
             // between entries; or the variant MODE selects)
             const float4 rgba = sample_rgba<MODE>(rep, tfv, ip, f, df, &L.phong);
             const float alpha = segment_alpha(rgba.w, delta);
+            if constexpr (CKPT) {
+                if (j >= ck_next) {  // first composited sample of a later segment
+                    const int k = j / L.ckpt_seg;
+                    float *row = L.ckpt + oidx * L.ckpt_K;
+                    // segments passed over without a composited sample get -1
+                    for (int kk = ck_first < 0 ? k : ck_last + 1; kk <= k; ++kk)
+                        row[kk] = kk == k ? Tr : -1.0f;
+                    if (ck_first < 0) ck_first = k;
+                    ck_last = k;
+                    ck_next = (k + 1) * L.ckpt_seg;
+                }
+                jlast = j;
+            }
             const float w = Tr * alpha;
             C0 = fmaf(w, rgba.x, C0);
             C1 = fmaf(w, rgba.y, C1);
             C2 = fmaf(w, rgba.z, C2);
             Tr = Tr - w;
             ++executed;
+            ++resampled;
             if (1.0f - Tr > thr) done = true;
             ++j;
         }
@@ -237,18 +259,21 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
         // be overwritten by a stale value from another
         if (L.accum) {
             if (executed > 0) L.accum[oidx] = make_float4(C0, C1, C2, Tr);
-        } else {
+        } else if (!CKPT || L.out) {
             L.out[oidx] = make_float4(C0, C1, C2, 1.0f - Tr);
         }
+        if constexpr (CKPT) L.ckpt_head[oidx] = make_int2(ck_first < 0 ? 0 : ck_first, jlast);
     }
 
     if (L.counters) {
-        unsigned int nom = (unsigned)ray.nseg, ex = (unsigned)executed;
+        unsigned int nom = (unsigned)ray.nseg, ex = (unsigned)executed, rs = (unsigned)resampled;
         nom = __reduce_add_sync(0xffffffffu, nom);
         ex = __reduce_add_sync(0xffffffffu, ex);
+        rs = __reduce_add_sync(0xffffffffu, rs);
         if (lane == 0) {
             atomicAdd(&L.counters[0], (unsigned long long)nom);
             atomicAdd(&L.counters[1], (unsigned long long)ex);
+            if (rs) atomicAdd(&L.counters[2], (unsigned long long)rs);
         }
     }
 }

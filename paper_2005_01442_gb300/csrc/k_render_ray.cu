@@ -8,20 +8,24 @@ namespace vrc {
 
 constexpr int RAY_WARPS = 2;  // warps per CTA
 
-template <bool ESL, int MODE>
+template <bool ESL, int MODE, bool CKPT = false>
 __global__ void __launch_bounds__(32 * RAY_WARPS, 16 / RAY_WARPS) render_ray_kernel(RenderLaunch L) {
-    render_ray_tile<ESL, false, MODE>(L, blockIdx.x * RAY_WARPS + (threadIdx.x >> 5));
+    render_ray_tile<ESL, false, MODE, CKPT>(L, blockIdx.x * RAY_WARPS + (threadIdx.x >> 5));
 }
 
-template <int MODE>
+template <int MODE, bool CKPT = false>
 static void launch_mode(const RenderLaunch &L, unsigned grid, cudaStream_t st) {
-    if (L.dist) render_ray_kernel<true, MODE><<<grid, 32 * RAY_WARPS, 0, st>>>(L);
-    else render_ray_kernel<false, MODE><<<grid, 32 * RAY_WARPS, 0, st>>>(L);
+    if (L.dist) render_ray_kernel<true, MODE, CKPT><<<grid, 32 * RAY_WARPS, 0, st>>>(L);
+    else render_ray_kernel<false, MODE, CKPT><<<grid, 32 * RAY_WARPS, 0, st>>>(L);
 }
 
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st) {
     const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
     const unsigned grid = (unsigned)((tiles + RAY_WARPS - 1) / RAY_WARPS);
+    if (L.ckpt) {  // default variant only (checked by the caller)
+        launch_mode<MODE_CUBIC_POST, true>(L, grid, st);
+        return cudaGetLastError();
+    }
     switch (L.mode) {
     case MODE_LINEAR_POST: launch_mode<MODE_LINEAR_POST>(L, grid, st); break;
     case MODE_CUBIC_PRE: launch_mode<MODE_CUBIC_PRE>(L, grid, st); break;

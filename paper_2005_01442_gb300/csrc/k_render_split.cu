@@ -27,16 +27,17 @@ constexpr int SPLIT_WARPS = 8;      // warps per CTA of the second phase
 constexpr int SPLIT_CLAIM = 1;      // queued rays a group claims per atomic (more: the long
                                     // rays of a claim serialise and the frame waits on them)
 
-template <bool ESL>
+template <bool ESL, bool CKPT>
 __global__ void __launch_bounds__(32 * SPLIT_RAY_WARPS, 16 / SPLIT_RAY_WARPS)
     split_head_kernel(RenderLaunch L) {
-    render_ray_tile<ESL, true>(L, blockIdx.x * SPLIT_RAY_WARPS + (threadIdx.x >> 5));
+    render_ray_tile<ESL, true, MODE_CUBIC_POST, CKPT>(L, blockIdx.x * SPLIT_RAY_WARPS +
+                                                             (threadIdx.x >> 5));
 }
 
 // Four CTAs per SM (64 registers, a few spills): the march is bound by the latency of
 // dependent loads, and 32 resident warps hide it better than 24 at 80 registers (measured:
 // 0.377 vs 0.392 ms per 1024^2 CT frame; five CTAs at 48 registers spill too much).
-template <bool ESL, int MODE>
+template <bool ESL, int MODE, bool CKPT = false>
 __global__ void __launch_bounds__(32 * SPLIT_WARPS, 4) split_tail_kernel(RenderLaunch L) {
     constexpr int G = SPLIT_G;
     const int lane = threadIdx.x & 31;
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 4) split_tail_kernel(RenderL
     const unsigned nf = __ldcg(&L.split.head[0]), nb = __ldcg(&L.split.head[2]);
     const unsigned total = min(nf + nb, L.split.cap);
     unsigned long long executed = 0;
+    unsigned resampled = 0;
     unsigned next = 0, end = 0;  // rays claimed by this group and not yet started
     while (true) {
         if (next == end) {  // claim SPLIT_CLAIM consecutive rays with one atomic
@@ -69,8 +71,13 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 4) split_tail_kernel(RenderL
         ray_float(rp, Pf, df, inv_df);
         const uint8_t *dist = nullptr;
         if (ESL) dist = L.dist + octant_of(df) * nbricks;
-        group_march<ESL, G, MODE>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q,
-                                  gbase, RC0, RC1, RC2, RT, executed);
+        CkState ck;
+        if constexpr (CKPT) ck = {L.ckpt + (long)pix * L.ckpt_K, -1, -1, -1};
+        group_march<ESL, G, MODE, CKPT>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q,
+                                        gbase, RC0, RC1, RC2, RT, executed, resampled, &ck);
+        if constexpr (CKPT) {
+            if (q == 0) L.ckpt_head[pix] = make_int2(ck.first < 0 ? 0 : ck.first, ck.jlast);
+        }
         if (q == 0) {
             if (L.accum)  // ordered pass: T itself (a queued ray met a sample of the piece)
                 L.accum[pix] = make_float4(RC0, RC1, RC2, RT);
@@ -80,8 +87,11 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS, 4) split_tail_kernel(RenderL
     }
     if (L.counters) {
         unsigned ex = q == 0 ? (unsigned)executed : 0u;
+        unsigned rs = q == 0 ? resampled : 0u;
         ex = __reduce_add_sync(0xffffffffu, ex);
+        rs = __reduce_add_sync(0xffffffffu, rs);
         if (lane == 0 && ex) atomicAdd(&L.counters[1], (unsigned long long)ex);
+        if (lane == 0 && rs) atomicAdd(&L.counters[2], (unsigned long long)rs);
     }
 }
 
@@ -104,10 +114,10 @@ int tail_ctas(cudaError_t &e) {
 }
 }  // namespace
 
-template <int MODE>
+template <int MODE, bool CKPT = false>
 static void launch_tail(const RenderLaunch &L, int ctas, cudaStream_t st) {
-    if (L.dist) split_tail_kernel<true, MODE><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
-    else split_tail_kernel<false, MODE><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+    if (L.dist) split_tail_kernel<true, MODE, CKPT><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
+    else split_tail_kernel<false, MODE, CKPT><<<ctas, 32 * SPLIT_WARPS, 0, st>>>(L);
 }
 
 cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st) {
@@ -116,8 +126,18 @@ cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
     const unsigned grid = (unsigned)((tiles + SPLIT_RAY_WARPS - 1) / SPLIT_RAY_WARPS);
-    if (L.dist) split_head_kernel<true><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
-    else split_head_kernel<false><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+    const bool ck = L.ckpt != nullptr;  // default variant only (checked by the caller)
+    if (L.dist) {
+        if (ck) split_head_kernel<true, true><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+        else split_head_kernel<true, false><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+    } else {
+        if (ck) split_head_kernel<false, true><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+        else split_head_kernel<false, false><<<grid, 32 * SPLIT_RAY_WARPS, 0, st>>>(L);
+    }
+    if (ck) {
+        launch_tail<MODE_CUBIC_POST, true>(L, ctas, st);
+        return cudaGetLastError();
+    }
     switch (L.mode) {
     case MODE_LINEAR_POST: launch_tail<MODE_LINEAR_POST>(L, ctas, st); break;
     case MODE_CUBIC_PRE: launch_tail<MODE_CUBIC_PRE>(L, ctas, st); break;

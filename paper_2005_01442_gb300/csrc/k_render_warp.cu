@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(WC_RAYS, 2) render_warp_kernel(RenderLaunch L)
     const float inv_step = 1.0f / step;
     const long nbricks = ESL ? (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2] : 0;
     unsigned long long nominal = 0, executed = 0;
+    unsigned resampled = 0;
 
     // ---------------------------------------------------------------- phase 1: one ray per thread
     {
@@ -85,18 +86,21 @@ __global__ void __launch_bounds__(WC_RAYS, 2) render_warp_kernel(RenderLaunch L)
         if (ESL) dist = L.dist + octant_of(df) * nbricks;
         float RC0 = 0.0f, RC1 = 0.0f, RC2 = 0.0f, RT = 1.0f;
         group_march<ESL, G>(L, rp, dist, Pf, df, inv_df, inv_step, s_rec[qi].j0, gmask, q, gbase,
-                            RC0, RC1, RC2, RT, executed);
+                            RC0, RC1, RC2, RT, executed, resampled);
         if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
     }
 
     if (L.counters) {
         // nominal: summed over the phase-1 threads; executed: counted by each group's first lane
         unsigned long long ex = (lane & (G - 1)) == 0 ? executed : 0ull;
+        unsigned long long rs = (lane & (G - 1)) == 0 ? resampled : 0u;
         nominal = __reduce_add_sync(0xffffffffu, (unsigned)nominal);
         ex = __reduce_add_sync(0xffffffffu, (unsigned)ex);
+        rs = __reduce_add_sync(0xffffffffu, (unsigned)rs);
         if (lane == 0) {
             atomicAdd(&L.counters[0], nominal);
             atomicAdd(&L.counters[1], ex);
+            atomicAdd(&L.counters[2], rs);
         }
     }
 }

@@ -120,6 +120,9 @@ struct vrc_ctx {
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
     unsigned tf_version_counter = 0;
+    void *mb_scratch = nullptr;  // vrc_microbench buffers
+    unsigned char *ckpt_buf = nullptr;  // checkpoints of vrc_render_backward without ckpt_dev
+    size_t ckpt_bytes = 0;
 };
 
 namespace {
@@ -613,6 +616,40 @@ vrc_status split_queue(vrc_ctx *ctx, cudaStream_t st, size_t need, RaySplit &q) 
     return VRC_OK;
 }
 
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Checkpoint buffer of a render (vrc_ckpt_bytes): an int2 per pixel, then from a 256-byte
+// boundary K floats per pixel.
+struct CkptLayout {
+    size_t bytes = 0, head_bytes = 0;
+    int K = 0, seg = 0;
+};
+
+vrc_status ckpt_layout(vrc_ctx *ctx, const vrc_camera *cam, const vrc_params *p, const Volume &v,
+                       CkptLayout &out) {
+    if (!cam || !p) return fail(ctx, VRC_ERR_ARG, "camera and params must be non-NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return fail(ctx, VRC_ERR_ARG, "image size out of range");
+    if (!(p->step >= 1e-3f) || !isfinite(p->step))
+        return fail(ctx, VRC_ERR_ARG, "step must be finite and >= 1e-3");
+    const int seg = p->seg_len == 0 ? 64 : p->seg_len;
+    if (seg < 1 || seg > ADJ_MAX_SEG) return fail(ctx, VRC_ERR_ARG, "seg_len must be 0..128");
+    const size_t npix = (size_t)cam->width * cam->height;
+    out.seg = seg;
+    out.K = ckpt_segments(v.n, p->step, seg);
+    out.head_bytes = align256(npix * sizeof(int2));
+    out.bytes = out.head_bytes + align256(npix * (size_t)out.K * sizeof(float));
+    return VRC_OK;
+}
+
+// Binds a checkpoint buffer to a render launch.
+void bind_ckpt(RenderLaunch &L, void *buf, const CkptLayout &c) {
+    L.ckpt_head = (int2 *)buf;
+    L.ckpt = (float *)((unsigned char *)buf + c.head_bytes);
+    L.ckpt_K = c.K;
+    L.ckpt_seg = c.seg;
+}
+
 // Launches the render kernel params->kernel selects (0 and 6: split render, 1: per-ray,
 // 2..5: lane groups). Without a queue (queue_ok = false) kernel 0 runs per ray.
 vrc_status launch_render(vrc_ctx *ctx, const vrc_params *params, RenderLaunch &L,
@@ -697,6 +734,8 @@ vrc_status vrc_destroy(vrc_ctx *ctx) {
         if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
     }
     if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
+    cudaFree(ctx->mb_scratch);
+    cudaFree(ctx->ckpt_buf);
     delete ctx;
     return VRC_OK;
 }
@@ -953,13 +992,29 @@ vrc_status vrc_cellmask_get(vrc_ctx *ctx, int vol_id, int tf_id, int B, uint32_t
 
 vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                       const vrc_params *params, float *out_rgba_dev,
-                      unsigned long long *counters_dev, void *stream) {
+                      unsigned long long *counters_dev, void *ckpt_dev, void *stream) {
     if (!ctx) return VRC_ERR_ARG;
     if (!out_rgba_dev) return fail(ctx, VRC_ERR_ARG, "out_rgba_dev is NULL");
     if (((uintptr_t)out_rgba_dev & 15) != 0)
         return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be 16-byte aligned");
     if (counters_dev && ((uintptr_t)counters_dev & 7) != 0)
         return fail(ctx, VRC_ERR_ARG, "counters_dev must be 8-byte aligned");
+    CkptLayout ck;
+    if (ckpt_dev) {
+        if (((uintptr_t)ckpt_dev & 255) != 0)
+            return fail(ctx, VRC_ERR_ARG, "ckpt_dev must be 256-byte aligned");
+        Volume *v = get_vol(ctx, vol_id);
+        if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+        vrc_status s = ckpt_layout(ctx, cam, params, *v, ck);
+        if (s != VRC_OK) return s;
+        if (params->interp || params->preclass || params->shade || params->preint)
+            return fail(ctx, VRC_ERR_ARG, "checkpoints are recorded for the default variant only");
+        if (params->kernel != 0 && params->kernel != 1 && params->kernel != 6)
+            return fail(ctx, VRC_ERR_ARG, "checkpoints need kernel 0, 1 or 6");
+        if (params->kernel != 1 && ck.seg % SPLIT_G != 0)
+            return fail(ctx, VRC_ERR_ARG, "the split render checkpoints segments of a multiple "
+                                          "of %d samples (seg_len %d)", SPLIT_G, ck.seg);
+    }
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     RenderLaunch L;
@@ -967,7 +1022,21 @@ vrc_status vrc_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam
     if (s != VRC_OK) return s;
     L.out = (float4 *)out_rgba_dev;
     L.counters = counters_dev;
+    if (ckpt_dev) bind_ckpt(L, ckpt_dev, ck);
     return launch_render(ctx, params, L, st);
+}
+
+size_t vrc_ckpt_bytes(const vrc_camera *cam, const vrc_params *params, int vol_id,
+                      vrc_ctx *ctx) {
+    if (!ctx) return 0;
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) {
+        fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+        return 0;
+    }
+    CkptLayout ck;
+    if (ckpt_layout(ctx, cam, params, *v, ck) != VRC_OK) return 0;
+    return ck.bytes;
 }
 
 vrc_status vrc_render_host(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
@@ -1067,7 +1136,8 @@ vrc_status vrc_render_host_batch(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_
 
 vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera *cam,
                                const vrc_params *params, const float *grad_out_dev,
-                               float *grad_tf_dev, float *grad_vol_dev, void *stream) {
+                               const void *ckpt_dev, float *grad_tf_dev, float *grad_vol_dev,
+                               void *stream) {
     if (!ctx) return VRC_ERR_ARG;
     if (!params) return fail(ctx, VRC_ERR_ARG, "params is NULL");
     if (!grad_out_dev || !grad_tf_dev)
@@ -1076,31 +1146,77 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
         return fail(ctx, VRC_ERR_ARG, "grad_out_dev must be 16-byte aligned");
     if (((uintptr_t)grad_tf_dev & 3) != 0 || ((uintptr_t)grad_vol_dev & 3) != 0)
         return fail(ctx, VRC_ERR_ARG, "gradient buffers must be 4-byte aligned");
-    const int seg = params->seg_len == 0 ? 64 : params->seg_len;
-    if (seg < 1 || seg > ADJ_MAX_SEG) return fail(ctx, VRC_ERR_ARG, "seg_len must be 0..128");
+    if (ckpt_dev && ((uintptr_t)ckpt_dev & 255) != 0)
+        return fail(ctx, VRC_ERR_ARG, "ckpt_dev must be 256-byte aligned");
     if (params->interp || params->preclass || params->shade || params->preint)
         return fail(ctx, VRC_ERR_ARG, "the adjoint differentiates the default variant only");
+    Volume *v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
+    CkptLayout ck;
+    vrc_status s = ckpt_layout(ctx, cam, params, *v, ck);
+    if (s != VRC_OK) return s;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     AdjointLaunch A;
-    vrc_status s = prepare_render(ctx, vol_id, tf_id, cam, params, st, A.L);
+    s = prepare_render(ctx, vol_id, tf_id, cam, params, st, A.L);
     if (s != VRC_OK) return s;
-    // longest possible ray: the box diagonal
-    const double diag = sqrt((double)A.L.grid.n[0] * A.L.grid.n[0] +
-                             (double)A.L.grid.n[1] * A.L.grid.n[1] +
-                             (double)A.L.grid.n[2] * A.L.grid.n[2]);
-    const double max_samples = ceil(diag / (double)params->step) + 2.0;
-    if (max_samples > (double)ADJ_MAX_CKPT * seg)
-        return fail(ctx, VRC_ERR_ARG,
-                    "rays may hold %.0f samples, above %d checkpoints x seg_len %d; raise "
-                    "seg_len or the step", max_samples, ADJ_MAX_CKPT, seg);
     A.grad_out = (const float4 *)grad_out_dev;
     A.grad_tf = grad_tf_dev;
     A.grad_vol = grad_vol_dev;
-    A.seg = seg;
+    A.seg = ck.seg;
     A.L.out = nullptr;
     A.L.counters = nullptr;
+    if (ckpt_dev) {
+        bind_ckpt(A.L, const_cast<void *>(ckpt_dev), ck);
+    } else {
+        // render the checkpoints first, one ray per thread, into the context's buffer
+        if (ctx->ckpt_bytes < ck.bytes) {
+            CK(cudaStreamSynchronize(st), "sync before checkpoint realloc");
+            cudaFree(ctx->ckpt_buf);
+            ctx->ckpt_buf = nullptr;
+            ctx->ckpt_bytes = 0;
+            CK(cudaMalloc(&ctx->ckpt_buf, ck.bytes), "cudaMalloc(checkpoints)");
+            ctx->ckpt_bytes = ck.bytes;
+        }
+        bind_ckpt(A.L, ctx->ckpt_buf, ck);
+        CK(launch_render_ray(A.L, st), "checkpoint render launch");
+    }
     CK(launch_adjoint(A, st), "adjoint launch");
+    return VRC_OK;
+}
+
+vrc_status vrc_microbench(vrc_ctx *ctx, int kind, double *rate_out, void *stream) {
+    if (!ctx) return VRC_ERR_ARG;
+    if (!rate_out) return fail(ctx, VRC_ERR_ARG, "rate_out is NULL");
+    if (kind < MB_FMA || kind > MB_LDS) return fail(ctx, VRC_ERR_ARG, "kind must be 0, 1 or 2");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->mb_scratch) {
+        CK(cudaMalloc(&ctx->mb_scratch, microbench_scratch_bytes()), "cudaMalloc(microbench)");
+        CK(cudaMemsetAsync(ctx->mb_scratch, 0, microbench_scratch_bytes(), st), "memset");
+    }
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attribute");
+    // 8 CTAs of 256 threads per SM (64 warps: the most an SM holds)
+    const int ctas = std::min(sms * 8, 65536);
+    const int iters = kind == MB_FMA ? 4096 : 2048;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    cudaError_t e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {  // one warm-up, best of five
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = launch_microbench(kind, ctas, iters, ctx->mb_scratch, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "microbenchmark");
+    *rate_out = microbench_work(kind, ctas, iters) / (best * 1e-3);
     return VRC_OK;
 }
 
@@ -1135,8 +1251,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char *g_noalloc_ptr[kMaxDevices] = {};
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 // Device address of the scratch array on the current device (looked up once per device).
 vrc_status noalloc_scratch(vrc_ctx *ctx, unsigned char **out) {
     if (ctx->device < 0 || ctx->device >= kMaxDevices)
@@ -1170,6 +1284,9 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     if (params->preint)
         return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not pre-integrate (the table "
                                       "would need memory)");
+    // no queue here (it would need device memory): kernel 0 renders per ray
+    if (params->kernel == 6)
+        return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not run the split render (kernel 6)");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     Volume *v = get_vol(ctx, vol_id);
@@ -1229,9 +1346,6 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     }
     L.out = (float4 *)out_rgba_dev;
     L.counters = counters_dev;
-    // no queue here (it would need device memory): kernel 0 renders per ray
-    if (params->kernel == 6)
-        return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not run the split render (kernel 6)");
     return launch_render(ctx, params, L, st, false);
 }
 

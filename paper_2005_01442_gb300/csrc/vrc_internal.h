@@ -407,7 +407,28 @@ struct RenderLaunch {
     const float4 *preint;          // MODE_PREINT only: the table for slabs of length step
     float4 *accum;                 // NULL, or the running (C, T) image of an ordered pass
     int accum_pitch;               // its pixels per row (the full image's width)
+    // checkpoints for the reverse mode (NULL: none): per pixel (first checkpointed segment,
+    // last composited sample) in ckpt_head, and ckpt_K floats from ckpt + pixel * ckpt_K: the
+    // transmittance at the start of segments of ckpt_seg samples
+    int2 *ckpt_head;
+    float *ckpt;
+    int ckpt_K, ckpt_seg;
 };
+
+// Checkpoint state of one ray while it is composited (reverse-mode checkpoints).
+struct CkState {
+    float *row;  // the ray's ckpt_K floats
+    int first;   // first segment written (-1: none yet)
+    int last;    // last segment written
+    int jlast;   // last composited sample (-1: none)
+};
+
+// Segments that the longest ray of a volume box can hold at `step` in segments of `seg`.
+inline int ckpt_segments(const int n[3], float step, int seg) {
+    const double d = __builtin_sqrt((double)n[0] * n[0] + (double)n[1] * n[1] + (double)n[2] * n[2]);
+    const double samples = __builtin_ceil(d / (double)step) + 2.0;
+    return (int)__builtin_ceil(samples / (double)seg);
+}
 
 // Bit of the cell holding sample base ip (ip in [-1, n-1]); 0: the sample's opacity is zero.
 __device__ __forceinline__ bool cell_open(const uint32_t *__restrict__ cells, int cwx,
@@ -502,7 +523,6 @@ cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st);
 // Reverse mode of one render: grad_out is the loss gradient per pixel (H x W x RGBA);
 // grad_tf (256 x 4) and grad_vol (nx*ny*nz, x fastest, may be NULL) are accumulated.
 constexpr int ADJ_MAX_SEG = 128;   // largest checkpoint interval (samples)
-constexpr int ADJ_MAX_CKPT = 256;  // checkpoints per ray: rays up to 256 * seg samples
 struct AdjointLaunch {
     RenderLaunch L;
     const float4 *grad_out;
@@ -511,6 +531,13 @@ struct AdjointLaunch {
     int seg;
 };
 cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st);
+
+// Microbenchmarks of the stencil's two roofs (k_microbench.cu): FP32 fused multiply-adds,
+// 16-byte loads that hit in L1, 16-byte loads from shared memory.
+enum { MB_FMA = 0, MB_L1 = 1, MB_LDS = 2 };
+size_t microbench_scratch_bytes();
+cudaError_t launch_microbench(int kind, int ctas, int iters, void *scratch, cudaStream_t st);
+double microbench_work(int kind, int ctas, int iters);  // flops (MB_FMA) or bytes per launch
 
 // Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
 // entries in arrival order; ctl holds the device-side front and the host-published tail.

@@ -29,7 +29,7 @@ EXPORTS = [
     "vrc_last_error_message", "vrc_status_str", "vrc_version", "vrc_aabbs_get",
     "vrc_pieces_build", "vrc_pieces_get", "vrc_pieces_free", "vrc_grid_order", "vrc_box_rect",
     "vrc_render_piece", "vrc_composite", "vrc_render_sortlast", "vrc_render_ordered",
-    "vrc_render_host_batch",
+    "vrc_render_host_batch", "vrc_ckpt_bytes", "vrc_microbench",
 ]
 
 
@@ -94,12 +94,15 @@ def load(build_if_missing: bool = False):
     L.vrc_occupancy_build.argtypes = [vp, ip, ip, ip, vp]
     L.vrc_occupancy_get.argtypes = [vp, ip, ip, ip, vp, vp]
     L.vrc_cellmask_get.argtypes = [vp, ip, ip, ip, vp, C.c_long, vp]
-    L.vrc_render.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp, vp]
+    L.vrc_render.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp, vp,
+                             vp]
+    L.vrc_ckpt_bytes.argtypes = [C.POINTER(vrc_camera), C.POINTER(vrc_params), ip, vp]
+    L.vrc_microbench.argtypes = [vp, ip, C.POINTER(C.c_double), vp]
     L.vrc_render_host.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp, vp]
     L.vrc_render_noalloc.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                      vp, vp]
     L.vrc_render_backward.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params),
-                                      vp, vp, vp, vp]
+                                      vp, vp, vp, vp, vp]
     L.vrc_server_create.argtypes = [vp, ip, C.POINTER(vp)]
     L.vrc_server_submit.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                     C.POINTER(C.c_longlong)]
@@ -129,8 +132,9 @@ def load(build_if_missing: bool = False):
     L.vrc_status_str.restype = C.c_char_p
     L.vrc_version.restype = ip
     for name in EXPORTS:
-        if name not in ("vrc_last_error_message", "vrc_status_str"):
+        if name not in ("vrc_last_error_message", "vrc_status_str", "vrc_ckpt_bytes"):
             getattr(L, name).restype = ip
+    L.vrc_ckpt_bytes.restype = C.c_size_t
     _lib = L
     return L
 

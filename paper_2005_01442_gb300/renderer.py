@@ -168,10 +168,13 @@ class Renderer:
     # -- rendering ----------------------------------------------------------------------------
     def render(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
                brick: int = 0, out=None, counters=None, stream=None, kernel: int = 0,
-               interp: int = 0, preclass: int = 0, phong=None, preint: int = 0):
+               interp: int = 0, preclass: int = 0, phong=None, preint: int = 0,
+               ckpt=None, seg_len: int = 64):
         """Renders into a (H, W, 4) float32 CUDA tensor (allocated when `out` is None).
-        `counters`: optional int64 CUDA tensor of 2 elements incremented by (nominal,
-        executed) samples."""
+        `counters`: optional int64 CUDA tensor of 3 elements incremented by (nominal,
+        executed, resampled) samples. `ckpt`: optional uint8 CUDA tensor of
+        ckpt_bytes(...) bytes that receives the reverse-mode checkpoints (segments of
+        `seg_len` samples)."""
         torch = _torch()
         if out is None:
             out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
@@ -180,13 +183,43 @@ class Renderer:
         assert out.numel() == cam.height * cam.width * 4
         cptr = None
         if counters is not None:
-            assert counters.is_cuda and counters.dtype == torch.int64 and counters.numel() == 2
+            assert counters.is_cuda and counters.dtype == torch.int64 and counters.numel() == 3
             cptr = C.c_void_p(counters.data_ptr())
+        kptr = None
+        if ckpt is not None:
+            assert ckpt.is_cuda and ckpt.is_contiguous()
+            kptr = C.c_void_p(ckpt.data_ptr())
         cs = native.camera_struct(cam)
-        ps = native.params_struct(step, ert, brick, 64, kernel, interp, preclass, phong, preint)
+        ps = native.params_struct(step, ert, brick, seg_len, kernel, interp, preclass, phong,
+                                  preint)
         self._ck(self.lib.vrc_render(self.ctx, int(vol_id), int(tf_id), C.byref(cs), C.byref(ps),
-                                     C.c_void_p(out.data_ptr()), cptr, _stream_ptr(stream)))
+                                     C.c_void_p(out.data_ptr()), cptr, kptr, _stream_ptr(stream)))
         return out
+
+    def ckpt_bytes(self, vol_id: int, cam, step: float = 0.5, seg_len: int = 64) -> int:
+        """vrc_ckpt_bytes: size of the checkpoint buffer of a render of `cam`."""
+        cs = native.camera_struct(cam)
+        ps = native.params_struct(step, 1.0, 0, seg_len, 0)
+        n = self.lib.vrc_ckpt_bytes(C.byref(cs), C.byref(ps), int(vol_id), self.ctx)
+        if n == 0:
+            raise native.VrcError(-1, self.lib.vrc_last_error_message(self.ctx).decode())
+        return int(n)
+
+    def ckpt_buffer(self, vol_id: int, cam, step: float = 0.5, seg_len: int = 64):
+        """A CUDA byte tensor for the checkpoints of a render of `cam` (256-byte aligned, as
+        the caching allocator returns every block)."""
+        torch = _torch()
+        t = torch.empty(self.ckpt_bytes(vol_id, cam, step, seg_len), dtype=torch.uint8,
+                        device=f"cuda:{self.device}")
+        assert t.data_ptr() % 256 == 0
+        return t
+
+    def microbench(self, kind: int, stream=None) -> float:
+        """vrc_microbench: 0 = FP32 flop/s, 1 = L1-hit 16-byte load bytes/s, 2 = shared-memory
+        16-byte load bytes/s, measured on this context's device."""
+        r = C.c_double()
+        self._ck(self.lib.vrc_microbench(self.ctx, int(kind), C.byref(r), _stream_ptr(stream)))
+        return r.value
 
     def render_host(self, vol_id: int, tf_id: int, cam, step: float = 0.5, ert: float = 1.0,
                     brick: int = 0, out=None, stream=None, kernel: int = 0,
@@ -225,14 +258,16 @@ class Renderer:
 
     def render_backward(self, vol_id: int, tf_id: int, cam, grad_out, grad_tf, grad_vol=None,
                         step: float = 0.5, ert: float = 1.0, brick: int = 0, seg_len: int = 64,
-                        stream=None):
+                        stream=None, ckpt=None, kernel: int = 0):
         """Adds dL/dTF to grad_tf (256x4 CUDA float32) and dL/dvoxel to grad_vol ((nz, ny, nx)
-        CUDA float32, optional) for dL/dimage = grad_out ((H, W, 4) CUDA float32)."""
+        CUDA float32, optional) for dL/dimage = grad_out ((H, W, 4) CUDA float32). `ckpt`: the
+        checkpoints of a render with the same arguments (else the call renders its own)."""
         g = grad_out.contiguous()
         cs = native.camera_struct(cam)
-        ps = native.params_struct(step, ert, brick, seg_len, 0)
+        ps = native.params_struct(step, ert, brick, seg_len, kernel)
         self._ck(self.lib.vrc_render_backward(
             self.ctx, int(vol_id), int(tf_id), C.byref(cs), C.byref(ps), C.c_void_p(g.data_ptr()),
+            C.c_void_p(ckpt.data_ptr()) if ckpt is not None else None,
             C.c_void_p(grad_tf.data_ptr()),
             C.c_void_p(grad_vol.data_ptr()) if grad_vol is not None else None,
             _stream_ptr(stream)))

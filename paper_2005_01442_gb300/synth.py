@@ -236,6 +236,29 @@ def tf_ct(seed: int | None = None, lo: float = CT_LO, hi: float = CT_HI) -> np.n
     return tf_from_control_points(xs, pts[:, 1:])
 
 
+_CT_DENSE_POINTS = np.array([
+    # HU,     r,    g,    b,    alpha (per unit voxel length)
+    [-1024.0, 0.00, 0.00, 0.00, 0.000],
+    [-300.0, 0.55, 0.35, 0.30, 0.000],
+    [-100.0, 0.75, 0.50, 0.42, 0.004],
+    [40.0, 0.85, 0.55, 0.45, 0.012],
+    [120.0, 0.90, 0.60, 0.50, 0.020],
+    [300.0, 0.95, 0.20, 0.15, 0.080],
+    [700.0, 1.00, 0.92, 0.82, 0.300],
+    [3071.0, 1.00, 1.00, 1.00, 0.800],
+])
+
+
+def tf_ct_dense(lo: float = CT_LO, hi: float = CT_HI) -> np.ndarray:
+    """Dense CT transfer function: air transparent, soft tissue (0-80 HU) semi-transparent at
+    about 0.01-0.02 opacity per voxel, vessels and bone more opaque. Rays through the body run
+    for hundreds of samples and nearly every occupied brick is resampled throughout -- the
+    regime where the stencil's gather and FP32 work, not empty-space skipping, set the
+    frame time."""
+    xs = (_CT_DENSE_POINTS[:, 0] - lo) / (hi - lo) * 255.0
+    return tf_from_control_points(xs, _CT_DENSE_POINTS[:, 1:])
+
+
 # ---------------------------------------------------------------------------------------
 # Cameras (inputs). Fields mirror the C struct used on both sides of the parity tests.
 

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "vrc.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*\s*|vrc_status\s+|int\s+)(vrc_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*\s*|vrc_status\s+|int\s+|size_t\s+)(vrc_\w+)\s*\(",
                                  src, re.M)))
 
 
@@ -45,7 +45,9 @@ def test_host_only_calls(lib):
     # NULL context and NULL outputs are rejected before touching the device
     assert lib.vrc_create(None, 0) == -1
     assert lib.vrc_destroy(None) == 0
-    assert lib.vrc_render(None, 1, 1, None, None, None, None, None) == -1
+    assert lib.vrc_render(None, 1, 1, None, None, None, None, None, None) == -1
+    assert lib.vrc_ckpt_bytes(None, None, 1, None) == 0
+    assert lib.vrc_microbench(None, 0, None, None) == -1
     assert lib.vrc_bricks_build(None, 1, 8, None) == -1
 
 

@@ -167,6 +167,137 @@ def test_gradients_match_central_differences(R, orc, torch):
     R.free_volume(vid)
 
 
+def _pixel_weights(rng, cam, n):
+    """A loss gradient that is zero except on n seeded pixels (N(0, 1) per channel)."""
+    g = np.zeros((cam.height, cam.width, 4), np.float32)
+    flat = rng.choice(cam.width * cam.height, size=n, replace=False)
+    g.reshape(-1, 4)[flat] = rng.normal(0, 1, (n, 4)).astype(np.float32)
+    return g, np.stack([flat % cam.width, flat // cam.width], -1)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("forward", ["replay", "split"])
+def test_backward_at_the_differentiation_config(R, orc, torch, forward):
+    """The differentiation workload's own sizes: 256^3 float32 CT, 512^2 images, 8^3 bricks;
+    4096 seeded pixels of each of 2 orbit cameras carry the loss. Gradients against the FP64
+    oracle's reverse mode on the same pixels, with checkpoints rendered by the backward call
+    itself (one ray per thread) or recorded by the split render."""
+    vol = synth.ct_float_downsampled(7)
+    tf = synth.tf_ct()
+    lo, hi = synth.CT_LO, synth.CT_HI
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, lo, hi)
+    rng = np.random.default_rng(14)
+    gtf = torch.zeros((256, 4), device="cuda")
+    gvol = torch.zeros(vol.shape, device="cuda")
+    rtf = np.zeros((256, 4))
+    rvol = np.zeros(vol.shape)
+    for cam in synth.orbit_cameras(7, 2, synth.dims_of(vol), 512, 512):
+        g, pix = _pixel_weights(rng, cam, 4096)
+        gt = torch.tensor(g, device="cuda")
+        ck = None
+        if forward == "split":
+            ck = R.ckpt_buffer(vid, cam, 0.5, 64)
+            R.render(vid, tid, cam, brick=8, ckpt=ck)
+        R.render_backward(vid, tid, cam, gt, gtf, gvol, step=0.5, brick=8, ckpt=ck)
+        a, b = orc.render_grad(vol, tf, lo, hi, cam, 0.5, g.reshape(-1, 4)[pix[:, 1] * cam.width
+                               + pix[:, 0]].astype(np.float64), brick=8, pixels=pix)
+        rtf += a
+        rvol += b
+    _rel_check_tf(gtf.cpu().numpy().astype(np.float64), rtf)
+    _rel_check_vol(gvol.cpu().numpy().astype(np.float64), rvol)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+@pytest.mark.parametrize("forward", ["replay", "ray", "split"])
+def test_long_rays_with_hundreds_of_checkpoints(R, orc, torch, forward):
+    """Rays of 6400 samples (a 48 x 48 x 1600 volume along z at step 0.25) in segments of 16:
+    400 checkpoints per ray, compared with the FP64 oracle's reverse mode; a perspective view
+    along the long axis as well."""
+    vol = synth.ct_volume((1600, 48, 48), seed=41).astype(np.float32)
+    tf = synth.tf_ct_dense()
+    tf[:, 3] *= 0.1  # about 0.0012 opacity per voxel: rays cross the whole volume
+    lo, hi = synth.CT_LO, synth.CT_HI
+    dims = synth.dims_of(vol)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, lo, hi)
+    cams = [synth.ortho_z_camera(dims, 12, 12),
+            synth.Camera(0, (23.5, 27.0, -300.0), (23.5, 23.5, 800.0), (0.0, 1.0, 0.0), 4.0,
+                         (0.0, 0.0), 10, 8).as_float32()]
+    rng = np.random.default_rng(43)
+    for cam in cams:
+        g = rng.normal(0, 1, (cam.height, cam.width, 4)).astype(np.float32)
+        gtf = torch.zeros((256, 4), device="cuda")
+        gvol = torch.zeros(vol.shape, device="cuda")
+        ck = None
+        if forward != "replay":
+            ck = R.ckpt_buffer(vid, cam, 0.25, 16)
+            assert ck.numel() >= 400 * 4 * cam.width * cam.height
+            R.render(vid, tid, cam, step=0.25, brick=8, ckpt=ck, seg_len=16,
+                     kernel=1 if forward == "ray" else 0)
+        R.render_backward(vid, tid, cam, torch.tensor(g, device="cuda"), gtf, gvol, step=0.25,
+                          brick=8, seg_len=16, ckpt=ck)
+        rtf, rvol = orc.render_grad(vol, tf, lo, hi, cam, 0.25, g.astype(np.float64), brick=8)
+        _rel_check_tf(gtf.cpu().numpy().astype(np.float64), rtf)
+        _rel_check_vol(gvol.cpu().numpy().astype(np.float64), rvol)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+def test_recorded_checkpoints_equal_replayed_ones(R, torch):
+    """Checkpoints recorded by the per-ray render equal the ones the backward renders itself
+    (same kernel arithmetic), so the gradients agree up to the order of float atomics; the
+    split render's checkpoints differ only by the rounding of its block compositing."""
+    vol, tf = _scene(seed=39)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(54, 1, synth.dims_of(vol), 40, 36)[0]
+    g = torch.randn((cam.height, cam.width, 4), device="cuda")
+    out = {}
+    for how in ("replay", "ray", "split"):
+        gtf = torch.zeros((256, 4), device="cuda")
+        gvol = torch.zeros(vol.shape, device="cuda")
+        ck = None
+        if how != "replay":
+            ck = R.ckpt_buffer(vid, cam)
+            R.render(vid, tid, cam, ert=0.999, brick=8, ckpt=ck, kernel=1 if how == "ray" else 6)
+        R.render_backward(vid, tid, cam, g, gtf, gvol, ert=0.999, brick=8, ckpt=ck)
+        out[how] = (gtf, gvol)
+    for a, b in zip(out["ray"], out["replay"]):
+        assert float((a - b).abs().max()) <= 1e-6 * float(b.abs().max())
+    for a, b in zip(out["split"], out["replay"]):
+        assert float((a - b).abs().max()) <= 2e-3 * float(b.abs().max())
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+def test_checkpoint_arguments_are_checked(R, torch):
+    from paper_2005_01442_gb300 import native
+    vol, tf = _scene(seed=40, shape=(20, 24, 28))
+    vid = R.upload_volume(vol)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    cam = synth.orbit_cameras(55, 1, synth.dims_of(vol), 16, 12)[0]
+    n = R.ckpt_bytes(vid, cam, 0.5, 64)
+    K = -(-(int(np.ceil(np.sqrt(20 ** 2 + 24 ** 2 + 28 ** 2) / 0.5)) + 2) // 64)
+    assert n >= 16 * 12 * (8 + 4 * K)
+    ck = R.ckpt_buffer(vid, cam, 0.5, 24)
+    with pytest.raises(native.VrcError):  # the split render checkpoints multiples of 16
+        R.render(vid, tid, cam, ckpt=ck, seg_len=24, kernel=6)
+    R.render(vid, tid, cam, ckpt=ck, seg_len=24, kernel=1)
+    with pytest.raises(native.VrcError):  # lane-group kernels record no checkpoints
+        R.render(vid, tid, cam, ckpt=ck, seg_len=24, kernel=3)
+    with pytest.raises(native.VrcError):  # default variant only
+        R.render(vid, tid, cam, ckpt=ck, seg_len=24, kernel=1, interp=1)
+    with pytest.raises(native.VrcError):  # unaligned buffer
+        R.render(vid, tid, cam, ckpt=ck[16:], seg_len=24, kernel=1)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
 def test_autograd_function(R, torch):
     from paper_2005_01442_gb300.autograd import DifferentiableRenderer
     vol, tf = _scene(seed=37, shape=(32, 36, 40))
@@ -183,9 +314,11 @@ def test_autograd_function(R, torch):
     tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
     gtf = torch.zeros((256, 4), device="cuda")
     gvol = torch.zeros(vol.shape, device="cuda")
-    for c in cams:
-        img = R.render(vid, tid, c, brick=8, ert=0.999)
-        R.render_backward(vid, tid, c, 2 * (img - target), gtf, gvol, brick=8, ert=0.999)
+    for c in cams:  # the autograd forward records checkpoints with the split render
+        ck = R.ckpt_buffer(vid, c)
+        img = R.render(vid, tid, c, brick=8, ert=0.999, ckpt=ck)
+        R.render_backward(vid, tid, c, 2 * (img - target), gtf, gvol, brick=8, ert=0.999,
+                          ckpt=ck)
     assert float((t.grad.cuda() - gtf).abs().max()) <= 1e-5 * float(gtf.abs().max())
     assert float((v.grad - gvol).abs().max()) <= 1e-5 * float(gvol.abs().max())
     R.free_volume(vid)

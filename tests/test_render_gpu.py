@@ -96,11 +96,11 @@ def test_phantom_orthographic_parity(R, orc, torch, kernel):
     cam = synth.ortho_z_camera((64, 64, 64), 128, 128)
     vid = R.upload_volume(vol)
     tid = R.set_tf(tf, synth.PHANTOM_LO, synth.PHANTOM_HI)
-    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
     img = R.render(vid, tid, cam, step=0.5, counters=cnt, kernel=kernel).cpu().numpy()
     ref = orc.render(vol, tf, synth.PHANTOM_LO, synth.PHANTOM_HI, cam, 0.5)
     _check(img, ref)
-    assert cnt.tolist() == [2097152, 2097152]
+    assert cnt.tolist() == [2097152, 2097152, 2097152]  # no skipping: all resampled
     R.free_volume(vid)
     R.free_tf(tid)
 
@@ -116,7 +116,7 @@ def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
         R.build_bricks(vid, B)
     tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
     for cam in synth.orbit_cameras(40, 3, synth.dims_of(vol), 96, 80):
-        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         img = R.render(vid, tid, cam, step=0.5, ert=ert, brick=B, counters=cnt,
                        kernel=kernel).cpu().numpy()
         ref, margin, rc = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=ert,
@@ -125,6 +125,9 @@ def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
         assert cnt[0].item() == rc[0] or abs(cnt[0].item() - rc[0]) <= 8  # segment counts
         # executed: samples in occupied bricks up to termination, as the oracle counts them
         # (a pixel whose termination float rounding decides may stop one sample apart)
+        assert cnt[2].item() <= cnt[1].item()  # resampled: executed minus clear cells
+        if B == 0:
+            assert cnt[2].item() == cnt[1].item()
         if ert >= 1.0:
             assert cnt[1].item() == rc[1]
         else:
@@ -143,10 +146,10 @@ def test_empty_space_leaping_bit_identical(R, torch, kernel):
     tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
     for cam in synth.orbit_cameras(41, 4, synth.dims_of(vol), 120, 90):
         for ert in (1.0, 0.999):
-            c0 = torch.zeros(2, dtype=torch.int64, device="cuda")
+            c0 = torch.zeros(3, dtype=torch.int64, device="cuda")
             ref = R.render(vid, tid, cam, ert=ert, brick=0, counters=c0, kernel=kernel)
             for B in (8, 16):
-                c1 = torch.zeros(2, dtype=torch.int64, device="cuda")
+                c1 = torch.zeros(3, dtype=torch.int64, device="cuda")
                 img = R.render(vid, tid, cam, ert=ert, brick=B, counters=c1, kernel=kernel)
                 assert torch.equal(img, ref)
                 assert c1[0] == c0[0] and c1[1] < c0[1]
@@ -343,13 +346,13 @@ def test_split_long_rays_parity_and_sample_count(R, orc, torch, B):
                 synth.orbit_cameras(9, 1, synth.dims_of(vol), 45, 38)[0]):
         ref, (onom, _) = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=1.0,
                                     return_counts=True)
-        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         img = R.render(vid, tid, cam, step=0.5, ert=1.0, brick=B, counters=cnt, kernel=6)
         _check(img.cpu().numpy(), ref)
-        nominal, executed = cnt.tolist()
-        assert nominal == onom
+        nominal, executed, resampled = cnt.tolist()
+        assert nominal == onom and resampled <= executed
         if B == 0:
-            assert executed == nominal
+            assert executed == nominal == resampled
         one = R.render(vid, tid, cam, step=0.5, ert=1.0, brick=B, kernel=1)
         assert float((img - one).abs().max()) <= 1e-5
     R.free_tf(tid)
@@ -520,8 +523,8 @@ def test_variants_rejected_by_adjoint_and_server(R, torch):
     gtf = torch.zeros((256, 4), device="cuda")
     st = R.lib.vrc_render_backward(R.ctx, vid, tid, C.byref(native.camera_struct(cam)),
                                    C.byref(native.params_struct(0.5, 1.0, 0, 64, 0, 1, 0)),
-                                   C.c_void_p(g.data_ptr()), C.c_void_p(gtf.data_ptr()), None,
-                                   None)
+                                   C.c_void_p(g.data_ptr()), None, C.c_void_p(gtf.data_ptr()),
+                                   None, None)
     assert st == -1
     srv = C.c_void_p()
     native.check(R.ctx, R.lib.vrc_server_create(R.ctx, 4, C.byref(srv)))
@@ -596,7 +599,7 @@ def test_preint_parity(R, orc, torch, kernel, step, ert):
     vid = R.upload_volume(vol)
     tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
     for cam in synth.orbit_cameras(48, 2, synth.dims_of(vol), 64, 56):
-        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         img = R.render(vid, tid, cam, step=step, ert=ert, kernel=kernel, preint=1,
                        counters=cnt).cpu().numpy()
         ref, margin, (nom, ex) = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, step,
@@ -604,7 +607,7 @@ def test_preint_parity(R, orc, torch, kernel, step, ert):
                                             preint=1)
         _check(img, ref, margin if ert < 1 else None)
         if ert >= 1.0:
-            assert cnt.tolist() == [nom, ex]
+            assert cnt.tolist() == [nom, ex, ex]
     R.free_tf(tid)
     R.free_volume(vid)
 

@@ -47,14 +47,40 @@ def test_noalloc_render_matches_render(env):
     for B in (8, 16):
         for kernel in (1, 2):
             for cam in cams:  # two calls in a row share (and overwrite) the fixed array
-                c0 = torch.zeros(2, dtype=torch.int64, device="cuda")
+                c0 = torch.zeros(3, dtype=torch.int64, device="cuda")
                 ref = R.render(vid, tid, cam, ert=0.999, brick=B, kernel=kernel, counters=c0)
                 out = torch.full_like(ref, float("nan"))
-                c1 = torch.zeros(2, dtype=torch.int64, device="cuda")
+                c1 = torch.zeros(3, dtype=torch.int64, device="cuda")
                 native.check(R.ctx, _noalloc(torch, native, R, vid, tid, cam, B, kernel, out, c1))
                 torch.cuda.synchronize()
                 assert float((out - ref).abs().max()) <= 1e-4
                 assert torch.equal(out, ref) and torch.equal(c0, c1)
+    assert R.last_device_error() == 0
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
+def test_noalloc_render_without_room_for_the_cell_mask(env):
+    """A volume whose cell-mask build scratch does not fit behind the brick fields (256 x 256 x
+    128: about 9 MB of run ids) renders without clear-cell skipping: the same pixels as
+    vrc_render, bit for bit, and at least as many executed samples."""
+    torch, native, R = env
+    vol = synth.ct_volume((128, 256, 256), seed=15)
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    R.build_bricks(vid, 16)
+    tid = R.set_tf(synth.tf_ct(), synth.CT_LO, synth.CT_HI)
+    cams = synth.orbit_cameras(25, 2, synth.dims_of(vol), 96, 80)
+    for B in (8, 16):
+        for cam in cams:  # two calls in a row
+            c0 = torch.zeros(3, dtype=torch.int64, device="cuda")
+            ref = R.render(vid, tid, cam, ert=0.999, brick=B, kernel=1, counters=c0)
+            out = torch.full_like(ref, float("nan"))
+            c1 = torch.zeros(3, dtype=torch.int64, device="cuda")
+            native.check(R.ctx, _noalloc(torch, native, R, vid, tid, cam, B, 1, out, c1))
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+            assert int(c1[0]) == int(c0[0]) and int(c1[1]) >= int(c0[1])
     assert R.last_device_error() == 0
     R.free_volume(vid)
     R.free_tf(tid)
