@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--cameras", type=int, default=16)
     p.add_argument("--kernel", type=int, default=0)
     p.add_argument("--no-dense", action="store_true")
+    p.add_argument("--tf", default="ct", choices=["ct", "dense"],
+                   help="transfer function of the headline frames (dense: soft tissue "
+                        "semi-transparent)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
@@ -68,8 +71,10 @@ def parse():
 
 
 def workload_config(args):
+    tf = "" if getattr(args, "tf", "ct") == "ct" else "_densetf"
     return {"workload": f"ct512x512x400_i16_to_1024sq_persp30_step0.5_B{args.brick}_ert0.999_"
-                        f"{args.cameras}cams",
+                        f"{args.cameras}cams{tf}",
+            "transfer_function": getattr(args, "tf", "ct"),
             "volume": [512, 512, 400], "volume_dtype": "int16", "image": [1024, 1024],
             "fovy_deg": 30.0, "step": 0.5, "brick": args.brick, "ert": 0.999,
             "cameras": args.cameras, "ct_seed": 3, "camera_seed": 4,
@@ -331,7 +336,7 @@ def main():
         return
 
     vol = synth.ct_volume()
-    tf = synth.tf_ct()
+    tf = synth.tf_ct() if args.tf == "ct" else synth.tf_ct_dense()
     dims = synth.dims_of(vol)
     cams = synth.orbit_cameras(4 + 1000 * rank, args.cameras, dims, 1024, 1024)
     R = Renderer(local)

@@ -99,9 +99,11 @@ def test_served_images_match_the_oracle(env, host_vols, orc):
     srv = serve.BatchedServer(R, max_slots=16, budget_ms=200.0, idle_ms=5.0)
     outs = [torch.full((r.cam.height, r.cam.width, 4), float("nan"), device="cuda") for r in reqs]
     handles = [srv.submit(r, o) for r, o in zip(reqs, outs)]
+    pending = set(range(len(reqs)))
     t0 = time.time()
-    while not all(srv.done(hd) for hd in handles):
+    while pending:
         srv.pump()
+        pending = {k for k in pending if not srv.done(handles[k])}
         assert time.time() - t0 < 60.0
     torch.cuda.synchronize()
     srv.close()
