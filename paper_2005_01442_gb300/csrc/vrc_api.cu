@@ -46,6 +46,8 @@ struct Volume {
     void *dpad = nullptr;          // compact padded copy (brick tables)
     float4 *drep = nullptr;        // x-replicated float4 copy (rendering)
     uint8_t *mask_scratch = nullptr;  // cell-mask build scratch (cellmask_scratch_bytes)
+    float *dpadf = nullptr;           // float32 copy of dpad (TMA-staged render), on first use
+    struct alignas(64) { unsigned char b[128]; } tmap;  // tensor map of dpadf
     Bricks bricks[2];               // B = 8, B = 16
     std::map<long, Occ> occ;        // key: tf_id * 2 + (B == 16)
 };
@@ -164,6 +166,7 @@ struct DeviceGuard {
 
 void free_volume(Volume &v) {
     cudaFree(v.dpad);
+    cudaFree(v.dpadf);
     cudaFree(v.drep);
     cudaFree(v.mask_scratch);
     for (auto &b : v.bricks) {
@@ -534,7 +537,10 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
     if (isnan(p->ert_threshold)) return fail(ctx, VRC_ERR_ARG, "ert_threshold is NaN");
     if (p->brick != 0 && p->brick != 8 && p->brick != 16)
         return fail(ctx, VRC_ERR_ARG, "brick must be 0, 8 or 16");
-    if (p->kernel < 0 || p->kernel > 6) return fail(ctx, VRC_ERR_ARG, "kernel must be 0..6");
+    if (p->kernel < 0 || p->kernel > 7) return fail(ctx, VRC_ERR_ARG, "kernel must be 0..7");
+    if (p->kernel == 7 && (p->interp || p->preclass || p->shade || p->preint))
+        return fail(ctx, VRC_ERR_ARG, "the TMA-staged render (kernel 7) renders the default "
+                                      "variant only");
     if ((p->interp != 0 && p->interp != 1) || (p->preclass != 0 && p->preclass != 1))
         return fail(ctx, VRC_ERR_ARG, "interp and preclass must be 0 or 1");
     if (p->shade != 0 && p->shade != 1) return fail(ctx, VRC_ERR_ARG, "shade must be 0 or 1");
@@ -574,6 +580,15 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
             t->preint_version = t->version;
         }
         L.preint = t->preint;
+    }
+    if (p->kernel == 7) {
+        if (!v->dpadf) {
+            CK(cudaMalloc(&v->dpadf, (size_t)v->pnx * v->pny * v->pnz * sizeof(float)),
+               "cudaMalloc(float volume)");
+            CK(launch_padded_to_float(view_of(*v), v->dpadf, st), "float volume launch");
+            CK(encode_tma_map(v->tmap.b, v->dpadf, v->pnx, v->pny, v->pnz), "tensor map");
+        }
+        L.tma_map = v->tmap.b;
     }
     L.phong.ka = p->ka;
     L.phong.kd = p->kd;
@@ -671,6 +686,8 @@ vrc_status launch_render(vrc_ctx *ctx, const vrc_params *params, RenderLaunch &L
         CK(launch_render_split(L, st), "render launch");
     } else if (k >= 2 && k <= 5) {
         CK(launch_render_warp(L, lanes_of(k), st), "render launch");
+    } else if (k == 7) {
+        CK(launch_render_tma(L.tma_map, L, st), "render launch");
     } else {
         CK(launch_render_ray(L, st), "render launch");
     }
@@ -812,6 +829,7 @@ vrc_status vrc_volume_update(vrc_ctx *ctx, int vol_id, const void *data, int on_
     }
     if (e == cudaSuccess) e = launch_pad_volume(src, v->dtype, v->n, v->dpad, v->pnx, v->pny, v->pnz, st);
     if (e == cudaSuccess) e = launch_replicate_x4(src, v->dtype, v->n, v->drep, st);
+    if (e == cudaSuccess && v->dpadf) e = launch_padded_to_float(view_of(*v), v->dpadf, st);
     if (staging) {
         cudaError_t e2 = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = e2;
@@ -1287,6 +1305,9 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
     // no queue here (it would need device memory): kernel 0 renders per ray
     if (params->kernel == 6)
         return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not run the split render (kernel 6)");
+    if (params->kernel == 7)
+        return fail(ctx, VRC_ERR_ARG, "vrc_render_noalloc does not run the TMA-staged render "
+                                      "(kernel 7: its float copy of the volume needs memory)");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     Volume *v = get_vol(ctx, vol_id);
@@ -1586,6 +1607,8 @@ vrc_status render_piece(vrc_ctx *ctx, Plan &p, int piece, const vrc_camera *cam,
                     params->brick, p.B);
     if (params->preint)
         return fail(ctx, VRC_ERR_ARG, "pre-integrated slabs span pieces: not with pieces");
+    if (params->kernel == 7)
+        return fail(ctx, VRC_ERR_ARG, "pieces render with kernels 0..6");
     RenderLaunch L;
     vrc_status s = prepare_render(ctx, p.vol_id, p.tf_id, cam, params, st, L);
     if (s != VRC_OK) return s;
@@ -1927,7 +1950,7 @@ vrc_status vrc_render_ordered(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
     if (s != VRC_OK) return s;
     if (!out_dev || ((uintptr_t)out_dev & 15) != 0)
         return fail(ctx, VRC_ERR_ARG, "out_dev must be non-NULL and 16-byte aligned");
-    if (params && params->kernel >= 2 && params->kernel <= 5)
+    if (params && params->kernel >= 2 && params->kernel != 6)
         return fail(ctx, VRC_ERR_ARG, "an ordered pass runs the split or per-ray kernel only");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;

@@ -121,6 +121,8 @@ struct RaySetup {
     ff d[3];     // unit direction
     ff L;        // t_out - t_in
     int nseg;    // number of segments (0 = miss)
+    float t0f;   // t_in in float: distance of the entry point from the eye (perspective) or
+                 // from the image plane (orthographic)
 };
 
 // Float-only slab test that reports rays missing the box by a clear margin (so that the
@@ -213,6 +215,7 @@ __device__ __forceinline__ void ray_setup(const CamDev &cam, const RayGrid &g, i
         r.pin[k] = ff_add(o[k], ff_mul(t0, d[k]));
     }
     r.L = ff_sub(t1, t0);
+    r.t0f = t0.hi + t0.lo;
     float Lf = r.L.hi + r.L.lo;
     float ns = ceilf(Lf / g.step);
     if (!(ns >= 1.0f)) ns = 1.0f;          // L > 0: at least one (short) segment

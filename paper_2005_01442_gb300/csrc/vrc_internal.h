@@ -413,6 +413,7 @@ struct RenderLaunch {
     int2 *ckpt_head;
     float *ckpt;
     int ckpt_K, ckpt_seg;
+    const void *tma_map;  // host address of the volume's tensor map (kernel 7; launcher only)
 };
 
 // Checkpoint state of one ray while it is composited (reverse-mode checkpoints).
@@ -516,6 +517,13 @@ cudaError_t launch_composite(const CompositeArgs &a, float4 *out, cudaStream_t s
 cudaError_t launch_accum_init(float4 *accum, long n, cudaStream_t st);
 cudaError_t launch_accum_finish(const float4 *accum, float4 *out, long n, cudaStream_t st);
 cudaError_t launch_render_ray(const RenderLaunch &L, cudaStream_t st);
+// TMA-staged render (k_render_tma.cu): a float32 copy of the padded volume (same layout as
+// VolView, element type float) and a tensor map of it (tma_map_bytes() bytes, 64-byte
+// aligned) are built once per volume; L.tma_map points at the map.
+cudaError_t launch_padded_to_float(const VolView &v, float *dst, cudaStream_t st);
+size_t tma_map_bytes();
+cudaError_t encode_tma_map(void *map_out, const float *base, int pnx, int pny, int pnz);
+cudaError_t launch_render_tma(const void *map, const RenderLaunch &L, cudaStream_t st);
 cudaError_t launch_render_warp(const RenderLaunch &L, int lanes_per_ray, cudaStream_t st);
 // Both phases of the split render; L.split.head must be zero (it is left nonzero).
 cudaError_t launch_render_split(const RenderLaunch &L, cudaStream_t st);

@@ -88,7 +88,7 @@ def test_occupancy_bit_exact(R, orc, B):
 
 # ------------------------------------------------------------- a3-a9: images vs the oracle
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_phantom_orthographic_parity(R, orc, torch, kernel):
     """64^3 uint16 phantom, 128^2 orthographic along +z, step 0.5, no skipping."""
     vol = synth.phantom()
@@ -105,7 +105,7 @@ def test_phantom_orthographic_parity(R, orc, torch, kernel):
     R.free_tf(tid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("B", [0, 8, 16])
 @pytest.mark.parametrize("ert", [1.0, 0.999])
 def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
@@ -136,7 +136,7 @@ def test_ct_perspective_parity(R, orc, torch, B, ert, kernel):
     R.free_tf(tid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_empty_space_leaping_bit_identical(R, torch, kernel):
     """Skipping (leaps over empty bricks, clear cells) changes no pixel, bit for bit."""
     vol = _ct_small(seed=5)
@@ -173,7 +173,7 @@ def test_early_termination_bound(R, torch):
     R.free_volume(vid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_float_volume_and_ragged_sizes(R, orc, kernel):
     rng = np.random.default_rng(9)
     vol = (rng.normal(0, 1, (13, 17, 19)).cumsum(0) * 40).astype(np.float32)
@@ -192,7 +192,7 @@ def test_float_volume_and_ragged_sizes(R, orc, kernel):
     R.free_volume(vid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_degenerate_cases(R, orc, kernel):
     tf = synth.tf_random(3)
     # 1x1x1 volume, 1x1 image, step longer than the box
@@ -287,7 +287,7 @@ def ct_full(R):
     R.free_tf(tid)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("B", [8, 16])
 def test_ct_full_size_sampled_parity(R, orc, torch, ct_full, B, kernel):
     """512^2 x 400 CT, 1024^2 perspective, step 0.5, ESL, ERT 0.999: 4096 sampled pixels per
@@ -303,6 +303,47 @@ def test_ct_full_size_sampled_parity(R, orc, torch, ct_full, B, kernel):
         _check(img[pix[:, 1], pix[:, 0]], ref, margin)
         noesl = R.render(vid, tid, cam, step=0.5, ert=0.999, brick=0, kernel=kernel).cpu().numpy()
         assert np.array_equal(img, noesl)
+
+
+@pytest.mark.parametrize("tf_kind", ["ct", "dense"])
+def test_tma_staged_render_equals_per_ray_kernel(R, torch, ct_full, tf_kind):
+    """The TMA-staged render (kernel 7) resamples from shared memory in the per-ray kernel's
+    order: the same image bit for bit, and the same sample counts, on the full-size CT with
+    both transfer functions, 1024^2 and 256^2 images (the latter covering several voxels per
+    pixel, where some windows fall back to L1)."""
+    vol, vid, tid = ct_full
+    if tf_kind == "dense":
+        tid = R.set_tf(synth.tf_ct_dense(), synth.CT_LO, synth.CT_HI)
+    for size in (1024, 256):
+        for cam in synth.orbit_cameras(11, 2, synth.dims_of(vol), size, size):
+            for B in (0, 8):
+                ca = torch.zeros(3, dtype=torch.int64, device="cuda")
+                cb = torch.zeros(3, dtype=torch.int64, device="cuda")
+                a = R.render(vid, tid, cam, ert=0.999, brick=B, kernel=1, counters=ca)
+                b = R.render(vid, tid, cam, ert=0.999, brick=B, kernel=7, counters=cb)
+                assert torch.equal(a, b), (size, B, float((a - b).abs().max()))
+                assert torch.equal(ca, cb)
+    if tf_kind == "dense":
+        R.free_tf(tid)
+    assert R.last_device_error() == 0
+
+
+def test_dense_tf_full_size_sampled_parity(R, orc, torch, ct_full):
+    """The dense transfer function (long rays, nearly every sample resampled) on the full-size
+    CT at 1024^2: 2048 sampled pixels of the split render and of the TMA-staged render against
+    the oracle."""
+    vol, vid, _ = ct_full
+    tf = synth.tf_ct_dense()
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    rng = np.random.default_rng(12)
+    cam = synth.orbit_cameras(13, 1, synth.dims_of(vol), 1024, 1024)[0]
+    pix = np.stack([rng.integers(0, 1024, 2048), rng.integers(0, 1024, 2048)], -1)
+    ref, margin = orc.render(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, ert=0.999, brick=8,
+                             pixels=pix, return_margin=True)
+    for kernel in (0, 7):
+        img = R.render(vid, tid, cam, ert=0.999, brick=8, kernel=kernel).cpu().numpy()
+        _check(img[pix[:, 1], pix[:, 0]], ref, margin)
+    R.free_tf(tid)
 
 
 def test_kernels_agree(R, torch, ct_full):
