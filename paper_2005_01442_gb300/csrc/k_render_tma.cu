@@ -17,7 +17,9 @@
 //      mbarrier that every thread waits on (bounded);
 //   4. every thread composites its ray's samples in the window -- exact placement, brick and
 //      cell-mask skipping, the 64-tap cubic B-spline from shared memory, classification,
-//      opacity correction, early termination -- exactly as the per-ray kernel does.
+//      opacity correction, early termination -- with the per-ray kernel's arithmetic (its
+//      float pre-test of clear cells is left out: it pays only where most samples are
+//      skipped, and the exact test decides the same way).
 //
 // Windows whose box does not fit (a tile that covers many voxels: small images, close-up
 // perspective) are resampled through L1 from the x-replicated layout instead; both paths
@@ -259,25 +261,12 @@ __global__ void __launch_bounds__(TM_THREADS, 8)
                 }
                 in_run = true;
             }
-            int qs = QS_EXACT;
-            if (ESL && cells && j < nseg - 1) {
-                qs = quick_skip(bricks, dist, cells, cwx, gn, Pf, df, step, j, run_lin,
-                                run_empty);
-                if (qs == QS_EMPTY_BRICK) {
-                    ++j;
-                    in_run = false;
-                    continue;
-                }
-                if (qs == QS_CLEAR_CELL) {
-                    ++j;
-                    ++executed;
-                    continue;
-                }
-            }
+            // exact placement first (nearly every sample that reaches here is resampled when
+            // rays are long), then the brick and cell tests on the exact cell
             int ip[3];
             float f[3], delta;
             place(rp, step, gn, j, ip, f, delta);
-            if (ESL && qs == QS_EXACT) {
+            if (ESL) {
                 const int lin = brick_of(bricks, ip);
                 if (lin != run_lin) {
                     run_lin = lin;
