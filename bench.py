@@ -264,6 +264,7 @@ def roofline(executed: int, resampled: int, launch_ms: float, peaks: dict, kerne
 
 
 SERVE_SIZES = [(512, 512), (1024, 1024), (2048, 2048)]
+SERVE_HBM_BUDGET = 8 << 30  # device bytes of the requests in flight (images + ray queues)
 
 
 def serve_bench(R, torch, vols, tids, runs, warmup, brick, seed):
@@ -282,15 +283,15 @@ def serve_bench(R, torch, vols, tids, runs, warmup, brick, seed):
     torch.cuda.synchronize()
     out = {"volumes": [list(d) for d in vols.values()], "transfer_functions": len(tids),
            "images": [f"{w}x{h}" for w, h in SERVE_SIZES],
-           "warmup_s": warmup, "hbm_image_budget_bytes": 2 << 30, "runs": []}
+           "warmup_s": warmup, "hbm_budget_bytes": SERVE_HBM_BUDGET, "runs": []}
     for rate, seconds in runs:
         reqs = serve.poisson_requests(seed, rate, seconds + warmup, list(vols), tids,
                                       SERVE_SIZES, cam_fn, brick=brick)
         for kind in ("plain", "batched"):
             srv = serve.BatchedServer(R, max_slots=1024) if kind == "batched" else \
                 serve.PlainServer(R)
-            budget = serve.ImageBudget(2 << 30, lambda h, w: torch.empty(
-                (h, w, 4), dtype=torch.float32, device="cuda"))
+            budget = serve.ImageBudget(SERVE_HBM_BUDGET, lambda h, w: torch.empty(
+                (h, w, 4), dtype=torch.float32, device="cuda"), srv.extra_bytes_per_pixel)
             res = serve.run_open_loop(srv, reqs, budget, warmup=warmup)
             srv.close()
             res.pop("latencies_s")

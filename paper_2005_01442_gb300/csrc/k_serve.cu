@@ -3,20 +3,36 @@
 // volumes, transfer functions, cameras and image sizes share one persistent launch.
 //
 // The host appends requests to a FIFO in device memory (a slot record holding the request's
-// full render launch, then the queue entry, then the published tail, in that order on a copy
-// stream) while the kernel runs. Each warp repeatedly takes the oldest request that still has
-// unclaimed tiles, claims its next 8 x 4 pixel tile with an atomic counter, and renders it with
-// the same per-ray body as vrc_render (so a request's image is bit-identical alone and in the
-// mix: rays never interact). When a request's last tile is done, the finishing warp publishes
-// the request's sequence number in host-mapped memory. Requests that arrive while others are
-// being rendered start as soon as warps free up: their tiles overlap on the device.
+// full render launch, then its tile claim word, then the queue entry, then the published
+// tail, in that order on a copy stream) while the kernel runs. A request renders with the
+// split render (the default) or the per-ray body, in the same code as vrc_render, so its image
+// equals vrc_render's of the same kernel bit for bit alone or in the mix (rays never interact):
+//
+//   phase 1: warps claim 8 x 4 pixel tiles of the request; each lane sets its ray up and leaps
+//            to its first sample that may be non-zero, and queues the ray in the request's own
+//            ray queue (split render) or renders it to the end (per-ray body);
+//   phase 2: when the request's last tile is done, its queued rays open for claiming; groups
+//            of 16 lanes finish them in blocks of 16 consecutive samples (group_march).
+//
+// Warps look at the oldest few unfinished requests and take queued rays of the oldest one
+// first, then tiles, so requests that arrive while others render start as soon as warps free
+// up and their work overlaps on the device. When a request's last tile (or last queued ray)
+// is done, the finishing warp publishes its sequence number in host-mapped memory.
+//
+// Claims cannot touch a recycled slot: work is claimed only from a 64-bit word holding
+// (request sequence number << 32 | items not yet claimed) by compare-and-swap while the
+// sequence number is the one the warp's queue entry names. The host writes a new request's
+// words so that every intermediate state reads as "nothing to claim": the record copy sets
+// the tile word to (seq, 0) and the ray word to (seq, unopened) over the finished request's
+// (old seq, 0) words, and a second 8-byte copy then sets the tile word to (seq, tiles).
 //
 // Every wait is bounded: the launch leaves when its time budget (globaltimer) runs out, when
 // the queue stays empty longer than the idle limit, or when the host raises the stop flag.
 // Leaving is a decision of the whole launch (the first warp to time out raises a flag; no warp
 // claims new work after it), never of single warps, so new requests are not left to a few
-// surviving warps; warps only leave between tiles, so a claimed tile is always finished. The
+// surviving warps; warps only leave between claims, so claimed work is always finished. The
 // host relaunches while work remains.
+#include "k_group.cuh"
 #include "k_ray_tile.cuh"
 
 namespace vrc {
@@ -32,7 +48,10 @@ __device__ __forceinline__ T load_volatile(const T *p) {
     return *(const volatile T *)p;
 }
 
-constexpr int SERVE_CLAIM_MAX = 8;  // most tiles claimed by one atomic
+constexpr int SERVE_CLAIM_MAX = 8;   // most tiles claimed at once
+constexpr int SERVE_RAYS_MAX = 16;   // most queued rays claimed at once (8 per group)
+constexpr int SERVE_SCAN = 8;        // queue entries a warp looks at from the front
+constexpr int SERVE_CAS_TRIES = 4;   // compare-and-swap attempts per claim word and look
 
 // Claims walk a request's tiles in the order k -> (k * stride) mod ntiles, stride coprime to
 // ntiles: the tiles of one claim lie far apart in the image, so costly regions (bone) spread
@@ -41,22 +60,93 @@ __device__ __forceinline__ int scattered_tile(int k, int ntiles, int stride) {
     return (int)(((long long)k * stride) % ntiles);
 }
 
-__global__ void __launch_bounds__(32 * SERVE_WARPS, 16 / SERVE_WARPS)
+// Takes up to max_chunk items (about rem / div) from a claim word whose sequence number is
+// eseq; on success *rem is the count before the claim and *chunk the count taken.
+__device__ __forceinline__ bool claim_items(unsigned long long *word, unsigned eseq,
+                                            unsigned div, unsigned max_chunk, unsigned *rem,
+                                            unsigned *chunk) {
+    unsigned long long w = load_volatile(word);
+    for (int t = 0; t < SERVE_CAS_TRIES; ++t) {
+        if ((unsigned)(w >> 32) != eseq) return false;
+        const unsigned r = (unsigned)w;
+        if (r == 0u || r == SERVE_UNOPENED) return false;
+        const unsigned c = min(min(max(r / div, 1u), max_chunk), r);
+        const unsigned long long old = atomicCAS(word, w, w - c);
+        if (old == w) {
+            *rem = r;
+            *chunk = c;
+            return true;
+        }
+        w = old;
+    }
+    return false;
+}
+
+// Phase 1 of a claim: tiles k0 .. k0 + chunk - 1 of the request (out of line, one function
+// per body, so that the control loop and each body get their own register allocation).
+template <bool ESL, bool SPLIT>
+__device__ __noinline__ void serve_tiles(const RenderLaunch &L, int k0, int chunk, int ntiles,
+                                         int stride) {
+    for (int k = k0; k < k0 + chunk; ++k)
+        render_ray_tile<ESL, SPLIT>(L, scattered_tile(k, ntiles, stride));
+}
+
+// Phase 2 of a claim: queued rays c0 .. c0 + chunk - 1, alternately to the warp's two groups
+// of 16 lanes, each finished with group_march and written out.
+__device__ __noinline__ void serve_rays(const RenderLaunch &L, unsigned c0, unsigned chunk,
+                                        unsigned nf) {
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (SPLIT_G - 1), gbase = lane & ~(SPLIT_G - 1), group = lane >> 4;
+    const unsigned gmask = ((1u << SPLIT_G) - 1u) << gbase;
+    const float inv_step = 1.0f / L.grid.step;
+    const long nbricks = (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
+    unsigned long long executed = 0;
+    unsigned resampled = 0;
+    for (unsigned c = c0 + group; c < c0 + chunk; c += 2) {
+        const unsigned qi = c < nf ? c : L.split.cap - 1u - (c - nf);
+        RayPos rp;
+        int jlo, pix;
+        float RC0, RC1, RC2, RT;
+        split_load(L.split.rec + (long)qi * SPLIT_REC, rp, jlo, pix, RC0, RC1, RC2, RT);
+        float Pf[3], df[3], inv_df[3];
+        ray_float(rp, Pf, df, inv_df);
+        if (L.dist) {
+            const uint8_t *dist = L.dist + octant_of(df) * nbricks;
+            group_march<true, SPLIT_G>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q,
+                                       gbase, RC0, RC1, RC2, RT, executed, resampled);
+        } else {
+            group_march<false, SPLIT_G>(L, rp, nullptr, Pf, df, inv_df, inv_step, jlo, gmask,
+                                        q, gbase, RC0, RC1, RC2, RT, executed, resampled);
+        }
+        if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
+    }
+}
+
+// Marks a request finished for the host (after every pixel write of it).
+__device__ __forceinline__ void publish_done(int *done_flags, int slot, unsigned seq) {
+    __threadfence_system();
+    *(volatile int *)&done_flags[slot] = (int)seq;
+}
+
+__global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
     serve_kernel(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
-                 int *done_flags, unsigned long long budget_ns, unsigned long long idle_ns) {
+                 int *done_flags, unsigned long long *front_mirror,
+                 unsigned long long budget_ns, unsigned long long idle_ns) {
     // per-warp copy of the current request's launch record (reloaded when the request changes)
     __shared__ RenderLaunch s_launch[SERVE_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RenderLaunch &L = s_launch[warp];
-    int cached_slot = -1, cached_seq = -1;
+    int cached_slot = -1;
+    unsigned cached_seq = 0;
+    const unsigned nwarps = gridDim.x * SERVE_WARPS;
     const unsigned long long start = global_ns();
     unsigned long long idle_since = 0;
     unsigned sleep_ns = 256;
     while (true) {
-        // lane 0 takes every control decision; the warp follows it (render_ray_tile needs all
-        // 32 lanes together)
-        int action = 0;  // 0 = leave, 1 = idle, 2 = retry, 3 = render (slot, tile)
-        int slot = 0, tile = 0, ntiles = 0, seq = 0, chunk = 1;
+        // lane 0 takes every control decision; the warp follows it
+        int action = 0;  // 0 leave, 1 idle, 2 nothing claimable now, 3 tiles, 4 queued rays
+        int slot = 0;
+        unsigned seq = 0, rem = 0, chunk = 0;
         if (lane == 0) {
             const unsigned long long now = global_ns();
             if (load_volatile(&ctl->stop) || load_volatile(&ctl->leaving)) {
@@ -77,41 +167,59 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 16 / SERVE_WARPS)
                     }
                 } else {
                     idle_since = 0;
-                    slot = __ldcg(&queue[f % cap].slot);
-                    const int eseq = __ldcg(&queue[f % cap].seq);
-                    ServeSlot *S = slots + slot;
-                    // guided claims: big chunks while many tiles are left, single tiles at the
-                    // end of a request (its latency is that of its slowest warp)
-                    ntiles = __ldcg(&S->ntiles);
-                    const int left = ntiles - load_volatile(&S->next_tile);
-                    chunk = min(max(left / (2 * (int)gridDim.x * SERVE_WARPS), 1), SERVE_CLAIM_MAX);
-                    tile = atomicAdd(&S->next_tile, chunk);
-                    seq = __ldcg(&S->seq);
-                    if (tile >= ntiles || seq != eseq) {
-                        // every tile of the front request is claimed: move the front on
-                        atomicCAS(&ctl->front, f, f + 1);
-                        action = 2;
-                    } else {
-                        action = 3;
+                    action = 2;
+                    for (int k = 0; k < SERVE_SCAN && f + k < t; ++k) {
+                        const ServeEntry *e = &queue[(f + k) % cap];
+                        const int es = __ldcg(&e->slot);
+                        const unsigned eq = (unsigned)__ldcg(&e->seq);
+                        ServeSlot *S = slots + es;
+                        const unsigned long long w1 = load_volatile(&S->p1);
+                        if ((unsigned)(w1 >> 32) != eq) {  // finished, slot already reused
+                            if (k == 0 && atomicCAS(&ctl->front, f, f + 1) == f)
+                                *(volatile unsigned long long *)front_mirror = f + 1;
+                            continue;
+                        }
+                        // the oldest request's queued rays first, then tiles
+                        if (claim_items(&S->p2, eq, 2 * nwarps, SERVE_RAYS_MAX, &rem, &chunk)) {
+                            action = 4;
+                        } else if (claim_items(&S->p1, eq, 2 * nwarps, SERVE_CLAIM_MAX, &rem,
+                                               &chunk)) {
+                            action = 3;
+                        }
+                        if (action != 2) {
+                            slot = es;
+                            seq = eq;
+                            break;
+                        }
+                        if (k == 0) {
+                            // every tile claimed and every queued ray claimed (or none to
+                            // come): move the front on
+                            const unsigned long long w2 = load_volatile(&S->p2);
+                            if ((unsigned)load_volatile(&S->p1) == 0u &&
+                                (unsigned)(w2 >> 32) == eq && (unsigned)w2 == 0u &&
+                                atomicCAS(&ctl->front, f, f + 1) == f)
+                                *(volatile unsigned long long *)front_mirror = f + 1;
+                        }
                     }
                 }
             }
         }
         action = __shfl_sync(0xffffffffu, action, 0);
         if (action == 0) break;
-        if (action == 1) {  // idle: exponential back-off up to 32 us between polls
+        if (action == 1 || action == 2) {  // exponential back-off up to 32 us between polls
             __nanosleep(sleep_ns);
-            sleep_ns = min(sleep_ns * 2u, 32768u);
+            sleep_ns = min(sleep_ns * 2u, action == 1 ? 32768u : 4096u);
             continue;
         }
         sleep_ns = 256;
-        if (action == 2) continue;
         slot = __shfl_sync(0xffffffffu, slot, 0);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        ntiles = __shfl_sync(0xffffffffu, ntiles, 0);
         seq = __shfl_sync(0xffffffffu, seq, 0);
+        rem = __shfl_sync(0xffffffffu, rem, 0);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         ServeSlot *S = slots + slot;
+        // a successful claim keeps the request (and its slot record) alive until this warp's
+        // work is done
+        __threadfence();
         if (slot != cached_slot || seq != cached_seq) {
             // the request's launch record, read around L1 (the host rewrites recycled slots)
             const int *src = (const int *)&S->L;
@@ -120,22 +228,51 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 16 / SERVE_WARPS)
                 dst[i] = __ldcg(src + i);
             cached_slot = slot;
             cached_seq = seq;
-            __syncwarp();
-        }
-        const int last = min(tile + chunk, ntiles);
-        const int stride = __ldcg(&S->stride);
-        for (int k = tile; k < last; ++k) {
-            const int t = scattered_tile(k, ntiles, stride);
-            if (L.dist) render_ray_tile<true>(L, t);
-            else render_ray_tile<false>(L, t);
         }
         __syncwarp();
-        if (lane == 0) {
-            __threadfence();  // these tiles' pixels before the count
-            const int d = atomicAdd(&S->done_tiles, last - tile);
-            if (d + (last - tile) == ntiles) {
-                __threadfence_system();  // every tile's pixels before the host sees completion
-                *(volatile int *)&done_flags[slot] = seq;
+        const bool split = L.split.head != nullptr;
+        if (action == 3) {
+            // phase 1: tiles k = ntiles - rem .. ntiles - rem + chunk - 1
+            const int ntiles = __ldcg(&S->ntiles), stride = __ldcg(&S->stride);
+            const int k0 = ntiles - (int)rem;
+            if (split) {
+                if (L.dist) serve_tiles<true, true>(L, k0, (int)chunk, ntiles, stride);
+                else serve_tiles<false, true>(L, k0, (int)chunk, ntiles, stride);
+            } else {
+                if (L.dist) serve_tiles<true, false>(L, k0, (int)chunk, ntiles, stride);
+                else serve_tiles<false, false>(L, k0, (int)chunk, ntiles, stride);
+            }
+            __threadfence();  // these tiles' pixels and queued rays before the count
+            __syncwarp();
+            if (lane == 0) {
+                const int d = atomicAdd(&S->p1_done, (int)chunk);
+                if (d + (int)chunk == ntiles) {  // this warp finished the request's phase 1
+                    __threadfence();
+                    unsigned total = 0, nf = 0;
+                    if (split) {
+                        nf = __ldcg(&L.split.head[0]);
+                        total = min(nf + __ldcg(&L.split.head[2]), L.split.cap);
+                    }
+                    if (total > 0) {
+                        S->p2_total = (int)total;
+                        S->p2_nf = (int)nf;
+                        __threadfence();
+                        atomicExch(&S->p2, ((unsigned long long)seq << 32) | total);
+                    } else {
+                        atomicExch(&S->p2, (unsigned long long)seq << 32);
+                        publish_done(done_flags, slot, seq);
+                    }
+                }
+            }
+        } else {
+            // phase 2: queued rays c = total - rem .. total - rem + chunk - 1
+            const unsigned total = (unsigned)__ldcg(&S->p2_total);
+            serve_rays(L, total - rem, chunk, (unsigned)__ldcg(&S->p2_nf));
+            __threadfence();  // these rays' pixels before the count
+            __syncwarp();
+            if (lane == 0) {
+                const int d = atomicAdd(&S->p2_done, (int)chunk);
+                if (d + (int)chunk == (int)total) publish_done(done_flags, slot, seq);
             }
         }
         __syncwarp();
@@ -145,10 +282,11 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 16 / SERVE_WARPS)
 const void *serve_kernel_ptr() { return (const void *)serve_kernel; }
 
 cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
-                         int *done_flags, unsigned long long budget_ns,
-                         unsigned long long idle_ns, int ctas, cudaStream_t st) {
-    serve_kernel<<<ctas, 32 * SERVE_WARPS, 0, st>>>(slots, queue, cap, ctl, done_flags, budget_ns,
-                                                    idle_ns);
+                         int *done_flags, unsigned long long *front_mirror,
+                         unsigned long long budget_ns, unsigned long long idle_ns, int ctas,
+                         cudaStream_t st) {
+    serve_kernel<<<ctas, 32 * SERVE_WARPS, 0, st>>>(slots, queue, cap, ctl, done_flags,
+                                                    front_mirror, budget_ns, idle_ns);
     return cudaGetLastError();
 }
 

@@ -1373,6 +1373,9 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
 // ------------------------------------------------------------------------------------------
 // Persistent batched serving (kernel in k_serve.cu). The host side publishes requests into
 // device memory through a copy stream while the persistent kernel runs on its own stream.
+// Split-render requests get their own ray queue from a stream-ordered memory pool the server
+// owns (allocated on the copy stream at submission, freed there once the request is done), so
+// no allocation waits for the running kernel.
 struct vrc_server {
     vrc_ctx *ctx = nullptr;
     int max_slots = 0, cap = 0, ctas = 0;
@@ -1380,16 +1383,20 @@ struct vrc_server {
     ServeEntry *d_queue = nullptr;
     ServeCtl *d_ctl = nullptr;
     int *h_done = nullptr, *d_done = nullptr;        // host-mapped completion flags
+    unsigned long long *h_front = nullptr, *d_front = nullptr;  // host-mapped front mirror
     ServeSlot *h_slot_stage = nullptr;               // pinned staging, one record per slot
+    unsigned long long *h_claim_stage = nullptr;     // pinned staging, one tile word per slot
     ServeEntry *h_entry_stage = nullptr;             // pinned staging ring (cap)
     unsigned long long *h_tail_stage = nullptr;      // pinned staging ring (cap)
     int *h_stop_stage = nullptr;
     cudaStream_t s_ctl = nullptr, s_run = nullptr;
     cudaEvent_t ev_run = nullptr;
+    cudaMemPool_t pool = nullptr;
     bool launched = false;
     unsigned long long tail = 0;
     long long next_seq = 0;
     std::vector<long long> slot_seq;  // request in each slot, -1 when free
+    std::vector<void *> region;       // ray queue of the split request in each slot
 };
 
 namespace {
@@ -1397,15 +1404,22 @@ namespace {
 void server_free(vrc_server *s) {
     if (!s) return;
     if (s->s_run) cudaStreamSynchronize(s->s_run);
-    if (s->s_ctl) cudaStreamSynchronize(s->s_ctl);
+    if (s->s_ctl) {
+        for (void *r : s->region)
+            if (r) cudaFreeAsync(r, s->s_ctl);
+        cudaStreamSynchronize(s->s_ctl);
+    }
     cudaFree(s->d_slots);
     cudaFree(s->d_queue);
     cudaFree(s->d_ctl);
     cudaFreeHost(s->h_done);
+    cudaFreeHost(s->h_front);
     cudaFreeHost(s->h_slot_stage);
+    cudaFreeHost(s->h_claim_stage);
     cudaFreeHost(s->h_entry_stage);
     cudaFreeHost(s->h_tail_stage);
     cudaFreeHost(s->h_stop_stage);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->ev_run) cudaEventDestroy(s->ev_run);
     if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
     if (s->s_run) cudaStreamDestroy(s->s_run);
@@ -1415,6 +1429,14 @@ void server_free(vrc_server *s) {
 bool server_slot_free(vrc_server *s, int slot) {
     const long long q = s->slot_seq[slot];
     return q < 0 || *(volatile int *)&s->h_done[slot] == (int)q;
+}
+
+// Returns a finished request's ray queue to the pool (stream-ordered on the copy stream).
+void server_release_region(vrc_server *s, int slot) {
+    if (s->region[slot]) {
+        cudaFreeAsync(s->region[slot], s->s_ctl);
+        s->region[slot] = nullptr;
+    }
 }
 
 }  // namespace
@@ -1431,22 +1453,36 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
     s->max_slots = max_slots;
     s->cap = 4 * max_slots;
     s->slot_seq.assign(max_slots, -1);
+    s->region.assign(max_slots, nullptr);
     cudaError_t e = cudaSuccess;
     auto ck = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     ck(cudaMalloc(&s->d_slots, sizeof(ServeSlot) * max_slots));
     ck(cudaMalloc(&s->d_queue, sizeof(ServeEntry) * s->cap));
     ck(cudaMalloc(&s->d_ctl, sizeof(ServeCtl)));
     ck(cudaHostAlloc(&s->h_done, sizeof(int) * max_slots, cudaHostAllocMapped));
+    ck(cudaHostAlloc(&s->h_front, sizeof(unsigned long long), cudaHostAllocMapped));
     ck(cudaHostAlloc(&s->h_slot_stage, sizeof(ServeSlot) * max_slots, cudaHostAllocDefault));
+    ck(cudaHostAlloc(&s->h_claim_stage, sizeof(unsigned long long) * max_slots, cudaHostAllocDefault));
     ck(cudaHostAlloc(&s->h_entry_stage, sizeof(ServeEntry) * s->cap, cudaHostAllocDefault));
     ck(cudaHostAlloc(&s->h_tail_stage, sizeof(unsigned long long) * s->cap, cudaHostAllocDefault));
     ck(cudaHostAlloc(&s->h_stop_stage, sizeof(int), cudaHostAllocDefault));
     if (e == cudaSuccess) ck(cudaHostGetDevicePointer((void **)&s->d_done, s->h_done, 0));
+    if (e == cudaSuccess) ck(cudaHostGetDevicePointer((void **)&s->d_front, s->h_front, 0));
     ck(cudaStreamCreateWithFlags(&s->s_ctl, cudaStreamNonBlocking));
     ck(cudaStreamCreateWithFlags(&s->s_run, cudaStreamNonBlocking));
     ck(cudaEventCreateWithFlags(&s->ev_run, cudaEventDisableTiming));
     if (e == cudaSuccess) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        ck(cudaMemPoolCreate(&s->pool, &props));
+        unsigned long long keep = ~0ull;  // keep freed queues mapped for the next requests
+        if (e == cudaSuccess) ck(cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    if (e == cudaSuccess) {
         for (int i = 0; i < max_slots; ++i) s->h_done[i] = -1;
+        *s->h_front = 0;
         ck(cudaMemset(s->d_ctl, 0, sizeof(ServeCtl)));
         ck(cudaMemset(s->d_slots, 0, sizeof(ServeSlot) * max_slots));
         int per_sm = 0, sms = 0;
@@ -1472,46 +1508,78 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     if (!ticket) return fail(ctx, VRC_ERR_ARG, "ticket is NULL");
     if (!out_rgba_dev || ((uintptr_t)out_rgba_dev & 15) != 0)
         return fail(ctx, VRC_ERR_ARG, "out_rgba_dev must be a 16-byte aligned device pointer");
-    if (params && params->kernel >= 2)
-        return fail(ctx, VRC_ERR_ARG, "the server renders with the per-ray kernel (kernel 0 or 1)");
-    if (params && (params->interp || params->preclass || params->shade || params->preint))
+    if (!params) return fail(ctx, VRC_ERR_ARG, "params is NULL");
+    if (params->kernel != 0 && params->kernel != 1 && params->kernel != 6)
+        return fail(ctx, VRC_ERR_ARG, "the server renders with the split render (kernel 0 or 6) "
+                                      "or the per-ray kernel (1)");
+    if (params->interp || params->preclass || params->shade || params->preint)
         return fail(ctx, VRC_ERR_ARG, "the server renders the default variant only");
     DeviceGuard g(ctx->device);
     const int slot = (int)(s->next_seq % s->max_slots);
     if (!server_slot_free(s, slot)) return fail(ctx, VRC_ERR_BUSY, "all %d slots in flight", s->max_slots);
+    // the ring must not overwrite entries the kernel may still read (from the front on)
+    if (s->tail - *(volatile unsigned long long *)s->h_front >= (unsigned long long)s->cap)
+        return fail(ctx, VRC_ERR_BUSY, "the request queue is full");
     ServeSlot &rec = s->h_slot_stage[slot];
     vrc_status st = prepare_render(ctx, vol_id, tf_id, cam, params, s->s_ctl, rec.L);
     if (st != VRC_OK) return st;
+    server_release_region(s, slot);  // a finished request nobody polled
+    const bool split = params->kernel != 1;
+    const size_t npix = (size_t)cam->width * cam->height;
+    if (split) {
+        void *r = nullptr;
+        const size_t bytes = 256 + npix * SPLIT_REC * sizeof(float4);
+        cudaError_t e = cudaMallocFromPoolAsync(&r, bytes, s->pool, s->s_ctl);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, VRC_ERR_OOM, "no device memory for a ray queue of %zu bytes", bytes);
+        }
+        s->region[slot] = r;
+        CK(cudaMemsetAsync(r, 0, 256, s->s_ctl), "server submit");
+        rec.L.split.head = (unsigned *)r;
+        rec.L.split.rec = (float4 *)((unsigned char *)r + 256);
+        rec.L.split.cap = (unsigned)npix;
+        rec.L.split.long_len = (unsigned)(0.35f * (rec.L.grid.n[0] + rec.L.grid.n[1] +
+                                                    rec.L.grid.n[2]) / 3.0f / rec.L.grid.step);
+    }
     rec.L.out = (float4 *)out_rgba_dev;
     rec.L.counters = nullptr;
     rec.ntiles = ((cam->width + 7) / 8) * ((cam->height + 3) / 4);
     {
         // a stride near ntiles / golden ratio, made coprime to ntiles
         auto gcd = [](long a, long b) { while (b) { long t = a % b; a = b; b = t; } return a; };
-        long st = (long)(rec.ntiles * 0.6180339887) | 1;
-        while (rec.ntiles > 1 && gcd(st, rec.ntiles) != 1) ++st;
-        rec.stride = rec.ntiles > 1 ? (int)(st % rec.ntiles) : 1;
+        long st2 = (long)(rec.ntiles * 0.6180339887) | 1;
+        while (rec.ntiles > 1 && gcd(st2, rec.ntiles) != 1) ++st2;
+        rec.stride = rec.ntiles > 1 ? (int)(st2 % rec.ntiles) : 1;
         if (rec.stride == 0) rec.stride = 1;
     }
-    rec.next_tile = 0;
-    rec.done_tiles = 0;
     const long long seq = s->next_seq++;
-    rec.seq = (int)(seq & 0x7fffffff);
-    s->slot_seq[slot] = rec.seq;
+    const unsigned useq = (unsigned)(seq & 0x7fffffff);
+    rec.p1 = (unsigned long long)useq << 32;                    // nothing to claim yet
+    rec.p2 = ((unsigned long long)useq << 32) | SERVE_UNOPENED;  // phase 1 not finished
+    rec.p1_done = 0;
+    rec.p2_total = 0;
+    rec.p2_nf = 0;
+    rec.p2_done = 0;
+    s->h_claim_stage[slot] = ((unsigned long long)useq << 32) | (unsigned)rec.ntiles;
+    s->slot_seq[slot] = (long long)useq;
     s->h_done[slot] = -1;
     const int qi = (int)(s->tail % (unsigned long long)s->cap);
     s->h_entry_stage[qi].slot = slot;
-    s->h_entry_stage[qi].seq = rec.seq;
+    s->h_entry_stage[qi].seq = (int)useq;
     s->tail += 1;
     s->h_tail_stage[qi] = s->tail;
-    // record, then queue entry, then tail: stream order makes each visible before the next
+    // record, then its tile claim word, then queue entry, then tail: stream order makes each
+    // visible before the next
     CK(cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(ServeSlot), cudaMemcpyHostToDevice, s->s_ctl),
        "server submit");
+    CK(cudaMemcpyAsync(&s->d_slots[slot].p1, &s->h_claim_stage[slot], sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, s->s_ctl), "server submit");
     CK(cudaMemcpyAsync(s->d_queue + qi, &s->h_entry_stage[qi], sizeof(ServeEntry),
                        cudaMemcpyHostToDevice, s->s_ctl), "server submit");
     CK(cudaMemcpyAsync(&s->d_ctl->tail, &s->h_tail_stage[qi], sizeof(unsigned long long),
                        cudaMemcpyHostToDevice, s->s_ctl), "server submit");
-    *ticket = rec.seq;
+    *ticket = (long long)useq;
     return VRC_OK;
 }
 
@@ -1535,7 +1603,7 @@ extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long l
             // the published tail must reach the device before the kernel could idle out
             CK(cudaStreamSynchronize(s->s_ctl), "server publish");
             CK(cudaMemsetAsync(&s->d_ctl->leaving, 0, sizeof(int), s->s_run), "serve launch");
-            CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done,
+            CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
                             (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
                             s->s_run), "serve launch");
             CK(cudaEventRecord(s->ev_run, s->s_run), "serve launch");
@@ -1554,7 +1622,11 @@ extern "C" vrc_status vrc_server_poll(vrc_server *s, long long ticket, int *done
     if (ticket < 0 || s->slot_seq[slot] != ticket)
         return fail(s->ctx, VRC_ERR_ARG, "ticket %lld is not in flight", ticket);
     *done = *(volatile int *)&s->h_done[slot] == (int)ticket ? 1 : 0;
-    if (*done) s->slot_seq[slot] = -1;
+    if (*done) {
+        s->slot_seq[slot] = -1;
+        DeviceGuard g(s->ctx->device);
+        server_release_region(s, slot);
+    }
     return VRC_OK;
 }
 

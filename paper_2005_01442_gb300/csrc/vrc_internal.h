@@ -549,29 +549,36 @@ double microbench_work(int kind, int ctas, int iters);  // flops (MB_FMA) or byt
 
 // Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
 // entries in arrival order; ctl holds the device-side front and the host-published tail.
-constexpr int SERVE_WARPS = 2;  // warps per CTA of the persistent kernel
+constexpr int SERVE_WARPS = 4;                    // warps per CTA of the persistent kernel
+constexpr unsigned SERVE_UNOPENED = 0xffffffffu;  // ray claim word: phase 1 not finished
 struct ServeSlot {
-    RenderLaunch L;  // the request's render
-    int ntiles;      // 8 x 4 pixel tiles of its image
-    int next_tile;   // tiles claimed (device atomics)
-    int done_tiles;  // tiles finished (device atomics)
-    int seq;         // request sequence number (published on completion)
-    int stride;      // tile order: k -> k * stride mod ntiles (stride coprime to ntiles)
-    int pad[3];
+    RenderLaunch L;          // the request's render (L.split.head != NULL: split render, with
+                             // the request's own ray queue)
+    unsigned long long p1;   // (seq << 32) | tiles not yet claimed
+    unsigned long long p2;   // (seq << 32) | queued rays not yet claimed, or SERVE_UNOPENED
+    int ntiles;              // 8 x 4 pixel tiles of its image
+    int stride;              // tile order: k -> k * stride mod ntiles (stride coprime to ntiles)
+    int p1_done;             // tiles finished (device atomics)
+    int p2_total;            // rays phase 1 queued (set when phase 1 finishes)
+    int p2_nf;               // of them, records at the queue's front
+    int p2_done;             // queued rays finished (device atomics)
 };
 struct ServeEntry {
     int slot;
     int seq;
 };
 struct ServeCtl {
-    unsigned long long front;  // oldest queue entry that may still have unclaimed tiles
+    unsigned long long front;  // oldest queue entry that may still have work to claim
     unsigned long long tail;   // entries published by the host
     int stop;                  // host request to leave
     int leaving;               // set by the first warp that times out; no new claims after it
 };
 const void *serve_kernel_ptr();
+// front_mirror: host-mapped copy of ctl->front (a lower bound of it) that the host reads
+// before it publishes a new entry into the ring of `cap` entries
 cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
-                         int *done_flags, unsigned long long budget_ns,
-                         unsigned long long idle_ns, int ctas, cudaStream_t st);
+                         int *done_flags, unsigned long long *front_mirror,
+                         unsigned long long budget_ns, unsigned long long idle_ns, int ctas,
+                         cudaStream_t st);
 
 }  // namespace vrc

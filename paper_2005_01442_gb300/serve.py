@@ -7,11 +7,14 @@ image size. Admission is by an HBM budget for output images (volumes, brick tabl
 occupancy stay resident); admitted requests go to
 
 * BatchedServer -- vrc_server_*: requests are appended to a device FIFO while one persistent
-  kernel runs; its warps claim 8 x 4 pixel tiles of the oldest unfinished request, so requests
-  that arrive while others render start as soon as warps free up and overlap on the device;
+  kernel runs; its warps claim 8 x 4 pixel tiles (phase 1 of the split render) and queued rays
+  (phase 2) of the oldest unfinished requests, so requests that arrive while others render
+  start as soon as warps free up and overlap on the device; each split request holds a ray
+  queue of 112 bytes per pixel while it is in flight;
 * PlainServer -- one vrc_render launch per request, in arrival order on one stream.
 
-Both render each pixel with the same per-ray code, so images are bit-identical across them.
+Both render with the split render by default (the per-ray kernel with kernel=1), so images are
+bit-identical across them. Admission counts each server's device bytes per pixel in flight.
 run_open_loop() replays a request list against a server and reports p50/p99 latency (arrival
 to completion observed by the host) and images/s. Only scheduling and bookkeeping happen in
 Python; all rendering runs in the library's kernels.
@@ -62,20 +65,22 @@ def poisson_requests(seed: int, rate: float, duration: float, vol_ids, tf_ids, s
 
 
 class ImageBudget:
-    """Admission by HBM budget: a request is admitted when its output image fits in what the
-    in-flight images leave of the budget (first come, first served). Buffers are pooled by
-    size and reused."""
+    """Admission by HBM budget: a request is admitted when its device memory -- the output
+    image (16 bytes per pixel) plus whatever the server holds per pixel while it renders --
+    fits in what the in-flight requests leave of the budget (first come, first served). Image
+    buffers are pooled by size and reused."""
 
-    def __init__(self, budget_bytes: int, alloc):
+    def __init__(self, budget_bytes: int, alloc, extra_bytes_per_pixel: int = 0):
         self.budget = int(budget_bytes)
         self.used = 0
         self.alloc = alloc  # (height, width) -> buffer
+        self.per_pixel = 16 + int(extra_bytes_per_pixel)
         self.free = collections.defaultdict(list)
 
     def try_acquire(self, h: int, w: int):
-        need = h * w * 16
+        need = h * w * self.per_pixel
         if need > self.budget:
-            raise ValueError(f"a {w}x{h} image ({need} bytes) exceeds the whole budget")
+            raise ValueError(f"a {w}x{h} request ({need} bytes) exceeds the whole budget")
         if self.used + need > self.budget:
             return None
         self.used += need
@@ -83,7 +88,7 @@ class ImageBudget:
         return pool.pop() if pool else self.alloc(h, w)
 
     def release(self, h: int, w: int, buf):
-        self.used -= h * w * 16
+        self.used -= h * w * self.per_pixel
         self.free[(h, w)].append(buf)
 
 
@@ -93,9 +98,12 @@ class BatchedServer:
     name = "batched"
 
     def __init__(self, renderer, max_slots: int = 1024, budget_ms: float = 250.0,
-                 idle_ms: float = 5.0):
+                 idle_ms: float = 5.0, kernel: int = 0):
         self.R = renderer
         self.lib = renderer.lib
+        self.kernel = int(kernel)
+        # device bytes a request holds per pixel besides its image: its ray queue
+        self.extra_bytes_per_pixel = 0 if self.kernel == 1 else 112
         ptr = C.c_void_p()
         native.check(renderer.ctx, self.lib.vrc_server_create(renderer.ctx, int(max_slots),
                                                               C.byref(ptr)))
@@ -106,7 +114,7 @@ class BatchedServer:
     def submit(self, req: Request, out):
         t = C.c_longlong()
         cs = native.camera_struct(req.cam)
-        ps = native.params_struct(req.step, req.ert, req.brick, 64, 0)
+        ps = native.params_struct(req.step, req.ert, req.brick, 64, self.kernel)
         native.check(self.R.ctx, self.lib.vrc_server_submit(
             self.srv, int(req.vol_id), int(req.tf_id), C.byref(cs), C.byref(ps),
             C.c_void_p(out.data_ptr()), C.byref(t)))
@@ -134,16 +142,18 @@ class PlainServer:
     """One vrc_render launch per request, FIFO on one stream; completion by CUDA event."""
 
     name = "plain"
+    extra_bytes_per_pixel = 0  # the context's one split queue per stream is not per request
 
-    def __init__(self, renderer):
+    def __init__(self, renderer, kernel: int = 0):
         import torch
         self.torch = torch
         self.R = renderer
+        self.kernel = int(kernel)
         self.stream = torch.cuda.Stream()
 
     def submit(self, req: Request, out):
         self.R.render(req.vol_id, req.tf_id, req.cam, step=req.step, ert=req.ert,
-                      brick=req.brick, out=out, stream=self.stream)
+                      brick=req.brick, out=out, stream=self.stream, kernel=self.kernel)
         ev = self.torch.cuda.Event()
         ev.record(self.stream)
         return ev

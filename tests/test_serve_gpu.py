@@ -1,7 +1,8 @@
 """Persistent batched serving on the GPU: every request's image in a mixed batch equals its
-image rendered alone by vrc_render (bit for bit: rays never interact and run the same code),
-requests overlap, the kernel leaves by itself when idle, and the open-loop driver works
-against both servers."""
+image rendered alone by vrc_render with the same kernel (bit for bit: rays never interact and
+run the same code) and the FP64 oracle's within the image tolerance, requests overlap, slots
+are reused safely back to back, the kernel leaves by itself when idle, and the open-loop driver
+works against both servers."""
 import numpy as np
 import pytest
 
@@ -53,10 +54,11 @@ def _requests(vids, tids, dims, n, seed):
     return out
 
 
-def test_batched_images_equal_alone(env):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_batched_images_equal_alone(env, kernel):
     torch, R, vids, tids, dims = env
     from paper_2005_01442_gb300 import serve
-    srv = serve.BatchedServer(R, max_slots=64, budget_ms=200.0, idle_ms=5.0)
+    srv = serve.BatchedServer(R, max_slots=64, budget_ms=200.0, idle_ms=5.0, kernel=kernel)
     reqs = _requests(vids, tids, dims, 48, 1)
     outs, handles = [], []
     for r in reqs:  # all submitted back to back: they share the persistent launch
@@ -73,8 +75,32 @@ def test_batched_images_equal_alone(env):
     torch.cuda.synchronize()
     for r, o in zip(reqs, outs):
         alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick,
-                         kernel=1)
+                         kernel=6 if kernel == 0 else 1)
         assert torch.equal(o, alone)
+    srv.close()
+
+
+def test_slots_reused_back_to_back(env):
+    """One slot, many requests submitted back to back into the running kernel: every slot
+    reuse must leave the next request complete (no claim may land on a reused slot) and its
+    image equal to the render alone."""
+    torch, R, vids, tids, dims = env
+    from paper_2005_01442_gb300 import serve
+    import time
+    srv = serve.BatchedServer(R, max_slots=1, budget_ms=2000.0, idle_ms=50.0)
+    reqs = _requests(vids, tids, dims, 40, 5)
+    t0 = time.time()
+    for r in reqs:
+        o = torch.full((r.cam.height, r.cam.width, 4), float("nan"), device="cuda")
+        h = srv.submit(r, o)
+        t1 = time.time()
+        while not srv.done(h):
+            srv.pump()
+            assert time.time() - t1 < 10.0, "a request did not complete"
+        alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick,
+                         kernel=6)
+        assert torch.equal(o, alone)
+    assert time.time() - t0 < 120.0
     srv.close()
 
 
@@ -139,7 +165,7 @@ def test_kernel_leaves_when_idle_and_relaunches(env):
         torch.cuda.synchronize()
         assert srv.pump() is False
         alone = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick,
-                         kernel=1)
+                         kernel=6)
         assert torch.equal(o, alone)
     srv.close()
 
@@ -154,7 +180,8 @@ def test_open_loop_run(env, kind):
     for r, a in zip(reqs, t):
         r.arrival = float(a)
     srv = serve.BatchedServer(R, max_slots=32) if kind == "batched" else serve.PlainServer(R)
-    budget = serve.ImageBudget(1 << 20, lambda h, w: torch.empty((h, w, 4), device="cuda"))
+    budget = serve.ImageBudget(8 << 20, lambda h, w: torch.empty((h, w, 4), device="cuda"),
+                               srv.extra_bytes_per_pixel)
     res = serve.run_open_loop(srv, reqs, budget, warmup=0.02)
     srv.close()
     assert res["requests"] > 0 and len(res["latencies_s"]) == res["requests"]
