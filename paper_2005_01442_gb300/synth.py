@@ -61,7 +61,9 @@ def _paint_ellipsoid(vol, center, semi, rot, value, mode):
 
 
 def _paint_capsule(vol, p0, p1, radius, value):
-    """Set `value` at voxel centres within `radius` of the segment p0-p1."""
+    """Set `value` at voxel centres within `radius` of the segment p0-p1. Works through the
+    bounding box 16 z-planes at a time, each restricted to the part of the box that the
+    segment's points within reach of those planes can touch (same per-voxel test)."""
     nz, ny, nx = vol.shape
     p0 = np.asarray(p0, np.float64)
     p1 = np.asarray(p1, np.float64)
@@ -69,13 +71,34 @@ def _paint_capsule(vol, p0, p1, radius, value):
     hi = np.minimum(np.ceil(np.maximum(p0, p1) + radius) + 2, [nx, ny, nz]).astype(int)
     if np.any(hi <= lo):
         return
-    z, y, x = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]),
-                          np.arange(lo[0], hi[0]), indexing="ij")
-    pts = np.stack([x, y, z], axis=-1).astype(np.float64)
     seg = p1 - p0
-    t = np.clip(((pts - p0) @ seg) / max(seg @ seg, 1e-12), 0.0, 1.0)
-    dist2 = ((pts - (p0 + t[..., None] * seg)) ** 2).sum(-1)
-    vol[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]][dist2 <= radius * radius] = value
+    for za in range(lo[2], hi[2], 16):
+        zb = min(int(hi[2]), za + 16)
+        # a voxel in planes za .. zb-1 within radius of the segment has its closest segment
+        # point at z in [za - radius, zb - 1 + radius]
+        if abs(seg[2]) > 1e-12:
+            ta = (za - radius - 1.0 - p0[2]) / seg[2]
+            tb = (zb + radius + 1.0 - p0[2]) / seg[2]
+            ta, tb = max(min(ta, tb), 0.0), min(max(ta, tb), 1.0)
+            if ta > tb:
+                continue
+        else:
+            if p0[2] < za - radius - 1.0 or p0[2] > zb + radius + 1.0:
+                continue
+            ta, tb = 0.0, 1.0
+        q0, q1 = p0 + ta * seg, p0 + tb * seg
+        xlo = max(int(math.floor(min(q0[0], q1[0]) - radius)) - 1, int(lo[0]))
+        xhi = min(int(math.ceil(max(q0[0], q1[0]) + radius)) + 2, int(hi[0]))
+        ylo = max(int(math.floor(min(q0[1], q1[1]) - radius)) - 1, int(lo[1]))
+        yhi = min(int(math.ceil(max(q0[1], q1[1]) + radius)) + 2, int(hi[1]))
+        if xhi <= xlo or yhi <= ylo:
+            continue
+        z, y, x = np.meshgrid(np.arange(za, zb), np.arange(ylo, yhi), np.arange(xlo, xhi),
+                              indexing="ij")
+        pts = np.stack([x, y, z], axis=-1).astype(np.float64)
+        t = np.clip(((pts - p0) @ seg) / max(seg @ seg, 1e-12), 0.0, 1.0)
+        dist2 = ((pts - (p0 + t[..., None] * seg)) ** 2).sum(-1)
+        vol[za:zb, ylo:yhi, xlo:xhi][dist2 <= radius * radius] = value
 
 
 def phantom(n: int = 64, seed: int = 1, n_ellipsoids: int = 10) -> np.ndarray:
@@ -100,7 +123,9 @@ def phantom(n: int = 64, seed: int = 1, n_ellipsoids: int = 10) -> np.ndarray:
 
 
 def _smooth_field(rng, shape, lo, hi, cell=64):
-    """Trilinear upsampling of a coarse uniform random grid: a smooth field in [lo, hi]."""
+    """Trilinear upsampling of a coarse uniform random grid: a smooth field in [lo, hi].
+    Returns a function of (z0, z1) giving planes z0 .. z1-1 (x and y are interpolated once on
+    the coarse planes, z per request: the same sums as interpolating the whole volume)."""
     nz, ny, nx = shape
     coarse = rng.uniform(lo, hi, (nz // cell + 2, ny // cell + 2, nx // cell + 2))
 
@@ -110,7 +135,7 @@ def _smooth_field(rng, shape, lo, hi, cell=64):
         return i0, t - i0
 
     out = coarse
-    for axis, n in ((2, nx), (1, ny), (0, nz)):
+    for axis, n in ((2, nx), (1, ny)):
         i0, w = axis_weights(n)
         a = np.take(out, i0, axis=axis)
         b = np.take(out, i0 + 1, axis=axis)
@@ -118,7 +143,14 @@ def _smooth_field(rng, shape, lo, hi, cell=64):
         shp[axis] = n
         w = w.reshape(shp)
         out = a * (1.0 - w) + b * w
-    return out
+    iz, wz = axis_weights(nz)
+
+    def planes(z0, z1):
+        w = wz[z0:z1].reshape(-1, 1, 1)
+        a = np.take(out, iz[z0:z1], axis=0)
+        b = np.take(out, iz[z0:z1] + 1, axis=0)
+        return a * (1.0 - w) + b * w
+    return planes
 
 
 def ct_volume(shape=(400, 512, 512), seed: int = 3, n_bones: int = 30,
@@ -148,10 +180,9 @@ def ct_volume(shape=(400, 512, 512), seed: int = 3, n_bones: int = 30,
     for z0 in range(0, nz, slab):
         z1 = min(nz, z0 + slab)
         noise = rng.standard_normal((z1 - z0, ny, nx)) * 10.0
-        vals = np.rint(tissue[z0:z1] + noise).astype(np.int16)
+        vals = np.rint(tissue(z0, z1) + noise).astype(np.int16)
         sl = vol[z0:z1]
         sl[:, body] = vals[:, body]
-    del tissue
 
     def point_in_body():
         while True:
