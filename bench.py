@@ -458,18 +458,22 @@ def main():
     kernel_ms = statistics.mean(frame_ms)
     kname = ("one render call: split_head_kernel + split_tail_kernel" if args.kernel in (0, 6)
              else f"render kernel {args.kernel}")
-    dense = None
+    # the other workload (the dense transfer function) and the other kernel (TMA-staged), A/B
+    legs = []
     if not args.no_dense:
-        dense = dense_tf_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, world,
-                             dev)
+        other_tf = "dense" if args.tf == "ct" else "ct"
+        other_k = 7 if args.kernel in (0, 6) else 0
+        for tfk, k in ((args.tf, other_k), (other_tf, args.kernel), (other_tf, other_k)):
+            legs.append(frames_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler,
+                                   world, dev, tfk, k))
     line = None
     if rank == 0:
         peaks = measure_peaks(R, sms)  # after the timed regions
         roof = roofline(executed // args.cameras, resampled // args.cameras, kernel_ms, peaks,
                         kname)
-        if dense is not None:
-            dense["roofline"] = roofline(dense.pop("_executed"), dense.pop("_resampled"),
-                                         dense["ms_per_frame"], peaks, kname)
+        for leg in legs:
+            leg["roofline"] = roofline(leg.pop("_executed"), leg.pop("_resampled"),
+                                       leg["ms_per_frame"], peaks, leg["kernel_name"])
         sgemm = fp32_sgemm_tflops(torch, dev)
         cpu = None
         if not args.no_cpu_baseline:
@@ -499,7 +503,7 @@ def main():
             "render_kernel_ms": kernel_ms,
             "roofline": roof,
             "fp32_sgemm_tflops_measured": sgemm,
-            "dense_tf": dense,
+            "other_workloads_and_kernels": legs,
             "cpu_baseline": cpu, "e2e": e2e,
             # bricks, occupancy, 3 summed-volume passes, distance, cell mask; per frame the
             # split render's two kernels (one for the per-ray kernel)
@@ -526,24 +530,25 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def dense_tf_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, world, dev):
-    """The same volume and cameras with a transfer function that makes soft tissue
-    semi-transparent: frame time of the render call (CUDA events, L2 flushed before each group
-    of frames) and its sample counts, with its own clock record."""
+def frames_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, world, dev,
+               tf_kind: str, kernel: int):
+    """The headline volume and cameras with transfer function `tf_kind` ("ct" or "dense": soft
+    tissue semi-transparent) rendered by `kernel`: frame time of the render call (CUDA events,
+    L2 flushed before each group of frames), its sample counts and its own clock record."""
     B = args.brick
-    tid = R.set_tf(synth.tf_ct_dense(), synth.CT_LO, synth.CT_HI)
+    tf = synth.tf_ct() if tf_kind == "ct" else synth.tf_ct_dense()
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
     R.build_occupancy(vid, tid, B)
     cnt = torch.zeros((len(cams), 3), dtype=torch.int64, device=dev)
     for i, cam in enumerate(cams):
-        R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], counters=cnt[i],
-                 kernel=args.kernel)
+        R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], counters=cnt[i], kernel=kernel)
     torch.cuda.synchronize()
     nominal, executed, resampled = [int(x) for x in cnt.sum(0).tolist()]
     steps = max(1, min(args.steps, 5))
     for _ in range(max(args.warmup, 3)):
         flush.fill_(1.0)
         for i, cam in enumerate(cams):
-            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=args.kernel)
+            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=kernel)
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in cams] for _ in range(steps)]
     if world > 1:
@@ -555,15 +560,17 @@ def dense_tf_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, 
         flush.fill_(float(s))
         for i, cam in enumerate(cams):
             ev[s][i][0].record(stream)
-            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=args.kernel)
+            R.render(vid, tid, cam, ert=0.999, brick=B, out=out[i], kernel=kernel)
             ev[s][i][1].record(stream)
     torch.cuda.synchronize()
     sampler.mark(False)
     ms = statistics.mean(a.elapsed_time(b) for fr in ev for a, b in fr)
     R.free_tf(tid)
     nf = len(cams)
-    return {"transfer_function": "soft tissue semi-transparent (about 0.01-0.02 opacity per "
-                                 "voxel), vessels and bone more opaque",
+    return {"transfer_function": ("CT (transparent below 150 HU; vessels, bone)" if tf_kind == "ct"
+                                  else "dense: soft tissue semi-transparent (about 0.01-0.02 "
+                                       "opacity per voxel), vessels and bone more opaque"),
+            "kernel": kernel, "kernel_name": KERNEL_NAMES.get(kernel, str(kernel)),
             "ms_per_frame": ms, "frames_timed": steps * nf,
             "gsamples_per_s": executed / nf / (ms / 1e3) / 1e9,
             "gsamples_resampled_per_s": resampled / nf / (ms / 1e3) / 1e9,
@@ -572,6 +579,12 @@ def dense_tf_leg(args, torch, R, synth, vid, cams, out, flush, stream, sampler, 
                                   "resampled": resampled // nf},
             "clocks": sampler.summary(),
             "_executed": executed // nf, "_resampled": resampled // nf}
+
+
+KERNEL_NAMES = {0: "split render (split_head_kernel + split_tail_kernel)",
+                6: "split render (split_head_kernel + split_tail_kernel)",
+                1: "one ray per thread (render_ray_kernel)",
+                7: "TMA-staged boxes in shared memory (render_tma_kernel)"}
 
 
 def _gauss_blur(a, sigma=1.5, radius=5):
