@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 
 FLOPS_PER_SAMPLE = 230        # algorithmic FP32 flops per sample (FMA = 2)
 GATHER_BYTES_PER_SAMPLE = 128  # 64 int16 taps: the least a sample reads from on-chip memory
+ADJ_FLOPS_PER_SAMPLE = 400     # reverse mode: forward recompute 230 + backward chain about 170
+ADJ_ATOMIC_BYTES_PER_SAMPLE = 256  # 64 voxel-gradient float atomics per resampled sample
 FP32_LANES = 128
 L1_BYTES_PER_CLK = 128
 SM_MAX_MHZ = 2070.0
@@ -268,7 +270,7 @@ SERVE_HBM_BUDGET = 8 << 30  # device bytes of the requests in flight (images + r
 SERVE_P99_CAP_MS = 33.0     # latency cap of the rate sweep: one frame at 30 frames/s
 
 
-def serve_bench(R, torch, vols, tids, runs, warmup, brick, seed, p99_cap_ms=SERVE_P99_CAP_MS):
+def serve_bench(R, torch, vols, tids, runs, brick, seed, p99_cap_ms=SERVE_P99_CAP_MS):
     """Open-loop Poisson load (seeded) of mixed volumes, transfer functions, orbit cameras and
     image sizes, replayed against the one-launch-per-request server and the persistent
     batched server for each (offered rate, seconds, warm-up seconds) run; admission by an HBM
@@ -693,7 +695,7 @@ def run_mode(args, torch, R, synth):
         for c, im in zip(cams, imgs):
             R.render(vid, tid, c, brick=args.brick, out=im, counters=cnt)
         torch.cuda.synchronize()
-        executed = int(cnt[1])
+        executed, resampled = int(cnt[1]), int(cnt[2])
 
         # the forward records each camera's checkpoints; the adjoint reads them
         cks = [R.ckpt_buffer(vid, c, 0.5, 64) for c in cams]
@@ -713,6 +715,24 @@ def run_mode(args, torch, R, synth):
         f_ms = _timed(torch, fwd, args.steps)
         b_ms = _timed(torch, bwd, args.steps)
         loss = float(sum(((im - t) ** 2).sum() for im, t in zip(imgs, targets)))
+        # roofline of the adjoint launches: every resampled sample is recomputed from its
+        # segment checkpoint (230 flop) and walked back (about 170 flop: classification and
+        # opacity chain, 64 tap weights times the value gradient), and adds 64 float gradients
+        # (256 bytes of vector atomics) into the voxel gradients
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fma = min(R.microbench(0), sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6)
+        red = R.microbench(3)
+        t_b = b_ms / 1e3
+        alu = ADJ_FLOPS_PER_SAMPLE * resampled / t_b
+        atom = ADJ_ATOMIC_BYTES_PER_SAMPLE * resampled / t_b
+        adj_roof = {"bound": "atomics" if atom / red >= alu / fma else "alu",
+                    "alu_frac": alu / fma, "atomic_frac": atom / red,
+                    "frac": max(alu / fma, atom / red),
+                    "achieved_tflops": alu / 1e12, "achieved_atomic_gbs": atom / 1e9,
+                    "peak_fp32_tflops": fma / 1e12, "peak_atomic_gbs_measured": red / 1e9,
+                    "basis": f"{ADJ_FLOPS_PER_SAMPLE} flop and {ADJ_ATOMIC_BYTES_PER_SAMPLE} B of "
+                             "float atomics per resampled sample over the adjoint launches' time; "
+                             "atomic peak = vrc_microbench kind 3 (of measured)"}
         print(json.dumps({
             "mode": "adjoint", "metric": "forward+adjoint Gsamples/s", "data": "synthetic",
             "config": {"volume": [256, 256, 256], "volume_dtype": "float32",
@@ -721,7 +741,8 @@ def run_mode(args, torch, R, synth):
             "forward_ms_per_step": f_ms, "backward_ms_per_step": b_ms,
             "forward": "split render recording checkpoints (seg_len 64)",
             "checkpoint_bytes_per_camera": int(cks[0].numel()),
-            "executed_samples_per_step": executed, "loss": loss,
+            "executed_samples_per_step": executed, "resampled_samples_per_step": resampled,
+            "loss": loss, "adjoint_roofline": adj_roof,
             "value": executed / ((f_ms + b_ms) / 1e3) / 1e9, "unit": "Gsamples/s",
             "gpu_launches": 8 * args.steps * 3, "clocks": _clocks()}), flush=True)
         return

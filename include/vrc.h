@@ -428,9 +428,10 @@ vrc_status vrc_render_ordered(vrc_ctx *ctx, int plan_id, const vrc_camera *cam,
  * counterpart; used to state the render's roofline against this device's own rates):
  * kind 0 = FP32 fused multiply-add rate of the CUDA cores (flop/s, FMA = 2 flop), 1 = rate of
  * 16-byte global loads that hit in L1 (bytes/s), 2 = rate of 16-byte shared-memory loads
- * (bytes/s). Every SM runs 64 warps; the best of five timed launches after one warm-up is
- * returned in *rate_out. Synchronises `stream`; allocates a small context-owned buffer on
- * first use. */
+ * (bytes/s), 3 = rate of 16-byte vector float atomic adds to scattered addresses of a 64 MB
+ * buffer (payload bytes/s; the reverse mode's gradient sums). Every SM runs 64 warps; the
+ * best of five timed launches after one warm-up is returned in *rate_out. Synchronises
+ * `stream`; allocates context-owned buffers on first use (64 MB for kind 3). */
 vrc_status vrc_microbench(vrc_ctx *ctx, int kind, double *rate_out, void *stream);
 
 /* Reads and clears the device error word shared by the context's kernels: 0 when no kernel

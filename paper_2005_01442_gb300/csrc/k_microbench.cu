@@ -1,7 +1,9 @@
-// Microbenchmarks that measure the two roofs of the resampling stencil on the device at hand:
-// the FP32 fused multiply-add rate of the CUDA cores, and the rate at which warps read 16-byte
-// vectors that hit in L1 (global loads) or in shared memory. The render's roofline takes the
-// lower of each measured rate and its unit-count figure. Nothing here is part of the method.
+// Microbenchmarks that measure the roofs of the resampling stencil on the device at hand: the
+// FP32 fused multiply-add rate of the CUDA cores, the rate at which warps read 16-byte vectors
+// that hit in L1 (global loads) or in shared memory, and (for the reverse mode's scattered
+// gradient sums) the rate of 16-byte vector float atomics to global memory. The rooflines
+// take the lower of each measured rate and its unit-count figure. Nothing here is part of the
+// method.
 #include "vrc_internal.h"
 
 namespace vrc {
@@ -76,22 +78,39 @@ __global__ void __launch_bounds__(MB_THREADS) lds_kernel(int iters, float *sink)
     if (s == -1.2345e30f) sink[blockIdx.x] = s;
 }
 
+// Every thread adds float4 (1, 1, 1, 1) with vector float atomics at `iters` addresses spread
+// over n_f4 16-byte entries (a 64 MB buffer, much like a voxel-gradient volume).
+__global__ void __launch_bounds__(MB_THREADS) red_kernel(float4 *__restrict__ buf, int iters,
+                                                         unsigned n_f4) {
+    unsigned h = (blockIdx.x * MB_THREADS + threadIdx.x) * 2654435761u;
+    for (int i = 0; i < iters; ++i) {
+        h = h * 1664525u + 1013904223u;  // linear congruential step
+        atomicAdd(buf + (h >> 8) % n_f4, make_float4(1.0f, 1.0f, 1.0f, 1.0f));
+    }
+}
+
 }  // namespace
 
 size_t microbench_scratch_bytes() { return 1024 * sizeof(float4) + 65536 * sizeof(float); }
+size_t microbench_red_bytes() { return (size_t)64 << 20; }
 
-cudaError_t launch_microbench(int kind, int ctas, int iters, void *scratch, cudaStream_t st) {
+cudaError_t launch_microbench(int kind, int ctas, int iters, void *scratch, void *red_buf,
+                              cudaStream_t st) {
     float4 *buf = (float4 *)scratch;
     float *sink = (float *)((char *)scratch + 1024 * sizeof(float4));
     if (kind == MB_FMA) fma_kernel<<<ctas, MB_THREADS, 0, st>>>(iters, 0.999f, 1e-4f, sink);
     else if (kind == MB_L1) l1_kernel<<<ctas, MB_THREADS, 0, st>>>(buf, iters, sink);
-    else lds_kernel<<<ctas, MB_THREADS, 0, st>>>(iters, sink);
+    else if (kind == MB_LDS) lds_kernel<<<ctas, MB_THREADS, 0, st>>>(iters, sink);
+    else
+        red_kernel<<<ctas, MB_THREADS, 0, st>>>((float4 *)red_buf, iters,
+                                                 (unsigned)(microbench_red_bytes() / sizeof(float4)));
     return cudaGetLastError();
 }
 
 double microbench_work(int kind, int ctas, int iters) {
     const double threads = (double)ctas * MB_THREADS;
     if (kind == MB_FMA) return threads * iters * 16.0 * FMA_CHAINS * 2.0;  // flops
+    if (kind == MB_RED) return threads * iters * 16.0;                     // atomic payload
     return threads * iters * 8.0 * 16.0;                                   // bytes
 }
 

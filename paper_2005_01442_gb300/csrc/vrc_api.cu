@@ -123,6 +123,7 @@ struct vrc_ctx {
     cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
     unsigned tf_version_counter = 0;
     void *mb_scratch = nullptr;  // vrc_microbench buffers
+    void *mb_red = nullptr;
     unsigned char *ckpt_buf = nullptr;  // checkpoints of vrc_render_backward without ckpt_dev
     size_t ckpt_bytes = 0;
 };
@@ -752,6 +753,7 @@ vrc_status vrc_destroy(vrc_ctx *ctx) {
     }
     if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
     cudaFree(ctx->mb_scratch);
+    cudaFree(ctx->mb_red);
     cudaFree(ctx->ckpt_buf);
     delete ctx;
     return VRC_OK;
@@ -1206,25 +1208,30 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
 vrc_status vrc_microbench(vrc_ctx *ctx, int kind, double *rate_out, void *stream) {
     if (!ctx) return VRC_ERR_ARG;
     if (!rate_out) return fail(ctx, VRC_ERR_ARG, "rate_out is NULL");
-    if (kind < MB_FMA || kind > MB_LDS) return fail(ctx, VRC_ERR_ARG, "kind must be 0, 1 or 2");
+    if (kind < MB_FMA || kind > MB_RED) return fail(ctx, VRC_ERR_ARG, "kind must be 0..3");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (!ctx->mb_scratch) {
         CK(cudaMalloc(&ctx->mb_scratch, microbench_scratch_bytes()), "cudaMalloc(microbench)");
         CK(cudaMemsetAsync(ctx->mb_scratch, 0, microbench_scratch_bytes(), st), "memset");
     }
+    if (kind == MB_RED && !ctx->mb_red) {
+        CK(cudaMalloc(&ctx->mb_red, microbench_red_bytes()), "cudaMalloc(microbench)");
+        CK(cudaMemsetAsync(ctx->mb_red, 0, microbench_red_bytes(), st), "memset");
+    }
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attribute");
     // 8 CTAs of 256 threads per SM (64 warps: the most an SM holds)
     const int ctas = std::min(sms * 8, 65536);
-    const int iters = kind == MB_FMA ? 4096 : 2048;
+    const int iters = kind == MB_FMA ? 4096 : kind == MB_RED ? 64 : 2048;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
     cudaError_t e = cudaEventCreate(&e1);
     float best = 1e30f;
     for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {  // one warm-up, best of five
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess) e = launch_microbench(kind, ctas, iters, ctx->mb_scratch, st);
+        if (e == cudaSuccess)
+            e = launch_microbench(kind, ctas, iters, ctx->mb_scratch, ctx->mb_red, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;

@@ -540,11 +540,13 @@ struct AdjointLaunch {
 };
 cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st);
 
-// Microbenchmarks of the stencil's two roofs (k_microbench.cu): FP32 fused multiply-adds,
-// 16-byte loads that hit in L1, 16-byte loads from shared memory.
-enum { MB_FMA = 0, MB_L1 = 1, MB_LDS = 2 };
+// Microbenchmarks of the stencil's roofs (k_microbench.cu): FP32 fused multiply-adds, 16-byte
+// loads that hit in L1, 16-byte loads from shared memory, 16-byte float atomics to global.
+enum { MB_FMA = 0, MB_L1 = 1, MB_LDS = 2, MB_RED = 3 };
 size_t microbench_scratch_bytes();
-cudaError_t launch_microbench(int kind, int ctas, int iters, void *scratch, cudaStream_t st);
+size_t microbench_red_bytes();
+cudaError_t launch_microbench(int kind, int ctas, int iters, void *scratch, void *red_buf,
+                              cudaStream_t st);
 double microbench_work(int kind, int ctas, int iters);  // flops (MB_FMA) or bytes per launch
 
 // Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
