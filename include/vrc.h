@@ -115,7 +115,12 @@ typedef struct {
  *                  vrc_render_host only. The context builds the table (1 MB per transfer
  *                  function) on first use and again when the step changes; renders with
  *                  different steps and one transfer function must not overlap on
- *                  different streams. */
+ *                  different streams.
+ *   grad_open_alpha vrc_render_backward only: 0 = the opacity clamp has zero derivative at a
+ *                  table opacity of 0 (a transparent entry never receives a gradient, and
+ *                  samples skipped by leaping carry none); 1 = take the derivative there from
+ *                  above (delta), so an optimisation can open a fully transparent entry; needs
+ *                  brick = 0 (VRC_ERR_ARG otherwise), since every sample then carries gradient. */
 typedef struct {
     float step;
     float ert_threshold;
@@ -127,6 +132,7 @@ typedef struct {
     int shade;
     float ka, kd, ks, shininess;
     int preint;
+    int grad_open_alpha;
 } vrc_params;
 
 /* Creates a context bound to CUDA device `device`. */

@@ -34,7 +34,7 @@ class Params(C.Structure):
     _fields_ = [("step", C.c_double), ("ert", C.c_double), ("brick", C.c_int),
                 ("interp", C.c_int), ("preclass", C.c_int), ("shade", C.c_int),
                 ("preint", C.c_int), ("ka", C.c_double), ("kd", C.c_double), ("ks", C.c_double),
-                ("shininess", C.c_double)]
+                ("shininess", C.c_double), ("open_alpha", C.c_int)]
 
 
 class Ball(C.Structure):
@@ -288,9 +288,11 @@ def render(vol, tf, lo, hi, cam, step, ert=1.0, brick=0, pixels=None, ball=None,
     return res[0] if len(res) == 1 else tuple(res)
 
 
-def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, want_vol=True):
+def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, want_vol=True,
+                open_alpha=False):
     """Reverse-mode gradient of sum(g * image) w.r.t. the TF (256, 4) and the voxels
-    (vol.shape), in float64."""
+    (vol.shape), in float64. open_alpha: at table opacity 0 take the opacity correction's
+    derivative from above instead of from the clamped side (brick must be 0)."""
     vol = np.ascontiguousarray(vol)
     tf = np.ascontiguousarray(tf, np.float32)
     nz, ny, nx = vol.shape
@@ -302,7 +304,8 @@ def render_grad(vol, tf, lo, hi, cam, step, g, ert=1.0, brick=0, pixels=None, wa
     g = np.ascontiguousarray(np.asarray(g, np.float64).reshape(-1, 4))
     gtf = np.zeros((256, 4), np.float64)
     gvol = np.zeros(vol.shape, np.float64) if want_vol else None
-    par = Params(float(step), float(ert), int(brick), 0, 0, 0, 0, 0.0, 0.0, 0.0, 1.0)
+    par = Params(float(step), float(ert), int(brick), 0, 0, 0, 0, 0.0, 0.0, 0.0, 1.0,
+                 int(bool(open_alpha)))
     rc = lib().orc_render_grad(_ptr(vol), DTYPES[vol.dtype], nx, ny, nz, _ptr(tf), float(lo),
                                float(hi), C.byref(_cam(cam)), C.byref(par), _ptr(occ),
                                _ptr(pix), npix, _ptr(g), _ptr(gtf), _ptr(gvol))

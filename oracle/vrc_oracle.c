@@ -122,6 +122,7 @@ typedef struct {
     int shade;       /* 1: Phong shading with a headlight (cubic post-classification only) */
     int preint;      /* 1: pre-integrated classification (cubic post, no skipping) */
     double ka, kd, ks, shininess; /* Phong coefficients */
+    int open_alpha;  /* reverse mode: at opacity 0 take the derivative from above (brick 0) */
 } orc_params;
 
 #define PREINT_K 32 /* sub-steps of the pre-integration rule */
@@ -900,6 +901,8 @@ int orc_render_grad(const void *data, int dtype, int nx, int ny, int nz, const f
     if (par->brick > 0 && !occ) return ORC_EARG;
     if (par->interp != 0 || par->preclass != 0 || par->shade != 0)
         return ORC_EARG; /* cubic post-classification without shading only */
+    if (par->open_alpha && par->brick > 0)
+        return ORC_EARG; /* skipped samples would carry gradient: no leaping */
     orc_volume v = {data, dtype, {nx, ny, nz}};
     scene_t S;
     scene_init(&S, &v, NULL, tf, lo, hi, par, occ);
@@ -983,8 +986,11 @@ int orc_render_grad(const void *data, int dtype, int nx, int ny, int nz, const f
                 double raw = r->c.rgba[3];
                 /* The clamp of the opacity to [0, 1-2^-24] has kinks at both ends; there the
                  * derivative is the one-sided value on the clamped side (0). At a = 0 this makes
-                 * a sample in an empty brick contribute nothing, with or without leaping. */
-                double da = (raw > 0.0 && raw <= ALPHA_MAX)
+                 * a sample in an empty brick contribute nothing, with or without leaping. With
+                 * open_alpha the derivative at a = 0 is the one from above, delta (1-0)^(delta-1)
+                 * = delta, so that a fully transparent table entry receives a gradient. */
+                const int up = raw > 0.0 || (S.par->open_alpha && raw == 0.0);
+                double da = (up && raw <= ALPHA_MAX)
                                 ? r->delta * pow(1.0 - a, r->delta - 1.0) : 0.0;
                 drgba[3] = dalpha * da;
                 for (int c = 0; c < 4; ++c) {

@@ -168,8 +168,10 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
             const float d_r = ta * g.x, d_g = ta * g.y, d_b = ta * g.z;
             const float dalpha =
                 Tj * (g.x * (r - S0) + g.y * (gg - S1) + g.z * (b - S2) + g.w * U);
-            // opacity correction (zero derivative at the clamp ends)
-            const float da = (araw > 0.0f && araw <= ALPHA_MAX)
+            // opacity correction (zero derivative at the clamp ends; from above at 0 when
+            // asked)
+            const bool up = araw > 0.0f || (A.open_alpha && araw == 0.0f);
+            const float da = (up && araw <= ALPHA_MAX)
                                  ? delta * exp2f((delta - 1.0f) * __log2f(1.0f - a))
                                  : 0.0f;
             const float d_a = dalpha * da;

@@ -1170,6 +1170,11 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
         return fail(ctx, VRC_ERR_ARG, "ckpt_dev must be 256-byte aligned");
     if (params->interp || params->preclass || params->shade || params->preint)
         return fail(ctx, VRC_ERR_ARG, "the adjoint differentiates the default variant only");
+    if (params->grad_open_alpha != 0 && params->grad_open_alpha != 1)
+        return fail(ctx, VRC_ERR_ARG, "grad_open_alpha must be 0 or 1");
+    if (params->grad_open_alpha && params->brick != 0)
+        return fail(ctx, VRC_ERR_ARG, "grad_open_alpha needs brick 0: skipped samples would "
+                                      "carry gradient");
     Volume *v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VRC_ERR_ARG, "unknown volume id %d", vol_id);
     CkptLayout ck;
@@ -1184,6 +1189,7 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
     A.grad_tf = grad_tf_dev;
     A.grad_vol = grad_vol_dev;
     A.seg = ck.seg;
+    A.open_alpha = params->grad_open_alpha;
     A.L.out = nullptr;
     A.L.counters = nullptr;
     if (ckpt_dev) {

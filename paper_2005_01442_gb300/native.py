@@ -50,7 +50,7 @@ class vrc_params(C.Structure):
                 ("seg_len", C.c_int), ("kernel", C.c_int), ("interp", C.c_int),
                 ("preclass", C.c_int), ("shade", C.c_int), ("ka", C.c_float),
                 ("kd", C.c_float), ("ks", C.c_float), ("shininess", C.c_float),
-                ("preint", C.c_int)]
+                ("preint", C.c_int), ("grad_open_alpha", C.c_int)]
 
 
 class vrc_piece(C.Structure):
@@ -158,12 +158,12 @@ def camera_struct(cam) -> vrc_camera:
 
 
 def params_struct(step=0.5, ert=1.0, brick=0, seg_len=64, kernel=0, interp=0,
-                  preclass=0, phong=None, preint=0) -> vrc_params:
+                  preclass=0, phong=None, preint=0, open_alpha=False) -> vrc_params:
     """phong: None, or (ka, kd, ks, shininess) for headlight Blinn-Phong shading."""
     ka, kd, ks, shin = phong if phong is not None else (0.0, 0.0, 0.0, 1.0)
     return vrc_params(float(step), float(ert), int(brick), int(seg_len), int(kernel),
                       int(interp), int(preclass), int(phong is not None), float(ka), float(kd),
-                      float(ks), float(shin), int(preint))
+                      float(ks), float(shin), int(preint), int(bool(open_alpha)))
 
 
 def grid_order(cam, grid, cuts) -> list:

@@ -258,13 +258,14 @@ class Renderer:
 
     def render_backward(self, vol_id: int, tf_id: int, cam, grad_out, grad_tf, grad_vol=None,
                         step: float = 0.5, ert: float = 1.0, brick: int = 0, seg_len: int = 64,
-                        stream=None, ckpt=None, kernel: int = 0):
+                        stream=None, ckpt=None, kernel: int = 0, open_alpha: bool = False):
         """Adds dL/dTF to grad_tf (256x4 CUDA float32) and dL/dvoxel to grad_vol ((nz, ny, nx)
         CUDA float32, optional) for dL/dimage = grad_out ((H, W, 4) CUDA float32). `ckpt`: the
-        checkpoints of a render with the same arguments (else the call renders its own)."""
+        checkpoints of a render with the same arguments (else the call renders its own).
+        open_alpha: derivative from above at table opacity 0 (brick must be 0)."""
         g = grad_out.contiguous()
         cs = native.camera_struct(cam)
-        ps = native.params_struct(step, ert, brick, seg_len, kernel)
+        ps = native.params_struct(step, ert, brick, seg_len, kernel, open_alpha=open_alpha)
         self._ck(self.lib.vrc_render_backward(
             self.ctx, int(vol_id), int(tf_id), C.byref(cs), C.byref(ps), C.c_void_p(g.data_ptr()),
             C.c_void_p(ckpt.data_ptr()) if ckpt is not None else None,

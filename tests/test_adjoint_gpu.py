@@ -275,6 +275,50 @@ def test_recorded_checkpoints_equal_replayed_ones(R, torch):
     R.free_tf(tid)
 
 
+@pytest.mark.parametrize("forward", ["replay", "split"])
+def test_gradient_at_zero_opacity_from_above(R, orc, torch, forward):
+    """grad_open_alpha: fully transparent table entries receive the gradient the oracle's
+    derivative from above gives (brick 0: every sample carries gradient); with the default
+    convention they receive none; with leaping the option is refused."""
+    from paper_2005_01442_gb300 import native
+    vol, _ = _scene(seed=44, shape=(28, 32, 36))
+    tf = synth.tf_ct(seed=4)
+    lo, hi = synth.CT_LO, synth.CT_HI
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, lo, hi)
+    rng = np.random.default_rng(45)
+    for cam in synth.orbit_cameras(56, 2, synth.dims_of(vol), 30, 24):
+        g = rng.normal(0, 1, (cam.height, cam.width, 4)).astype(np.float32)
+        gt = torch.tensor(g, device="cuda")
+        ck = None
+        if forward == "split":
+            ck = R.ckpt_buffer(vid, cam)
+            R.render(vid, tid, cam, brick=0, ckpt=ck)
+        gtf = torch.zeros((256, 4), device="cuda")
+        gvol = torch.zeros(vol.shape, device="cuda")
+        R.render_backward(vid, tid, cam, gt, gtf, gvol, brick=0, ckpt=ck, open_alpha=True)
+        rtf, rvol = orc.render_grad(vol, tf, lo, hi, cam, 0.5, g.astype(np.float64),
+                                    open_alpha=True)
+        zero = tf[:, 3] == 0.0
+        assert np.abs(rtf[zero, 3]).max() > 0.0
+        _rel_check_tf(gtf.cpu().numpy().astype(np.float64), rtf)
+        _rel_check_vol(gvol.cpu().numpy().astype(np.float64), rvol)
+        # entries inside a run of zero opacities: every sample that interpolates them has
+        # opacity 0, so the default convention gives them no opacity gradient at all
+        inner = zero.copy()
+        inner[1:] &= zero[:-1]
+        inner[:-1] &= zero[1:]
+        assert np.abs(rtf[inner, 3]).max() > 0.0
+        shut = torch.zeros((256, 4), device="cuda")
+        R.render_backward(vid, tid, cam, gt, shut, None, brick=0, ckpt=ck)
+        assert float(shut[torch.tensor(inner, device="cuda"), 3].abs().max()) == 0.0
+        with pytest.raises(native.VrcError):
+            R.render_backward(vid, tid, cam, gt, shut, None, brick=8, open_alpha=True)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
 def test_checkpoint_arguments_are_checked(R, torch):
     from paper_2005_01442_gb300 import native
     vol, tf = _scene(seed=40, shape=(20, 24, 28))

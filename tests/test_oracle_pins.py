@@ -652,6 +652,41 @@ def test_gradient_closed_form_constant_volume(orc):
     assert abs(gtf[100, 0] - 4 * (1 - (1 - a64) ** nz)) < 1e-10
 
 
+def test_gradient_at_zero_opacity_from_above(orc):
+    """open_alpha: at a table opacity of exactly 0 the opacity correction's derivative is taken
+    from above: for a constant medium dA/da = L (1-0)^(L-1) = L per ray, where the default
+    (clamped side) gives 0; and for a CT scene it matches a one-sided forward difference of the
+    forward render (Richardson-extrapolated, h and h/2) on entries whose opacity is 0."""
+    nz = 12
+    vol = np.full((nz, 4, 4), 100.0, np.float32)
+    tf = np.zeros((256, 4), np.float32)
+    tf[100] = (0.2, 0.4, 0.6, 0.0)
+    cam = synth.ortho_z_camera((4, 4, nz), 2, 2)
+    g = np.zeros((4, 4))
+    g[:, 3] = 1.0
+    shut, _ = orc.render_grad(vol, tf, 0.0, 255.0, cam, 0.5, g)
+    opened, _ = orc.render_grad(vol, tf, 0.0, 255.0, cam, 0.5, g, open_alpha=True)
+    assert shut[100, 3] == 0.0
+    assert abs(opened[100, 3] - 4 * nz) < 1e-10
+    with pytest.raises(ValueError):  # leaping would drop the samples that carry it
+        orc.render_grad(vol, tf, 0.0, 255.0, cam, 0.5, g, brick=8, open_alpha=True)
+    # a CT scene: entries below 150 HU are fully transparent in this table
+    vol, tf, cam, g = _fd_setup()
+    tf = synth.tf_ct(seed=4)
+    gtf, _ = orc.render_grad(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5, g, open_alpha=True)
+    zero = np.flatnonzero((tf[:, 3] == 0.0) & (np.abs(gtf[:, 3]) > 1e-3 * np.abs(gtf[:, 3]).max()))
+    assert zero.size >= 5
+    rng = np.random.default_rng(19)
+    base = _loss(orc, vol, tf, cam, g)
+    for k in rng.permutation(zero)[:5]:
+        def fwd(h):
+            t = tf.copy()
+            t[k, 3] = np.float32(h)
+            return (_loss(orc, vol, t, cam, g) - base) / float(np.float32(h))
+        fd = 2.0 * fwd(5e-5) - fwd(1e-4)
+        assert abs(fd - gtf[k, 3]) <= 2e-3 * abs(gtf[k, 3]), (k, fd, gtf[k, 3])
+
+
 def _fd_setup():
     vol = synth.ct_volume((24, 24, 24), seed=31).astype(np.float32)
     vol = vol + np.random.default_rng(3).normal(0, 30, vol.shape).astype(np.float32)
