@@ -274,21 +274,25 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
 /* ---- Batched serving. The paper's cloud server serves several clients from one application
  * (Sec. "Cloud architecture"); here render requests of any resident volume, transfer
  * function, camera and image size share one persistent launch. Requests are appended to a
- * device FIFO while the kernel runs (a copy stream publishes them); its warps claim 8 x 4
- * pixel tiles of the oldest unfinished request and render them with the same per-ray code
- * as vrc_render, so every image equals the vrc_render image of the same request bit for
- * bit. Tiles of successive requests overlap on the device. Every device wait is bounded:
- * the kernel leaves after budget_ns, after idle_ns without work, or on vrc_server_destroy;
- * vrc_server_pump relaunches it while requests are pending. */
+ * device FIFO while the kernel runs (a copy stream publishes them). Its warps take work from
+ * the oldest unfinished requests: 8 x 4 pixel tiles, whose rays are set up and leap to their
+ * first sample that may be non-zero, then the request's queued rays, finished by groups of 16
+ * lanes -- the split render of vrc_render (kernel 0 or 6) -- or, with params->kernel 1,
+ * tiles rendered to the end one ray per thread. Every image therefore equals the vrc_render
+ * image of the same request and kernel bit for bit. Work of successive requests overlaps on
+ * the device. A split request holds a ray queue of 112 bytes per pixel (from a memory pool the
+ * server owns) until it completes. Every device wait is bounded: the kernel leaves after
+ * budget_ns, after idle_ns without work, or on vrc_server_destroy; vrc_server_pump relaunches
+ * it while requests are pending. */
 typedef struct vrc_server vrc_server;
 /* Creates a server on ctx with max_slots requests in flight at most (1..65536). */
 vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **server_out);
 /* Queues one render into out_rgba_dev (caller-owned, height x width x 4 floats, 16-byte
  * aligned, untouched by the caller until completion). Returns a ticket for vrc_server_poll.
  * Brick tables for params->brick must exist; the first request of a (volume, transfer
- * function, brick size) builds its occupancy. VRC_ERR_BUSY when max_slots are in flight.
- * params->kernel 2..6 is rejected (VRC_ERR_ARG): the server renders with the per-ray body
- * (kernel 0 and 1). */
+ * function, brick size) builds its occupancy. VRC_ERR_BUSY when max_slots are in flight or the
+ * device FIFO (4 x max_slots entries) is full; VRC_ERR_OOM when no ray queue can be had.
+ * params->kernel must be 0 or 6 (split render) or 1 (per-ray body), else VRC_ERR_ARG. */
 vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id, const vrc_camera *cam,
                              const vrc_params *params, float *out_rgba_dev, long long *ticket);
 /* Launches the persistent kernel if it is not running and requests are pending; *running

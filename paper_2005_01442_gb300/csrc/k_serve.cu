@@ -19,12 +19,16 @@
 // up and their work overlaps on the device. When a request's last tile (or last queued ray)
 // is done, the finishing warp publishes its sequence number in host-mapped memory.
 //
-// Claims cannot touch a recycled slot: work is claimed only from a 64-bit word holding
-// (request sequence number << 32 | items not yet claimed) by compare-and-swap while the
-// sequence number is the one the warp's queue entry names. The host writes a new request's
-// words so that every intermediate state reads as "nothing to claim": the record copy sets
-// the tile word to (seq, 0) and the ray word to (seq, unopened) over the finished request's
-// (old seq, 0) words, and a second 8-byte copy then sets the tile word to (seq, tiles).
+// Work is claimed by subtracting from a slot's count of unclaimed items (tiles, then queued
+// rays) after a plain read has seen items left; a claim that returns a positive count took
+// items of the request the slot holds at that moment, and the warp renders them from the
+// slot's record and accounts them to the slot's own sequence number, whatever queue entry led
+// it there. So a warp holding the entry of a request that has finished and whose slot was
+// reused cannot lose the new request's work: it either finds nothing to claim or does that
+// work itself. The host opens a slot in two copies -- the record with both counts at 0
+// ("nothing to claim"), then the tile count -- so a successful claim always sees a complete
+// record, and a slot is reused only once its previous request has published completion (every
+// claimed item is done by then).
 //
 // Every wait is bounded: the launch leaves when its time budget (globaltimer) runs out, when
 // the queue stays empty longer than the idle limit, or when the host raises the stop flag.
@@ -51,7 +55,6 @@ __device__ __forceinline__ T load_volatile(const T *p) {
 constexpr int SERVE_CLAIM_MAX = 8;   // most tiles claimed at once
 constexpr int SERVE_RAYS_MAX = 16;   // most queued rays claimed at once (8 per group)
 constexpr int SERVE_SCAN = 8;        // queue entries a warp looks at from the front
-constexpr int SERVE_CAS_TRIES = 4;   // compare-and-swap attempts per claim word and look
 
 // Claims walk a request's tiles in the order k -> (k * stride) mod ntiles, stride coprime to
 // ntiles: the tiles of one claim lie far apart in the image, so costly regions (bone) spread
@@ -60,26 +63,19 @@ __device__ __forceinline__ int scattered_tile(int k, int ntiles, int stride) {
     return (int)(((long long)k * stride) % ntiles);
 }
 
-// Takes up to max_chunk items (about rem / div) from a claim word whose sequence number is
-// eseq; on success *rem is the count before the claim and *chunk the count taken.
-__device__ __forceinline__ bool claim_items(unsigned long long *word, unsigned eseq,
-                                            unsigned div, unsigned max_chunk, unsigned *rem,
-                                            unsigned *chunk) {
-    unsigned long long w = load_volatile(word);
-    for (int t = 0; t < SERVE_CAS_TRIES; ++t) {
-        if ((unsigned)(w >> 32) != eseq) return false;
-        const unsigned r = (unsigned)w;
-        if (r == 0u || r == SERVE_UNOPENED) return false;
-        const unsigned c = min(min(max(r / div, 1u), max_chunk), r);
-        const unsigned long long old = atomicCAS(word, w, w - c);
-        if (old == w) {
-            *rem = r;
-            *chunk = c;
-            return true;
-        }
-        w = old;
-    }
-    return false;
+// Takes up to max_chunk items (about the count seen / div) from a count of unclaimed items;
+// on success *first is the count before the claim (items first - *chunk .. first - 1 are
+// taken, counted from the end) and *chunk the count taken.
+__device__ __forceinline__ bool claim_items(int *count, unsigned div, int max_chunk, int *first,
+                                            int *chunk) {
+    const int r = load_volatile(count);
+    if (r <= 0) return false;  // no subtraction on an exhausted count: it stays near zero
+    const int c = min(max(r / (int)div, 1), max_chunk);
+    const int old = atomicSub(count, c);
+    if (old <= 0) return false;
+    *first = old;
+    *chunk = min(c, old);
+    return true;
 }
 
 // Phase 1 of a claim: tiles k0 .. k0 + chunk - 1 of the request (out of line, one function
@@ -145,8 +141,7 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
     while (true) {
         // lane 0 takes every control decision; the warp follows it
         int action = 0;  // 0 leave, 1 idle, 2 nothing claimable now, 3 tiles, 4 queued rays
-        int slot = 0;
-        unsigned seq = 0, rem = 0, chunk = 0;
+        int slot = 0, first = 0, chunk = 0;
         if (lane == 0) {
             const unsigned long long now = global_ns();
             if (load_volatile(&ctl->stop) || load_volatile(&ctl->leaving)) {
@@ -171,35 +166,29 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
                     for (int k = 0; k < SERVE_SCAN && f + k < t; ++k) {
                         const ServeEntry *e = &queue[(f + k) % cap];
                         const int es = __ldcg(&e->slot);
-                        const unsigned eq = (unsigned)__ldcg(&e->seq);
+                        const int eq = __ldcg(&e->seq);
                         ServeSlot *S = slots + es;
-                        const unsigned long long w1 = load_volatile(&S->p1);
-                        if ((unsigned)(w1 >> 32) != eq) {  // finished, slot already reused
+                        if (load_volatile(&S->seq) != eq) {  // finished, slot already reused
                             if (k == 0 && atomicCAS(&ctl->front, f, f + 1) == f)
                                 *(volatile unsigned long long *)front_mirror = f + 1;
                             continue;
                         }
                         // the oldest request's queued rays first, then tiles
-                        if (claim_items(&S->p2, eq, 2 * nwarps, SERVE_RAYS_MAX, &rem, &chunk)) {
+                        if (claim_items(&S->p2_rem, 2 * nwarps, SERVE_RAYS_MAX, &first, &chunk)) {
                             action = 4;
-                        } else if (claim_items(&S->p1, eq, 2 * nwarps, SERVE_CLAIM_MAX, &rem,
+                        } else if (claim_items(&S->p1_rem, 2 * nwarps, SERVE_CLAIM_MAX, &first,
                                                &chunk)) {
                             action = 3;
                         }
                         if (action != 2) {
                             slot = es;
-                            seq = eq;
                             break;
                         }
-                        if (k == 0) {
-                            // every tile claimed and every queued ray claimed (or none to
-                            // come): move the front on
-                            const unsigned long long w2 = load_volatile(&S->p2);
-                            if ((unsigned)load_volatile(&S->p1) == 0u &&
-                                (unsigned)(w2 >> 32) == eq && (unsigned)w2 == 0u &&
-                                atomicCAS(&ctl->front, f, f + 1) == f)
-                                *(volatile unsigned long long *)front_mirror = f + 1;
-                        }
+                        // every tile and every queued ray claimed: move the front on
+                        if (k == 0 && load_volatile(&S->state) >= 1 &&
+                            load_volatile(&S->p1_rem) <= 0 && load_volatile(&S->p2_rem) <= 0 &&
+                            atomicCAS(&ctl->front, f, f + 1) == f)
+                            *(volatile unsigned long long *)front_mirror = f + 1;
                     }
                 }
             }
@@ -213,66 +202,71 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
         }
         sleep_ns = 256;
         slot = __shfl_sync(0xffffffffu, slot, 0);
-        seq = __shfl_sync(0xffffffffu, seq, 0);
-        rem = __shfl_sync(0xffffffffu, rem, 0);
+        first = __shfl_sync(0xffffffffu, first, 0);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         ServeSlot *S = slots + slot;
-        // a successful claim keeps the request (and its slot record) alive until this warp's
-        // work is done
+        // the claimed items belong to the request the slot holds now, which stays there (with
+        // its record) until this warp's work is done
         __threadfence();
-        if (slot != cached_slot || seq != cached_seq) {
+        const int seq = __ldcg(&S->seq);
+        if (slot != cached_slot || (unsigned)seq != cached_seq) {
             // the request's launch record, read around L1 (the host rewrites recycled slots)
             const int *src = (const int *)&S->L;
             int *dst = (int *)&L;
             for (int i = lane; i < (int)(sizeof(RenderLaunch) / sizeof(int)); i += 32)
                 dst[i] = __ldcg(src + i);
             cached_slot = slot;
-            cached_seq = seq;
+            cached_seq = (unsigned)seq;
         }
         __syncwarp();
         const bool split = L.split.head != nullptr;
         if (action == 3) {
             // phase 1: tiles k = ntiles - rem .. ntiles - rem + chunk - 1
             const int ntiles = __ldcg(&S->ntiles), stride = __ldcg(&S->stride);
-            const int k0 = ntiles - (int)rem;
+            const int k0 = ntiles - first;
             if (split) {
-                if (L.dist) serve_tiles<true, true>(L, k0, (int)chunk, ntiles, stride);
-                else serve_tiles<false, true>(L, k0, (int)chunk, ntiles, stride);
+                if (L.dist) serve_tiles<true, true>(L, k0, chunk, ntiles, stride);
+                else serve_tiles<false, true>(L, k0, chunk, ntiles, stride);
             } else {
-                if (L.dist) serve_tiles<true, false>(L, k0, (int)chunk, ntiles, stride);
-                else serve_tiles<false, false>(L, k0, (int)chunk, ntiles, stride);
+                if (L.dist) serve_tiles<true, false>(L, k0, chunk, ntiles, stride);
+                else serve_tiles<false, false>(L, k0, chunk, ntiles, stride);
             }
             __threadfence();  // these tiles' pixels and queued rays before the count
             __syncwarp();
             if (lane == 0) {
-                const int d = atomicAdd(&S->p1_done, (int)chunk);
-                if (d + (int)chunk == ntiles) {  // this warp finished the request's phase 1
+                const int d = atomicAdd(&S->p1_done, chunk);
+                if (d + chunk == ntiles) {  // this warp finished the request's phase 1
                     __threadfence();
                     unsigned total = 0, nf = 0;
                     if (split) {
                         nf = __ldcg(&L.split.head[0]);
                         total = min(nf + __ldcg(&L.split.head[2]), L.split.cap);
                     }
-                    if (total > 0) {
+                    if (total > 0) {  // open the queued rays, then say so
                         S->p2_total = (int)total;
                         S->p2_nf = (int)nf;
                         __threadfence();
-                        atomicExch(&S->p2, ((unsigned long long)seq << 32) | total);
+                        atomicExch(&S->p2_rem, (int)total);
+                        __threadfence();
+                        atomicExch(&S->state, 1);
                     } else {
-                        atomicExch(&S->p2, (unsigned long long)seq << 32);
-                        publish_done(done_flags, slot, seq);
+                        atomicExch(&S->state, 2);
+                        publish_done(done_flags, slot, (unsigned)seq);
                     }
                 }
             }
         } else {
             // phase 2: queued rays c = total - rem .. total - rem + chunk - 1
-            const unsigned total = (unsigned)__ldcg(&S->p2_total);
-            serve_rays(L, total - rem, chunk, (unsigned)__ldcg(&S->p2_nf));
+            const int total = __ldcg(&S->p2_total);
+            serve_rays(L, (unsigned)(total - first), (unsigned)chunk, (unsigned)__ldcg(&S->p2_nf));
             __threadfence();  // these rays' pixels before the count
             __syncwarp();
             if (lane == 0) {
-                const int d = atomicAdd(&S->p2_done, (int)chunk);
-                if (d + (int)chunk == (int)total) publish_done(done_flags, slot, seq);
+                const int d = atomicAdd(&S->p2_done, chunk);
+                if (d + chunk == total) {
+                    atomicExch(&S->state, 2);
+                    publish_done(done_flags, slot, (unsigned)seq);
+                }
             }
         }
         __syncwarp();

@@ -1398,7 +1398,7 @@ struct vrc_server {
     int *h_done = nullptr, *d_done = nullptr;        // host-mapped completion flags
     unsigned long long *h_front = nullptr, *d_front = nullptr;  // host-mapped front mirror
     ServeSlot *h_slot_stage = nullptr;               // pinned staging, one record per slot
-    unsigned long long *h_claim_stage = nullptr;     // pinned staging, one tile word per slot
+    int *h_claim_stage = nullptr;                    // pinned staging, one tile count per slot
     ServeEntry *h_entry_stage = nullptr;             // pinned staging ring (cap)
     unsigned long long *h_tail_stage = nullptr;      // pinned staging ring (cap)
     int *h_stop_stage = nullptr;
@@ -1475,7 +1475,7 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
     ck(cudaHostAlloc(&s->h_done, sizeof(int) * max_slots, cudaHostAllocMapped));
     ck(cudaHostAlloc(&s->h_front, sizeof(unsigned long long), cudaHostAllocMapped));
     ck(cudaHostAlloc(&s->h_slot_stage, sizeof(ServeSlot) * max_slots, cudaHostAllocDefault));
-    ck(cudaHostAlloc(&s->h_claim_stage, sizeof(unsigned long long) * max_slots, cudaHostAllocDefault));
+    ck(cudaHostAlloc(&s->h_claim_stage, sizeof(int) * max_slots, cudaHostAllocDefault));
     ck(cudaHostAlloc(&s->h_entry_stage, sizeof(ServeEntry) * s->cap, cudaHostAllocDefault));
     ck(cudaHostAlloc(&s->h_tail_stage, sizeof(unsigned long long) * s->cap, cudaHostAllocDefault));
     ck(cudaHostAlloc(&s->h_stop_stage, sizeof(int), cudaHostAllocDefault));
@@ -1568,13 +1568,15 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     }
     const long long seq = s->next_seq++;
     const unsigned useq = (unsigned)(seq & 0x7fffffff);
-    rec.p1 = (unsigned long long)useq << 32;                    // nothing to claim yet
-    rec.p2 = ((unsigned long long)useq << 32) | SERVE_UNOPENED;  // phase 1 not finished
+    rec.seq = (int)useq;
+    rec.state = 0;
+    rec.p1_rem = 0;  // nothing to claim until the record is complete on the device
+    rec.p2_rem = 0;
     rec.p1_done = 0;
     rec.p2_total = 0;
     rec.p2_nf = 0;
     rec.p2_done = 0;
-    s->h_claim_stage[slot] = ((unsigned long long)useq << 32) | (unsigned)rec.ntiles;
+    s->h_claim_stage[slot] = rec.ntiles;
     s->slot_seq[slot] = (long long)useq;
     s->h_done[slot] = -1;
     const int qi = (int)(s->tail % (unsigned long long)s->cap);
@@ -1582,11 +1584,11 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     s->h_entry_stage[qi].seq = (int)useq;
     s->tail += 1;
     s->h_tail_stage[qi] = s->tail;
-    // record, then its tile claim word, then queue entry, then tail: stream order makes each
+    // record, then its tile count, then queue entry, then tail: stream order makes each
     // visible before the next
     CK(cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(ServeSlot), cudaMemcpyHostToDevice, s->s_ctl),
        "server submit");
-    CK(cudaMemcpyAsync(&s->d_slots[slot].p1, &s->h_claim_stage[slot], sizeof(unsigned long long),
+    CK(cudaMemcpyAsync(&s->d_slots[slot].p1_rem, &s->h_claim_stage[slot], sizeof(int),
                        cudaMemcpyHostToDevice, s->s_ctl), "server submit");
     CK(cudaMemcpyAsync(s->d_queue + qi, &s->h_entry_stage[qi], sizeof(ServeEntry),
                        cudaMemcpyHostToDevice, s->s_ctl), "server submit");

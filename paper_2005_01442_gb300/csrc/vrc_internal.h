@@ -553,18 +553,20 @@ double microbench_work(int kind, int ctas, int iters);  // flops (MB_FMA) or byt
 // Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
 // entries in arrival order; ctl holds the device-side front and the host-published tail.
 constexpr int SERVE_WARPS = 4;                    // warps per CTA of the persistent kernel
-constexpr unsigned SERVE_UNOPENED = 0xffffffffu;  // ray claim word: phase 1 not finished
 struct ServeSlot {
     RenderLaunch L;          // the request's render (L.split.head != NULL: split render, with
                              // the request's own ray queue)
-    unsigned long long p1;   // (seq << 32) | tiles not yet claimed
-    unsigned long long p2;   // (seq << 32) | queued rays not yet claimed, or SERVE_UNOPENED
+    int seq;                 // the request in the slot (sequence number)
+    int state;               // 0 phase 1, 1 queued rays open, 2 every item claimed or none left
+    int p1_rem;              // tiles not yet claimed (claims subtract; <= 0: none)
+    int p2_rem;              // queued rays not yet claimed (opened by the end of phase 1)
     int ntiles;              // 8 x 4 pixel tiles of its image
     int stride;              // tile order: k -> k * stride mod ntiles (stride coprime to ntiles)
     int p1_done;             // tiles finished (device atomics)
     int p2_total;            // rays phase 1 queued (set when phase 1 finishes)
     int p2_nf;               // of them, records at the queue's front
     int p2_done;             // queued rays finished (device atomics)
+    int pad[2];
 };
 struct ServeEntry {
     int slot;
