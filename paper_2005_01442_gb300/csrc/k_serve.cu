@@ -88,14 +88,16 @@ __device__ __noinline__ void serve_tiles(const RenderLaunch &L, int k0, int chun
 }
 
 // Phase 2 of a claim: queued rays c0 .. c0 + chunk - 1, alternately to the warp's two groups
-// of 16 lanes, each finished with group_march and written out.
-__device__ __noinline__ void serve_rays(const RenderLaunch &L, unsigned c0, unsigned chunk,
-                                        unsigned nf) {
+// of 16 lanes, each finished with group_march and written out. The leaping variant is the
+// common one and stays inline; renders without bricks take an out-of-line copy.
+template <bool ESL>
+__device__ __forceinline__ void serve_rays_body(const RenderLaunch &L, unsigned c0,
+                                                unsigned chunk, unsigned nf) {
     const int lane = threadIdx.x & 31;
     const int q = lane & (SPLIT_G - 1), gbase = lane & ~(SPLIT_G - 1), group = lane >> 4;
     const unsigned gmask = ((1u << SPLIT_G) - 1u) << gbase;
     const float inv_step = 1.0f / L.grid.step;
-    const long nbricks = (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
+    const long nbricks = ESL ? (long)L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2] : 0;
     unsigned long long executed = 0;
     unsigned resampled = 0;
     for (unsigned c = c0 + group; c < c0 + chunk; c += 2) {
@@ -106,16 +108,16 @@ __device__ __noinline__ void serve_rays(const RenderLaunch &L, unsigned c0, unsi
         split_load(L.split.rec + (long)qi * SPLIT_REC, rp, jlo, pix, RC0, RC1, RC2, RT);
         float Pf[3], df[3], inv_df[3];
         ray_float(rp, Pf, df, inv_df);
-        if (L.dist) {
-            const uint8_t *dist = L.dist + octant_of(df) * nbricks;
-            group_march<true, SPLIT_G>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q,
-                                       gbase, RC0, RC1, RC2, RT, executed, resampled);
-        } else {
-            group_march<false, SPLIT_G>(L, rp, nullptr, Pf, df, inv_df, inv_step, jlo, gmask,
-                                        q, gbase, RC0, RC1, RC2, RT, executed, resampled);
-        }
+        const uint8_t *dist = ESL ? L.dist + octant_of(df) * nbricks : nullptr;
+        group_march<ESL, SPLIT_G>(L, rp, dist, Pf, df, inv_df, inv_step, jlo, gmask, q, gbase,
+                                  RC0, RC1, RC2, RT, executed, resampled);
         if (q == 0) L.out[pix] = make_float4(RC0, RC1, RC2, 1.0f - RT);
     }
+}
+
+__device__ __noinline__ void serve_rays_no_bricks(const RenderLaunch &L, unsigned c0,
+                                                  unsigned chunk, unsigned nf) {
+    serve_rays_body<false>(L, c0, chunk, nf);
 }
 
 // Marks a request finished for the host (after every pixel write of it).
@@ -124,17 +126,24 @@ __device__ __forceinline__ void publish_done(int *done_flags, int slot, unsigned
     *(volatile int *)&done_flags[slot] = (int)seq;
 }
 
-__global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
+// The two phases run as two persistent kernels, each compiled for its own occupancy (the
+// tiles' per-ray body wants more registers per thread, the queued rays' group march more
+// resident warps) and launched together with grids that fit side by side on every SM
+// (serve_ctas_per_sm). They share the slots, the FIFO and the leave flag; neither waits on
+// the other.
+template <int PHASE>
+__global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
     serve_kernel(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
                  int *done_flags, unsigned long long *front_mirror,
                  unsigned long long budget_ns, unsigned long long idle_ns) {
+    constexpr int WARPS = serve_warps(PHASE);
     // per-warp copy of the current request's launch record (reloaded when the request changes)
-    __shared__ RenderLaunch s_launch[SERVE_WARPS];
+    __shared__ RenderLaunch s_launch[WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RenderLaunch &L = s_launch[warp];
     int cached_slot = -1;
     unsigned cached_seq = 0;
-    const unsigned nwarps = gridDim.x * SERVE_WARPS;
+    const unsigned nwarps = gridDim.x * WARPS;
     const unsigned long long start = global_ns();
     unsigned long long idle_since = 0;
     unsigned sleep_ns = 256;
@@ -173,13 +182,13 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
                                 *(volatile unsigned long long *)front_mirror = f + 1;
                             continue;
                         }
-                        // the oldest request's queued rays first, then tiles
-                        if (claim_items(&S->p2_rem, 2 * nwarps, SERVE_RAYS_MAX, &first, &chunk)) {
+                        // the oldest request with work of this kernel's phase first
+                        if (PHASE == 2 &&
+                            claim_items(&S->p2_rem, 2 * nwarps, SERVE_RAYS_MAX, &first, &chunk))
                             action = 4;
-                        } else if (claim_items(&S->p1_rem, 2 * nwarps, SERVE_CLAIM_MAX, &first,
-                                               &chunk)) {
+                        if (PHASE == 1 &&
+                            claim_items(&S->p1_rem, 2 * nwarps, SERVE_CLAIM_MAX, &first, &chunk))
                             action = 3;
-                        }
                         if (action != 2) {
                             slot = es;
                             break;
@@ -220,7 +229,7 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
         }
         __syncwarp();
         const bool split = L.split.head != nullptr;
-        if (action == 3) {
+        if (PHASE == 1) {
             // phase 1: tiles k = ntiles - rem .. ntiles - rem + chunk - 1
             const int ntiles = __ldcg(&S->ntiles), stride = __ldcg(&S->stride);
             const int k0 = ntiles - first;
@@ -258,7 +267,9 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
         } else {
             // phase 2: queued rays c = total - rem .. total - rem + chunk - 1
             const int total = __ldcg(&S->p2_total);
-            serve_rays(L, (unsigned)(total - first), (unsigned)chunk, (unsigned)__ldcg(&S->p2_nf));
+            const unsigned nf = (unsigned)__ldcg(&S->p2_nf);
+            if (L.dist) serve_rays_body<true>(L, (unsigned)(total - first), (unsigned)chunk, nf);
+            else serve_rays_no_bricks(L, (unsigned)(total - first), (unsigned)chunk, nf);
             __threadfence();  // these rays' pixels before the count
             __syncwarp();
             if (lane == 0) {
@@ -273,14 +284,17 @@ __global__ void __launch_bounds__(32 * SERVE_WARPS, 4)
     }
 }
 
-const void *serve_kernel_ptr() { return (const void *)serve_kernel; }
-
-cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
-                         int *done_flags, unsigned long long *front_mirror,
-                         unsigned long long budget_ns, unsigned long long idle_ns, int ctas,
+cudaError_t launch_serve(int phase, ServeSlot *slots, const ServeEntry *queue, int cap,
+                         ServeCtl *ctl, int *done_flags, unsigned long long *front_mirror,
+                         unsigned long long budget_ns, unsigned long long idle_ns, int sms,
                          cudaStream_t st) {
-    serve_kernel<<<ctas, 32 * SERVE_WARPS, 0, st>>>(slots, queue, cap, ctl, done_flags,
-                                                    front_mirror, budget_ns, idle_ns);
+    const int ctas = sms * serve_ctas_per_sm(phase);
+    if (phase == 1)
+        serve_kernel<1><<<ctas, 32 * serve_warps(1), 0, st>>>(slots, queue, cap, ctl, done_flags,
+                                                              front_mirror, budget_ns, idle_ns);
+    else
+        serve_kernel<2><<<ctas, 32 * serve_warps(2), 0, st>>>(slots, queue, cap, ctl, done_flags,
+                                                              front_mirror, budget_ns, idle_ns);
     return cudaGetLastError();
 }
 

@@ -1402,8 +1402,8 @@ struct vrc_server {
     ServeEntry *h_entry_stage = nullptr;             // pinned staging ring (cap)
     unsigned long long *h_tail_stage = nullptr;      // pinned staging ring (cap)
     int *h_stop_stage = nullptr;
-    cudaStream_t s_ctl = nullptr, s_run = nullptr;
-    cudaEvent_t ev_run = nullptr;
+    cudaStream_t s_ctl = nullptr, s_run = nullptr, s_run1 = nullptr;  // phase 2, phase 1
+    cudaEvent_t ev_run = nullptr, ev_run1 = nullptr;
     cudaMemPool_t pool = nullptr;
     bool launched = false;
     unsigned long long tail = 0;
@@ -1417,6 +1417,7 @@ namespace {
 void server_free(vrc_server *s) {
     if (!s) return;
     if (s->s_run) cudaStreamSynchronize(s->s_run);
+    if (s->s_run1) cudaStreamSynchronize(s->s_run1);
     if (s->s_ctl) {
         for (void *r : s->region)
             if (r) cudaFreeAsync(r, s->s_ctl);
@@ -1434,8 +1435,10 @@ void server_free(vrc_server *s) {
     cudaFreeHost(s->h_stop_stage);
     if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->ev_run) cudaEventDestroy(s->ev_run);
+    if (s->ev_run1) cudaEventDestroy(s->ev_run1);
     if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
     if (s->s_run) cudaStreamDestroy(s->s_run);
+    if (s->s_run1) cudaStreamDestroy(s->s_run1);
     delete s;
 }
 
@@ -1483,7 +1486,9 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
     if (e == cudaSuccess) ck(cudaHostGetDevicePointer((void **)&s->d_front, s->h_front, 0));
     ck(cudaStreamCreateWithFlags(&s->s_ctl, cudaStreamNonBlocking));
     ck(cudaStreamCreateWithFlags(&s->s_run, cudaStreamNonBlocking));
+    ck(cudaStreamCreateWithFlags(&s->s_run1, cudaStreamNonBlocking));
     ck(cudaEventCreateWithFlags(&s->ev_run, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&s->ev_run1, cudaEventDisableTiming));
     if (e == cudaSuccess) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -1498,10 +1503,9 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
         *s->h_front = 0;
         ck(cudaMemset(s->d_ctl, 0, sizeof(ServeCtl)));
         ck(cudaMemset(s->d_slots, 0, sizeof(ServeSlot) * max_slots));
-        int per_sm = 0, sms = 0;
+        int sms = 0;
         ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-        ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(), 32 * SERVE_WARPS, 0));
-        s->ctas = sms * (per_sm > 0 ? per_sm : 1);
+        s->ctas = sms;  // the launches size their grids per SM
         ck(cudaDeviceSynchronize());
     }
     if (e != cudaSuccess) {
@@ -1606,9 +1610,11 @@ extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long l
     DeviceGuard g(ctx->device);
     bool busy = false;
     if (s->launched) {
-        cudaError_t q = cudaEventQuery(s->ev_run);
-        if (q == cudaErrorNotReady) busy = true;
-        else if (q != cudaSuccess) return cuda_fail(ctx, q, "serve kernel");
+        for (cudaEvent_t ev : {s->ev_run, s->ev_run1}) {
+            cudaError_t q = cudaEventQuery(ev);
+            if (q == cudaErrorNotReady) busy = true;
+            else if (q != cudaSuccess) return cuda_fail(ctx, q, "serve kernel");
+        }
     }
     if (!busy) {
         bool pending = false;
@@ -1617,11 +1623,18 @@ extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long l
         if (pending) {
             // the published tail must reach the device before the kernel could idle out
             CK(cudaStreamSynchronize(s->s_ctl), "server publish");
-            CK(cudaMemsetAsync(&s->d_ctl->leaving, 0, sizeof(int), s->s_run), "serve launch");
-            CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
+            CK(cudaMemsetAsync(&s->d_ctl->leaving, 0, sizeof(int), s->s_ctl), "serve launch");
+            CK(cudaStreamSynchronize(s->s_ctl), "serve launch");
+            // the queued-ray kernel first (it takes 3 CTAs of every SM), then the tile kernel
+            // in what is left
+            CK(launch_serve(2, s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
                             (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
                             s->s_run), "serve launch");
             CK(cudaEventRecord(s->ev_run, s->s_run), "serve launch");
+            CK(launch_serve(1, s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
+                            (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
+                            s->s_run1), "serve launch");
+            CK(cudaEventRecord(s->ev_run1, s->s_run1), "serve launch");
             s->launched = true;
             busy = true;
         }

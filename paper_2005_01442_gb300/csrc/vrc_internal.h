@@ -552,7 +552,11 @@ double microbench_work(int kind, int ctas, int iters);  // flops (MB_FMA) or byt
 
 // Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
 // entries in arrival order; ctl holds the device-side front and the host-published tail.
-constexpr int SERVE_WARPS = 4;                    // warps per CTA of the persistent kernel
+// The persistent serving kernels: phase 1 (tiles) and phase 2 (queued rays), warps per CTA and
+// CTAs per SM of each; together they fit one SM (65,536 registers: phase 2 at 64 registers per
+// thread, phase 1 at up to 128).
+constexpr int serve_warps(int phase) { return phase == 1 ? 2 : 8; }
+constexpr int serve_ctas_per_sm(int phase) { return phase == 1 ? 2 : 3; }
 struct ServeSlot {
     RenderLaunch L;          // the request's render (L.split.head != NULL: split render, with
                              // the request's own ray queue)
@@ -578,12 +582,11 @@ struct ServeCtl {
     int stop;                  // host request to leave
     int leaving;               // set by the first warp that times out; no new claims after it
 };
-const void *serve_kernel_ptr();
 // front_mirror: host-mapped copy of ctl->front (a lower bound of it) that the host reads
-// before it publishes a new entry into the ring of `cap` entries
-cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
-                         int *done_flags, unsigned long long *front_mirror,
-                         unsigned long long budget_ns, unsigned long long idle_ns, int ctas,
+// before it publishes a new entry into the ring of `cap` entries; sms: the device's SM count
+cudaError_t launch_serve(int phase, ServeSlot *slots, const ServeEntry *queue, int cap,
+                         ServeCtl *ctl, int *done_flags, unsigned long long *front_mirror,
+                         unsigned long long budget_ns, unsigned long long idle_ns, int sms,
                          cudaStream_t st);
 
 }  // namespace vrc
