@@ -52,8 +52,10 @@ __device__ __forceinline__ T load_volatile(const T *p) {
     return *(const volatile T *)p;
 }
 
-constexpr int SERVE_CLAIM_MAX = 8;   // most tiles claimed at once
-constexpr int SERVE_RAYS_MAX = 16;   // most queued rays claimed at once (8 per group)
+constexpr int SERVE_CLAIM_MIN = 4;   // fewest tiles claimed at once (while that many are left)
+constexpr int SERVE_CLAIM_MAX = 16;  // most tiles claimed at once
+constexpr int SERVE_RAYS_MIN = 4;    // fewest queued rays claimed at once (2 per group)
+constexpr int SERVE_RAYS_MAX = 32;   // most queued rays claimed at once (16 per group)
 constexpr int SERVE_SCAN = 8;        // queue entries a warp looks at from the front
 
 // Claims walk a request's tiles in the order k -> (k * stride) mod ntiles, stride coprime to
@@ -66,11 +68,11 @@ __device__ __forceinline__ int scattered_tile(int k, int ntiles, int stride) {
 // Takes up to max_chunk items (about the count seen / div) from a count of unclaimed items;
 // on success *first is the count before the claim (items first - *chunk .. first - 1 are
 // taken, counted from the end) and *chunk the count taken.
-__device__ __forceinline__ bool claim_items(int *count, unsigned div, int max_chunk, int *first,
-                                            int *chunk) {
+__device__ __forceinline__ bool claim_items(int *count, unsigned div, int min_chunk,
+                                            int max_chunk, int *first, int *chunk) {
     const int r = load_volatile(count);
     if (r <= 0) return false;  // no subtraction on an exhausted count: it stays near zero
-    const int c = min(max(r / (int)div, 1), max_chunk);
+    const int c = min(max(r / (int)div, min_chunk), max_chunk);
     const int old = atomicSub(count, c);
     if (old <= 0) return false;
     *first = old;
@@ -126,23 +128,24 @@ __device__ __forceinline__ void publish_done(int *done_flags, int slot, unsigned
     *(volatile int *)&done_flags[slot] = (int)seq;
 }
 
-// The two phases run as two persistent kernels, each compiled for its own occupancy (the
-// tiles' per-ray body wants more registers per thread, the queued rays' group march more
-// resident warps) and launched together with grids that fit side by side on every SM
-// (serve_ctas_per_sm). They share the slots, the FIFO and the leave flag; neither waits on
-// the other.
-template <int PHASE>
-__global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
+// One kernel does both phases, at the occupancy of the split render's second phase (the
+// bodies are bound by the latency of dependent loads: a persistent launch must keep every SM
+// as full of warps as a plain launch does, for whichever phase has work).
+__global__ void __launch_bounds__(32 * SERVE_WARPS, SERVE_CTAS_PER_SM)
     serve_kernel(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
                  int *done_flags, unsigned long long *front_mirror,
                  unsigned long long budget_ns, unsigned long long idle_ns) {
-    constexpr int WARPS = serve_warps(PHASE);
+    constexpr int WARPS = SERVE_WARPS;
     // per-warp copy of the current request's launch record (reloaded when the request changes)
     __shared__ RenderLaunch s_launch[WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RenderLaunch &L = s_launch[warp];
     int cached_slot = -1;
     unsigned cached_seq = 0;
+    int sticky = -1;  // slot of the warp's last claim: tried again before the queue is read
+    // what the warp's last fruitless look at the queue saw: new work can only appear when the
+    // host publishes (tail), when a request's queued rays open (epoch) or when a front moves
+    unsigned long long seen[4] = {~0ull, ~0ull, ~0ull, ~0ull};
     const unsigned nwarps = gridDim.x * WARPS;
     const unsigned long long start = global_ns();
     unsigned long long idle_since = 0;
@@ -158,10 +161,24 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
             } else if (now - start > budget_ns) {
                 atomicExch(&ctl->leaving, 1);  // the whole launch leaves, not this warp alone
                 action = 0;
+            } else if (sticky >= 0 &&
+                       (claim_items(&slots[sticky].p2_rem, nwarps, SERVE_RAYS_MIN,
+                                    SERVE_RAYS_MAX, &first, &chunk) ? (action = 4) :
+                        claim_items(&slots[sticky].p1_rem, nwarps, SERVE_CLAIM_MIN,
+                                    SERVE_CLAIM_MAX, &first, &chunk) ? (action = 3) : 0)) {
+                // more work from the slot of the last claim (whichever request it holds now):
+                // no queue reads on this path
+                slot = sticky;
+                idle_since = 0;
             } else {
+                sticky = -1;
                 const unsigned long long f = load_volatile(&ctl->front);
                 const unsigned long long t = load_volatile(&ctl->tail);
-                if (f >= t) {  // nothing published: bounded idle wait
+                const unsigned long long f1 = load_volatile(&ctl->front1);
+                const unsigned long long ep = load_volatile(&ctl->epoch);
+                if (f < t && f == seen[0] && t == seen[1] && f1 == seen[2] && ep == seen[3]) {
+                    action = 2;  // nothing has changed since the last fruitless look
+                } else if (f >= t) {  // nothing published: bounded idle wait
                     if (idle_since == 0) idle_since = now;
                     if (now - idle_since > idle_ns) {
                         atomicExch(&ctl->leaving, 1);
@@ -172,6 +189,8 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
                 } else {
                     idle_since = 0;
                     action = 2;
+                    // queued rays of the oldest requests (from the front, which moves once a
+                    // request's rays are all claimed)
                     for (int k = 0; k < SERVE_SCAN && f + k < t; ++k) {
                         const ServeEntry *e = &queue[(f + k) % cap];
                         const int es = __ldcg(&e->slot);
@@ -182,22 +201,51 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
                                 *(volatile unsigned long long *)front_mirror = f + 1;
                             continue;
                         }
-                        // the oldest request with work of this kernel's phase first
-                        if (PHASE == 2 &&
-                            claim_items(&S->p2_rem, 2 * nwarps, SERVE_RAYS_MAX, &first, &chunk))
+                        if (claim_items(&S->p2_rem, nwarps, SERVE_RAYS_MIN, SERVE_RAYS_MAX,
+                                        &first, &chunk)) {
                             action = 4;
-                        if (PHASE == 1 &&
-                            claim_items(&S->p1_rem, 2 * nwarps, SERVE_CLAIM_MAX, &first, &chunk))
-                            action = 3;
-                        if (action != 2) {
                             slot = es;
+                            sticky = es;
                             break;
                         }
-                        // every tile and every queued ray claimed: move the front on
+                        // every queued ray claimed, or none to come: move the front on
                         if (k == 0 && load_volatile(&S->state) >= 1 &&
-                            load_volatile(&S->p1_rem) <= 0 && load_volatile(&S->p2_rem) <= 0 &&
+                            load_volatile(&S->p2_rem) <= 0 &&
                             atomicCAS(&ctl->front, f, f + 1) == f)
                             *(volatile unsigned long long *)front_mirror = f + 1;
+                    }
+                    // else tiles of the oldest requests that still have some (from the tile
+                    // front, which moves once a request's tiles are all claimed, so requests
+                    // whose first phase is finishing do not hold the later ones back)
+                    if (action == 2) {
+                        unsigned long long f1 = load_volatile(&ctl->front1);
+                        if (f1 < f) {  // never behind the front
+                            atomicMax(&ctl->front1, f);
+                            f1 = f;
+                        }
+                        seen[0] = f;
+                        seen[1] = t;
+                        seen[2] = f1;
+                        seen[3] = ep;
+                        for (int k = 0; k < SERVE_SCAN && f1 + k < t; ++k) {
+                            const ServeEntry *e = &queue[(f1 + k) % cap];
+                            const int es = __ldcg(&e->slot);
+                            const int eq = __ldcg(&e->seq);
+                            ServeSlot *S = slots + es;
+                            if (load_volatile(&S->seq) == eq &&
+                                claim_items(&S->p1_rem, nwarps, SERVE_CLAIM_MIN, SERVE_CLAIM_MAX,
+                                            &first, &chunk)) {
+                                action = 3;
+                                slot = es;
+                                sticky = es;
+                                break;
+                            }
+                            if (k == 0 && (load_volatile(&S->seq) != eq ||
+                                           load_volatile(&S->p1_rem) <= 0) &&
+                                atomicCAS(&ctl->front1, f1, f1 + 1) == f1)
+                                seen[2] = ~0ull;  // moved: look again next time
+                        }
+                        if (action != 2) seen[0] = ~0ull;
                     }
                 }
             }
@@ -206,7 +254,7 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
         if (action == 0) break;
         if (action == 1 || action == 2) {  // exponential back-off up to 32 us between polls
             __nanosleep(sleep_ns);
-            sleep_ns = min(sleep_ns * 2u, action == 1 ? 32768u : 4096u);
+            sleep_ns = min(sleep_ns * 2u, 32768u);
             continue;
         }
         sleep_ns = 256;
@@ -229,7 +277,7 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
         }
         __syncwarp();
         const bool split = L.split.head != nullptr;
-        if (PHASE == 1) {
+        if (action == 3) {
             // phase 1: tiles k = ntiles - rem .. ntiles - rem + chunk - 1
             const int ntiles = __ldcg(&S->ntiles), stride = __ldcg(&S->stride);
             const int k0 = ntiles - first;
@@ -258,8 +306,10 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
                         atomicExch(&S->p2_rem, (int)total);
                         __threadfence();
                         atomicExch(&S->state, 1);
+                        atomicAdd(&ctl->epoch, 1ull);
                     } else {
                         atomicExch(&S->state, 2);
+                        atomicAdd(&ctl->epoch, 1ull);  // the front may move on
                         publish_done(done_flags, slot, (unsigned)seq);
                     }
                 }
@@ -276,6 +326,7 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
                 const int d = atomicAdd(&S->p2_done, chunk);
                 if (d + chunk == total) {
                     atomicExch(&S->state, 2);
+                    atomicAdd(&ctl->epoch, 1ull);
                     publish_done(done_flags, slot, (unsigned)seq);
                 }
             }
@@ -284,17 +335,12 @@ __global__ void __launch_bounds__(32 * serve_warps(PHASE), PHASE == 1 ? 8 : 4)
     }
 }
 
-cudaError_t launch_serve(int phase, ServeSlot *slots, const ServeEntry *queue, int cap,
-                         ServeCtl *ctl, int *done_flags, unsigned long long *front_mirror,
+cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
+                         int *done_flags, unsigned long long *front_mirror,
                          unsigned long long budget_ns, unsigned long long idle_ns, int sms,
                          cudaStream_t st) {
-    const int ctas = sms * serve_ctas_per_sm(phase);
-    if (phase == 1)
-        serve_kernel<1><<<ctas, 32 * serve_warps(1), 0, st>>>(slots, queue, cap, ctl, done_flags,
-                                                              front_mirror, budget_ns, idle_ns);
-    else
-        serve_kernel<2><<<ctas, 32 * serve_warps(2), 0, st>>>(slots, queue, cap, ctl, done_flags,
-                                                              front_mirror, budget_ns, idle_ns);
+    serve_kernel<<<sms * SERVE_CTAS_PER_SM, 32 * SERVE_WARPS, 0, st>>>(
+        slots, queue, cap, ctl, done_flags, front_mirror, budget_ns, idle_ns);
     return cudaGetLastError();
 }
 

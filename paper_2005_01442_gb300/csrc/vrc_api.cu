@@ -1386,9 +1386,10 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
 // ------------------------------------------------------------------------------------------
 // Persistent batched serving (kernel in k_serve.cu). The host side publishes requests into
 // device memory through a copy stream while the persistent kernel runs on its own stream.
-// Split-render requests get their own ray queue from a stream-ordered memory pool the server
-// owns (allocated on the copy stream at submission, freed there once the request is done), so
-// no allocation waits for the running kernel.
+// Split-render requests get their own ray queue from blocks the server owns: a finished
+// request's block goes back to a free list by size and is handed to a later request of the
+// same or a slightly smaller size; the server allocates a new block only when none fits (the
+// first requests of each size), so steady-state submission makes no allocation call.
 struct vrc_server {
     vrc_ctx *ctx = nullptr;
     int max_slots = 0, cap = 0, ctas = 0;
@@ -1404,12 +1405,14 @@ struct vrc_server {
     int *h_stop_stage = nullptr;
     cudaStream_t s_ctl = nullptr, s_run = nullptr, s_run1 = nullptr;  // phase 2, phase 1
     cudaEvent_t ev_run = nullptr, ev_run1 = nullptr;
-    cudaMemPool_t pool = nullptr;
+    std::multimap<size_t, void *> free_blocks;  // ray-queue blocks not in use, by size
+    std::vector<void *> all_blocks;
     bool launched = false;
     unsigned long long tail = 0;
     long long next_seq = 0;
     std::vector<long long> slot_seq;  // request in each slot, -1 when free
     std::vector<void *> region;       // ray queue of the split request in each slot
+    std::vector<size_t> region_bytes;
 };
 
 namespace {
@@ -1418,11 +1421,8 @@ void server_free(vrc_server *s) {
     if (!s) return;
     if (s->s_run) cudaStreamSynchronize(s->s_run);
     if (s->s_run1) cudaStreamSynchronize(s->s_run1);
-    if (s->s_ctl) {
-        for (void *r : s->region)
-            if (r) cudaFreeAsync(r, s->s_ctl);
-        cudaStreamSynchronize(s->s_ctl);
-    }
+    if (s->s_ctl) cudaStreamSynchronize(s->s_ctl);
+    for (void *b : s->all_blocks) cudaFree(b);
     cudaFree(s->d_slots);
     cudaFree(s->d_queue);
     cudaFree(s->d_ctl);
@@ -1433,7 +1433,6 @@ void server_free(vrc_server *s) {
     cudaFreeHost(s->h_entry_stage);
     cudaFreeHost(s->h_tail_stage);
     cudaFreeHost(s->h_stop_stage);
-    if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->ev_run) cudaEventDestroy(s->ev_run);
     if (s->ev_run1) cudaEventDestroy(s->ev_run1);
     if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
@@ -1447,12 +1446,31 @@ bool server_slot_free(vrc_server *s, int slot) {
     return q < 0 || *(volatile int *)&s->h_done[slot] == (int)q;
 }
 
-// Returns a finished request's ray queue to the pool (stream-ordered on the copy stream).
+// Returns a finished request's ray queue to the free list (the kernel is done with it: the
+// request published completion).
 void server_release_region(vrc_server *s, int slot) {
     if (s->region[slot]) {
-        cudaFreeAsync(s->region[slot], s->s_ctl);
+        s->free_blocks.emplace(s->region_bytes[slot], s->region[slot]);
         s->region[slot] = nullptr;
     }
+}
+
+// A ray-queue block of at least `bytes` (and at most twice that), reused or new.
+cudaError_t server_take_region(vrc_server *s, size_t bytes, void **out, size_t *got) {
+    auto it = s->free_blocks.lower_bound(bytes);
+    if (it != s->free_blocks.end() && it->first <= 2 * bytes) {
+        *out = it->second;
+        *got = it->first;
+        s->free_blocks.erase(it);
+        return cudaSuccess;
+    }
+    void *b = nullptr;
+    cudaError_t e = cudaMalloc(&b, bytes);
+    if (e != cudaSuccess) return e;
+    s->all_blocks.push_back(b);
+    *out = b;
+    *got = bytes;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -1470,6 +1488,7 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
     s->cap = 4 * max_slots;
     s->slot_seq.assign(max_slots, -1);
     s->region.assign(max_slots, nullptr);
+    s->region_bytes.assign(max_slots, 0);
     cudaError_t e = cudaSuccess;
     auto ck = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     ck(cudaMalloc(&s->d_slots, sizeof(ServeSlot) * max_slots));
@@ -1489,15 +1508,6 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
     ck(cudaStreamCreateWithFlags(&s->s_run1, cudaStreamNonBlocking));
     ck(cudaEventCreateWithFlags(&s->ev_run, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&s->ev_run1, cudaEventDisableTiming));
-    if (e == cudaSuccess) {
-        cudaMemPoolProps props = {};
-        props.allocType = cudaMemAllocationTypePinned;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = ctx->device;
-        ck(cudaMemPoolCreate(&s->pool, &props));
-        unsigned long long keep = ~0ull;  // keep freed queues mapped for the next requests
-        if (e == cudaSuccess) ck(cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep));
-    }
     if (e == cudaSuccess) {
         for (int i = 0; i < max_slots; ++i) s->h_done[i] = -1;
         *s->h_front = 0;
@@ -1545,16 +1555,18 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     const size_t npix = (size_t)cam->width * cam->height;
     if (split) {
         void *r = nullptr;
-        const size_t bytes = 256 + npix * SPLIT_REC * sizeof(float4);
-        cudaError_t e = cudaMallocFromPoolAsync(&r, bytes, s->pool, s->s_ctl);
+        size_t got = 0;
+        const size_t bytes = npix * SPLIT_REC * sizeof(float4);
+        cudaError_t e = server_take_region(s, bytes, &r, &got);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, VRC_ERR_OOM, "no device memory for a ray queue of %zu bytes", bytes);
         }
         s->region[slot] = r;
-        CK(cudaMemsetAsync(r, 0, 256, s->s_ctl), "server submit");
-        rec.L.split.head = (unsigned *)r;
-        rec.L.split.rec = (float4 *)((unsigned char *)r + 256);
+        s->region_bytes[slot] = got;
+        // the queue's counters live in the slot record (zeroed by its copy below)
+        rec.L.split.head = s->d_slots[slot].qhead;
+        rec.L.split.rec = (float4 *)r;
         rec.L.split.cap = (unsigned)npix;
         rec.L.split.long_len = (unsigned)(0.35f * (rec.L.grid.n[0] + rec.L.grid.n[1] +
                                                     rec.L.grid.n[2]) / 3.0f / rec.L.grid.step);
@@ -1574,6 +1586,7 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     const unsigned useq = (unsigned)(seq & 0x7fffffff);
     rec.seq = (int)useq;
     rec.state = 0;
+    memset(rec.qhead, 0, sizeof(rec.qhead));
     rec.p1_rem = 0;  // nothing to claim until the record is complete on the device
     rec.p2_rem = 0;
     rec.p1_done = 0;
@@ -1625,16 +1638,11 @@ extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long l
             CK(cudaStreamSynchronize(s->s_ctl), "server publish");
             CK(cudaMemsetAsync(&s->d_ctl->leaving, 0, sizeof(int), s->s_ctl), "serve launch");
             CK(cudaStreamSynchronize(s->s_ctl), "serve launch");
-            // the queued-ray kernel first (it takes 3 CTAs of every SM), then the tile kernel
-            // in what is left
-            CK(launch_serve(2, s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
+            CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
                             (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
                             s->s_run), "serve launch");
             CK(cudaEventRecord(s->ev_run, s->s_run), "serve launch");
-            CK(launch_serve(1, s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
-                            (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
-                            s->s_run1), "serve launch");
-            CK(cudaEventRecord(s->ev_run1, s->s_run1), "serve launch");
+            CK(cudaEventRecord(s->ev_run1, s->s_run), "serve launch");
             s->launched = true;
             busy = true;
         }

@@ -552,11 +552,11 @@ double microbench_work(int kind, int ctas, int iters);  // flops (MB_FMA) or byt
 
 // Persistent serving (k_serve.cu). A slot holds one request; the queue holds (slot, seq)
 // entries in arrival order; ctl holds the device-side front and the host-published tail.
-// The persistent serving kernels: phase 1 (tiles) and phase 2 (queued rays), warps per CTA and
-// CTAs per SM of each; together they fit one SM (65,536 registers: phase 2 at 64 registers per
-// thread, phase 1 at up to 128).
-constexpr int serve_warps(int phase) { return phase == 1 ? 2 : 8; }
-constexpr int serve_ctas_per_sm(int phase) { return phase == 1 ? 2 : 3; }
+// The persistent serving kernel: warps per CTA and CTAs per SM (64 registers per thread, the
+// occupancy of the split render's second phase: the bodies are bound by the latency of
+// dependent loads, so every SM keeps as many warps resident as it can).
+constexpr int SERVE_WARPS = 8;
+constexpr int SERVE_CTAS_PER_SM = 4;
 struct ServeSlot {
     RenderLaunch L;          // the request's render (L.split.head != NULL: split render, with
                              // the request's own ray queue)
@@ -570,6 +570,7 @@ struct ServeSlot {
     int p2_total;            // rays phase 1 queued (set when phase 1 finishes)
     int p2_nf;               // of them, records at the queue's front
     int p2_done;             // queued rays finished (device atomics)
+    unsigned qhead[4];       // the split request's ray-queue counters (front, -, back)
     int pad[2];
 };
 struct ServeEntry {
@@ -577,15 +578,17 @@ struct ServeEntry {
     int seq;
 };
 struct ServeCtl {
-    unsigned long long front;  // oldest queue entry that may still have work to claim
-    unsigned long long tail;   // entries published by the host
-    int stop;                  // host request to leave
-    int leaving;               // set by the first warp that times out; no new claims after it
+    unsigned long long front;   // oldest queue entry that may still have queued rays to claim
+    unsigned long long tail;    // entries published by the host
+    int stop;                   // host request to leave
+    int leaving;                // set by the first warp that times out; no new claims after it
+    unsigned long long front1;  // oldest entry that may still have tiles to claim (>= front)
+    unsigned long long epoch;   // bumped whenever queued rays open for claiming
 };
 // front_mirror: host-mapped copy of ctl->front (a lower bound of it) that the host reads
 // before it publishes a new entry into the ring of `cap` entries; sms: the device's SM count
-cudaError_t launch_serve(int phase, ServeSlot *slots, const ServeEntry *queue, int cap,
-                         ServeCtl *ctl, int *done_flags, unsigned long long *front_mirror,
+cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
+                         int *done_flags, unsigned long long *front_mirror,
                          unsigned long long budget_ns, unsigned long long idle_ns, int sms,
                          cudaStream_t st);
 
