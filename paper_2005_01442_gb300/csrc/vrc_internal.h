@@ -537,7 +537,8 @@ struct AdjointLaunch {
     float *grad_tf;
     float *grad_vol;
     int seg;
-    int open_alpha;  // derivative from above at table opacity 0
+    int open_alpha;     // derivative from above at table opacity 0
+    int *tile_counter;  // device int the launch zeroes: tiles claimed so far
 };
 cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st);
 
