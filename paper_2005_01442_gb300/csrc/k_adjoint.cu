@@ -18,8 +18,6 @@
 // so the last bits, vary from run to run). Samples in empty bricks or clear cells (opacity
 // exactly zero, whose derivative is taken as zero at the clamp, so that every contribution of
 // such a sample is exactly zero) are skipped exactly as in the forward.
-#include <algorithm>
-
 #include "vrc_internal.h"
 
 namespace vrc {
@@ -82,12 +80,15 @@ __device__ __forceinline__ void add_taps_x(float *row, int x0, int nx, float v0,
     atomicAdd(row + min(max(x0 + 3, 0), nx - 1), v3);
 }
 
-// The reverse walk of the 32 rays of one 8 x 4 pixel tile (one ray per lane); transfer-function
-// gradients go to the CTA's shared table s_gtf.
 template <bool ESL, bool VOLGRAD>
-__device__ __forceinline__ void adjoint_tile(const AdjointLaunch &A, int tile, float *s_gtf) {
+__global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A) {
+    __shared__ float s_gtf[256 * 4];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_gtf[i] = 0.0f;
+    __syncthreads();
     const RenderLaunch &L = A.L;
+
     const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
     const int tiles_x = (L.cam.width + 7) >> 3;
     const int px = (tile % tiles_x) * 8 + (lane & 7);
     const int py = (tile / tiles_x) * 4 + (lane >> 3);
@@ -215,26 +216,6 @@ __device__ __forceinline__ void adjoint_tile(const AdjointLaunch &A, int tile, f
             U = U - alpha * U;
         }
     }
-}
-
-// Rays of very different lengths (air, soft tissue, bone) make fixed tile-per-warp launches
-// wait on their longest rays: here a grid that fills the device once lets every warp claim
-// the next tile (A.tile_counter, zero at launch) until none is left, and flushes the CTA's
-// transfer-function gradients once at the end.
-template <bool ESL, bool VOLGRAD>
-__global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A) {
-    __shared__ float s_gtf[256 * 4];
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_gtf[i] = 0.0f;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int ntiles = ((A.L.cam.width + 7) >> 3) * ((A.L.cam.height + 3) >> 2);
-    while (true) {
-        int tile = 0;
-        if (lane == 0) tile = atomicAdd(A.tile_counter, 1);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        if (tile >= ntiles) break;
-        adjoint_tile<ESL, VOLGRAD>(A, tile, s_gtf);
-    }
     __syncthreads();
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
         const float v = s_gtf[i];
@@ -242,30 +223,15 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
     }
 }
 
-template <bool ESL, bool VOLGRAD>
-static cudaError_t launch_adjoint_t(const AdjointLaunch &A, cudaStream_t st) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel<ESL, VOLGRAD>,
-                                                          32 * ADJ_WARPS, 0);
-    if (e != cudaSuccess) return e;
-    const long tiles = (long)((A.L.cam.width + 7) / 8) * ((A.L.cam.height + 3) / 4);
-    const long fill = (long)sms * (per_sm > 0 ? per_sm : 1);
-    const unsigned grid = (unsigned)std::max(1L, std::min(fill, (tiles + ADJ_WARPS - 1) / ADJ_WARPS));
-    e = cudaMemsetAsync(A.tile_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    adjoint_kernel<ESL, VOLGRAD><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st) {
+    const long tiles = (long)((A.L.cam.width + 7) / 8) * ((A.L.cam.height + 3) / 4);
+    const unsigned grid = (unsigned)((tiles + ADJ_WARPS - 1) / ADJ_WARPS);
     const bool esl = A.L.dist != nullptr, vg = A.grad_vol != nullptr;
-    if (esl && vg) return launch_adjoint_t<true, true>(A, st);
-    if (esl) return launch_adjoint_t<true, false>(A, st);
-    if (vg) return launch_adjoint_t<false, true>(A, st);
-    return launch_adjoint_t<false, false>(A, st);
+    if (esl && vg) adjoint_kernel<true, true><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    else if (esl) adjoint_kernel<true, false><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    else if (vg) adjoint_kernel<false, true><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    else adjoint_kernel<false, false><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    return cudaGetLastError();
 }
 
 }  // namespace vrc

@@ -70,8 +70,8 @@ int slot_of(int B) { return B == 16 ? 1 : 0; }
 int lanes_of(int kernel) { return kernel == 3 ? 4 : kernel == 4 ? 8 : kernel == 5 ? 16 : 32; }
 
 // Queue of the split render, one per stream that renders with it (renders on one stream run
-// in order, so they can share it): a 256-byte header (pushed and claimed counts; word 4 is the
-// adjoint's tile counter), then `cap` ray records of SPLIT_REC float4.
+// in order, so they can share it): a 256-byte header (pushed, claimed counts), then `cap`
+// ray records of SPLIT_REC float4.
 struct SplitBuf {
     unsigned char *base = nullptr;
     size_t cap = 0;
@@ -1190,14 +1190,6 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
     A.grad_vol = grad_vol_dev;
     A.seg = ck.seg;
     A.open_alpha = params->grad_open_alpha;
-    {
-        // the tile counter: a word of the stream's split-render queue header (launches on one
-        // stream run in order, so they can share it)
-        RaySplit q;
-        s = split_queue(ctx, st, 1, q);
-        if (s != VRC_OK) return s;
-        A.tile_counter = (int *)(q.head + 4);
-    }
     A.L.out = nullptr;
     A.L.counters = nullptr;
     if (ckpt_dev) {

@@ -537,8 +537,7 @@ struct AdjointLaunch {
     float *grad_tf;
     float *grad_vol;
     int seg;
-    int open_alpha;     // derivative from above at table opacity 0
-    int *tile_counter;  // device int the launch zeroes: tiles claimed so far
+    int open_alpha;  // derivative from above at table opacity 0
 };
 cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st);
 
