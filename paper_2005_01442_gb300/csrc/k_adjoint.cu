@@ -3,26 +3,46 @@
 // its forward model (cubic B-spline resampling, post-classification, opacity correction,
 // front-to-back compositing, early termination).
 //
-// One thread per ray, reading the checkpoints of a forward render (RenderLaunch::ckpt): the
-// ray's last composited sample and, for each segment of `seg` samples up to it, the
-// transmittance at the segment's start (-1 for segments without a composited sample). Walking
-// the segments back to front: recompute the segment forward from its checkpoint (never
-// dividing by 1 - alpha), then walk its samples back to front keeping
-//   S = normalised colour behind the sample, U = transmittance behind the sample,
-//   dL/drgb_j   = T_j alpha_j g_rgb
-//   dL/dalpha_j = T_j [ g_rgb . (rgb_j - S) + g_A U ]
-//   S <- alpha_j rgb_j + (1 - alpha_j) S,   U <- (1 - alpha_j) U
-// and chain through alpha = 1 - (1-a)^delta, the table interpolation (into the two entries)
-// and the 64 B-spline taps (into the voxels). Transfer-function gradients are summed in
-// shared memory per CTA, voxel gradients with global float atomics (the summation order, and
-// so the last bits, vary from run to run). Samples in empty bricks or clear cells (opacity
-// exactly zero, whose derivative is taken as zero at the clamp, so that every contribution of
-// such a sample is exactly zero) are skipped exactly as in the forward.
+// It reads the checkpoints of a forward render (RenderLaunch::ckpt): the ray's last composited
+// sample and, for each segment of `seg` samples up to it, the transmittance at the segment's
+// start (-1 for segments without a composited sample). Given those, the segments of a ray are
+// independent but for what lies behind each, so a group of G lanes takes one ray and its
+// lanes take G consecutive segments at a time, back to front:
+//   1. each lane recomputes its segment forward from the checkpoint (never dividing by
+//      1 - alpha), keeping every sample's value and transmittance, and also composites the
+//      segment on its own from transmittance 1, P = (C, T);
+//   2. a scan of the "over" operator across the group gives each lane what lies behind its
+//      segment -- the segments of the lanes after it in this round, then the carry of the
+//      rounds before -- as S = normalised colour behind, U = transmittance behind;
+//   3. each lane walks its samples back to front:
+//        dL/drgb_j   = T_j alpha_j g_rgb
+//        dL/dalpha_j = T_j [ g_rgb . (rgb_j - S) + g_A U ]
+//        S <- alpha_j rgb_j + (1 - alpha_j) S,   U <- (1 - alpha_j) U
+//      and chains through alpha = 1 - (1-a)^delta, the table interpolation (into the two
+//      entries) and the 64 B-spline taps (into the voxels).
+// A long ray then costs about 1/G of its segments in serial steps. Transfer-function
+// gradients are summed in shared memory per CTA, voxel gradients with global float atomics
+// (the summation order, and so the last bits, vary from run to run). Samples in empty bricks
+// or clear cells (opacity exactly zero, whose derivative is taken as zero at the clamp, so
+// that every contribution of such a sample is exactly zero) are skipped exactly as in the
+// forward.
 #include "vrc_internal.h"
 
 namespace vrc {
 
 constexpr int ADJ_WARPS = 4;
+// Lanes per ray: more lanes shorten a ray's serial chain of segments, fewer keep more rays in
+// flight. Measured per launch (ms; 256^3 float32 CT without termination / 512^2 x 2000 int16
+// CT at step 0.25 with termination):
+//   image        1 lane   2      4      8
+//   256^2        1.14     0.82   0.61   0.34
+//   512^2        1.36     1.07   0.70   0.63
+//   1024^2       2.02     1.53   1.42   1.81    (512^2 x 2000: 2.08 1.78 1.55 1.62)
+//   2048^2       3.92     3.70   4.58   6.76
+//   4096^2 (512^2 x 2000)  7.92   7.53   9.99  15.2
+__host__ __device__ constexpr int adjoint_lanes_for(long pixels) {
+    return pixels < (512L << 10) ? 8 : pixels < (2048L << 10) ? 4 : 2;
+}
 
 struct SampleEval {
     float s;        // resampled value
@@ -80,28 +100,40 @@ __device__ __forceinline__ void add_taps_x(float *row, int x0, int nx, float v0,
     atomicAdd(row + min(max(x0 + 3, 0), nx - 1), v3);
 }
 
-template <bool ESL, bool VOLGRAD>
+template <bool ESL, bool VOLGRAD, int ADJ_G>
 __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A) {
     __shared__ float s_gtf[256 * 4];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_gtf[i] = 0.0f;
     __syncthreads();
     const RenderLaunch &L = A.L;
 
-    const int lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
-    const int tiles_x = (L.cam.width + 7) >> 3;
-    const int px = (tile % tiles_x) * 8 + (lane & 7);
-    const int py = (tile / tiles_x) * 4 + (lane >> 3);
-    const bool valid = px < L.cam.width && py < L.cam.height;
-    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (valid) g = A.grad_out[(long)py * L.cam.width + px];
-    const bool any_g = g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f;
-
-    RaySetup ray;
-    ray.nseg = 0;
-    if (valid && any_g) ray_setup(L.cam, L.grid, px, py, ray);
+    // ADJ_G lanes per ray: a warp takes a row of 32 / ADJ_G pixels, a CTA ADJ_WARPS such rows
+    // (ADJ_G from adjoint_lanes_for: the image's pixel count)
+    constexpr int G = ADJ_G, RX = 32 / ADJ_G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane & (G - 1), gbase = lane & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const int tiles_x = (L.cam.width + RX - 1) / RX;
+    const int px = (blockIdx.x % tiles_x) * RX + lane / G;
+    const int py = (blockIdx.x / tiles_x) * ADJ_WARPS + warp;
     const float step = L.grid.step;
     const int seg = A.seg;
+
+    // the forward's record of this ray: first checkpointed segment, last composited sample
+    // (read first: most rays of a CT view composite nothing and need no set-up)
+    bool work = false;
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int2 h = make_int2(0, -1);
+    if (px < L.cam.width && py < L.cam.height) {
+        g = A.grad_out[(long)py * L.cam.width + px];
+        if (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f) {
+            h = L.ckpt_head[(long)py * L.cam.width + px];
+            work = h.y >= 0;
+        }
+    }
+    RaySetup ray;
+    ray.nseg = 0;
+    if (work) ray_setup(L.cam, L.grid, px, py, ray);
     RayPos rp;
     ray_pos_init(ray, step, rp);
     float Pf[3], df[3], inv_df[3];
@@ -109,40 +141,79 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
     const uint8_t *dist = nullptr;
     if (ESL)
         dist = L.dist + (long)octant_of(df) * L.bricks.nb[0] * L.bricks.nb[1] * L.bricks.nb[2];
-
-    // the forward's record of this ray: first checkpointed segment, last composited sample
-    int k0 = 0, jlast = -1;
-    if (valid && any_g) {
-        const int2 h = L.ckpt_head[(long)py * L.cam.width + px];
-        k0 = max(h.x, 0);
-        jlast = min(h.y, rp.nseg - 1);
-    }
+    const int k0 = work ? max(h.x, 0) : 0;
+    const int jlast = work ? min(h.y, rp.nseg - 1) : -1;
     const float *ck_row = L.ckpt + ((long)py * L.cam.width + px) * L.ckpt_K;
+    const int klast = jlast >= 0 ? min(jlast / seg, L.ckpt_K - 1) : -1;
 
-    // ------------------------------------------------------------------ backward pass
-    float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, U = 1.0f;
     float buf_s[ADJ_MAX_SEG], buf_T[ADJ_MAX_SEG];
     int buf_j[ADJ_MAX_SEG];
-    for (int k = jlast >= 0 ? min(jlast / seg, L.ckpt_K - 1) : -1; k >= k0; --k) {
-        // recompute the segment forward from its checkpoint
-        float T = ck_row[k];
-        if (!(T >= 0.0f)) continue;  // no composited sample in this segment
+    // what lies behind the segments of the current round: normalised colour and transmittance
+    float cS0 = 0.0f, cS1 = 0.0f, cS2 = 0.0f, cU = 1.0f;
+    // rounds of G segments, back to front: lane q takes segment kr - q
+    for (int kr = klast; kr >= k0; kr -= G) {
+        const int k = kr - q;
+        float T = k >= k0 ? ck_row[k] : -1.0f;
+        // recompute the segment forward from its checkpoint (absolute transmittance T) and
+        // from 1 (its own composite over what lies behind it)
         int n = 0;
-        const int j1 = min(k * seg + seg, jlast + 1);
-        for (int j = k * seg; j < j1; ++j) {
-            int ip[3];
-            float f[3], delta;
-            place(rp, step, L.grid.n, j, ip, f, delta);
-            if (ESL && (dist[brick_of(L.bricks, ip)] != 0 ||
-                        (L.cells && !cell_open(L.cells, L.cwx, L.grid.n, ip))))
-                continue;
-            SampleEval e;
-            eval_sample(L, ip, f, delta, e);
-            buf_s[n] = e.s;
-            buf_T[n] = T;
-            buf_j[n] = j;
-            ++n;
-            T = T - T * e.alpha;
+        float l0 = 0.0f, l1 = 0.0f, l2 = 0.0f, lT = 1.0f;
+        if (T >= 0.0f) {  // else no composited sample in this segment
+            const int j1 = min(k * seg + seg, jlast + 1);
+            for (int j = k * seg; j < j1; ++j) {
+                int ip[3];
+                float f[3], delta;
+                place(rp, step, L.grid.n, j, ip, f, delta);
+                if (ESL && (dist[brick_of(L.bricks, ip)] != 0 ||
+                            (L.cells && !cell_open(L.cells, L.cwx, L.grid.n, ip))))
+                    continue;
+                SampleEval e;
+                eval_sample(L, ip, f, delta, e);
+                buf_s[n] = e.s;
+                buf_T[n] = T;
+                buf_j[n] = j;
+                ++n;
+                T = T - T * e.alpha;
+                const float w = lT * e.alpha;
+                l0 = fmaf(w, e.rgba.x, l0);
+                l1 = fmaf(w, e.rgba.y, l1);
+                l2 = fmaf(w, e.rgba.z, l2);
+                lT = lT - w;
+            }
+        }
+        // behind lane q's segment: the segments of lanes q-1 .. 0 of this round (front to
+        // back), then the carry. Inclusive scan v_q = P_q o P_{q-1} o ... o P_0 of the "over"
+        // operator (C_a, T_a) o (C_b, T_b) = (C_a + T_a C_b, T_a T_b).
+        float v0 = l0, v1 = l1, v2 = l2, vT = lT;
+        for (int o = 1; o < G; o <<= 1) {
+            const float p0 = __shfl_up_sync(gmask, v0, o, G);
+            const float p1 = __shfl_up_sync(gmask, v1, o, G);
+            const float p2 = __shfl_up_sync(gmask, v2, o, G);
+            const float pT = __shfl_up_sync(gmask, vT, o, G);
+            if (q >= o) {
+                v0 = fmaf(vT, p0, v0);
+                v1 = fmaf(vT, p1, v1);
+                v2 = fmaf(vT, p2, v2);
+                vT = vT * pT;
+            }
+        }
+        float e0 = __shfl_up_sync(gmask, v0, 1, G), e1 = __shfl_up_sync(gmask, v1, 1, G);
+        float e2 = __shfl_up_sync(gmask, v2, 1, G), eT = __shfl_up_sync(gmask, vT, 1, G);
+        if (q == 0) {
+            e0 = e1 = e2 = 0.0f;
+            eT = 1.0f;
+        }
+        float S0 = fmaf(eT, cS0, e0), S1 = fmaf(eT, cS1, e1), S2 = fmaf(eT, cS2, e2);
+        float U = eT * cU;
+        {  // the next round lies in front of this one: carry = v_{G-1} o carry
+            const float a0 = __shfl_sync(gmask, v0, G - 1, G);
+            const float a1 = __shfl_sync(gmask, v1, G - 1, G);
+            const float a2 = __shfl_sync(gmask, v2, G - 1, G);
+            const float aT = __shfl_sync(gmask, vT, G - 1, G);
+            cS0 = fmaf(aT, cS0, a0);
+            cS1 = fmaf(aT, cS1, a1);
+            cS2 = fmaf(aT, cS2, a2);
+            cU = aT * cU;
         }
         // back to front over the segment
         for (int i = n - 1; i >= 0; --i) {
@@ -223,14 +294,24 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) adjoint_kernel(AdjointLaunch A
     }
 }
 
-cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st) {
-    const long tiles = (long)((A.L.cam.width + 7) / 8) * ((A.L.cam.height + 3) / 4);
-    const unsigned grid = (unsigned)((tiles + ADJ_WARPS - 1) / ADJ_WARPS);
+template <int G>
+static void launch_adjoint_g(const AdjointLaunch &A, cudaStream_t st) {
+    constexpr int RX = 32 / G;
+    const unsigned grid = (unsigned)(((long)(A.L.cam.width + RX - 1) / RX) *
+                                     ((A.L.cam.height + ADJ_WARPS - 1) / ADJ_WARPS));
     const bool esl = A.L.dist != nullptr, vg = A.grad_vol != nullptr;
-    if (esl && vg) adjoint_kernel<true, true><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
-    else if (esl) adjoint_kernel<true, false><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
-    else if (vg) adjoint_kernel<false, true><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
-    else adjoint_kernel<false, false><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    if (esl && vg) adjoint_kernel<true, true, G><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    else if (esl) adjoint_kernel<true, false, G><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    else if (vg) adjoint_kernel<false, true, G><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+    else adjoint_kernel<false, false, G><<<grid, 32 * ADJ_WARPS, 0, st>>>(A);
+}
+
+cudaError_t launch_adjoint(const AdjointLaunch &A, cudaStream_t st) {
+    switch (adjoint_lanes_for((long)A.L.cam.width * A.L.cam.height)) {
+    case 8: launch_adjoint_g<8>(A, st); break;
+    case 4: launch_adjoint_g<4>(A, st); break;
+    default: launch_adjoint_g<2>(A, st);
+    }
     return cudaGetLastError();
 }
 

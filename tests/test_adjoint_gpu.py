@@ -211,6 +211,33 @@ def test_backward_at_the_differentiation_config(R, orc, torch, forward):
     R.free_tf(tid)
 
 
+@pytest.mark.parametrize("size", [1024, 1536])
+def test_backward_at_image_sizes_with_fewer_lanes_per_ray(R, orc, torch, size):
+    """Large images take fewer lanes per ray (4 at 1024^2, 2 at 1536^2): 2048 seeded pixels
+    carry the loss (every other pixel has none and is skipped), checkpoints from the split
+    render, gradients against the FP64 oracle's reverse mode on the same pixels."""
+    vol, tf = _scene(seed=47, shape=(48, 56, 64))
+    vid = R.upload_volume(vol)
+    R.build_bricks(vid, 8)
+    tid = R.set_tf(tf, synth.CT_LO, synth.CT_HI)
+    rng = np.random.default_rng(48)
+    cam = synth.orbit_cameras(49, 1, synth.dims_of(vol), size, size)[0]
+    g, pix = _pixel_weights(rng, cam, 2048)
+    ck = R.ckpt_buffer(vid, cam, 0.5, 64)
+    R.render(vid, tid, cam, brick=8, ckpt=ck)
+    gtf = torch.zeros((256, 4), device="cuda")
+    gvol = torch.zeros(vol.shape, device="cuda")
+    R.render_backward(vid, tid, cam, torch.tensor(g, device="cuda"), gtf, gvol, brick=8,
+                      ckpt=ck)
+    rtf, rvol = orc.render_grad(vol, tf, synth.CT_LO, synth.CT_HI, cam, 0.5,
+                                g.reshape(-1, 4)[pix[:, 1] * cam.width + pix[:, 0]]
+                                .astype(np.float64), brick=8, pixels=pix)
+    _rel_check_tf(gtf.cpu().numpy().astype(np.float64), rtf)
+    _rel_check_vol(gvol.cpu().numpy().astype(np.float64), rvol)
+    R.free_volume(vid)
+    R.free_tf(tid)
+
+
 @pytest.mark.parametrize("forward", ["replay", "ray", "split"])
 def test_long_rays_with_hundreds_of_checkpoints(R, orc, torch, forward):
     """Rays of 6400 samples (a 48 x 48 x 1600 volume along z at step 0.25) in segments of 16:
