@@ -86,7 +86,7 @@ typedef struct {
  *                  2..5 = lane groups: one ray per 32 (2), 4 (3), 8 (4) or 16 (5) lanes,
  *                  each group taking that many consecutive samples per step;
  *                  6 = split render: one lane per ray sets the ray up and leaps to its
- *                  first sample that may be non-zero, then groups of 16 lanes drawn from the
+ *                  first sample in an occupied brick, then groups of 16 lanes drawn from the
  *                  whole device finish the queued rays (the context keeps a queue of 112
  *                  bytes per pixel for each stream it renders on).
  *                  All kernels compute the same method; images agree within float
@@ -276,7 +276,7 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
  * function, camera and image size share one persistent launch. Requests are appended to a
  * device FIFO while the kernel runs (a copy stream publishes them). Its warps take work from
  * the oldest unfinished requests: 8 x 4 pixel tiles, whose rays are set up and leap to their
- * first sample that may be non-zero, then the request's queued rays, finished by groups of 16
+ * first sample in an occupied brick, then the request's queued rays, finished by groups of 16
  * lanes -- the split render of vrc_render (kernel 0 or 6) -- or, with params->kernel 1,
  * tiles rendered to the end one ray per thread. Every image therefore equals the vrc_render
  * image of the same request and kernel bit for bit. Work of successive requests overlaps on

@@ -52,7 +52,10 @@ __device__ __forceinline__ void render_ray_tile(const RenderLaunch &L, int tile)
     const ReplView rep = L.rep;
     const int gn[3] = {L.grid.n[0], L.grid.n[1], L.grid.n[2]};
     const TfView tfv = L.tf;
-    const uint32_t *cells = L.cells;
+    // the first phase of the split render queues a ray at its first sample in an occupied
+    // brick and leaves clear cells to the second phase, whose 16 lanes test 16 samples at a
+    // time (testing them here, one per lane and warp step, was 1.5% slower per frame)
+    const uint32_t *cells = SPLIT ? nullptr : L.cells;
     const int cwx = L.cwx;
 
     // output pixel; in an ordered pass over pieces (L.accum) the ray continues the colour and

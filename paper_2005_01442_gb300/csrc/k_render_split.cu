@@ -8,7 +8,7 @@
 //
 // 1. the per-ray body (k_ray_tile.cuh, SPLIT) sets every ray up with one lane, leaps over
 //    empty bricks and composites samples 0 .. SPLIT_J0 - 1; rays that never reach a sample
-//    that may be non-zero are written out, the others are appended to a queue with their
+//    in an occupied brick are written out, the others are appended to a queue with their
 //    colour and transmittance so far and the index of that sample;
 // 2. a grid sized to fill the device drains the queue, each group of SPLIT_G lanes claiming
 //    one ray at a time and finishing it with group_march (k_group.cuh): blocks of SPLIT_G

@@ -337,8 +337,8 @@ __device__ __forceinline__ int octant_of(const float df[3]) {
 // every ray with one lane and hands rays that go on to a queue; the second phase finishes
 // each queued ray with SPLIT_G lanes (blocks of SPLIT_G consecutive samples composited by a
 // scan), so no ray's cost rests on one lane. With SPLIT_J0 = 0 (the measured best on the
-// 512^2 x 400 CT) the first phase only sets rays up and leaps each to its first sample that
-// may be non-zero. SPLIT_G = 16 at four CTAs per SM measured best on that CT (8 lanes: 1.4%
+// 512^2 x 400 CT) the first phase only sets rays up and leaps each to its first sample in an
+// occupied brick. SPLIT_G = 16 at four CTAs per SM measured best on that CT (8 lanes: 1.4%
 // slower, 32 lanes 12% slower, 4 lanes 25% slower).
 constexpr int SPLIT_G = 16;
 constexpr int SPLIT_J0 = 0;  // a multiple of SPLIT_G
