@@ -268,12 +268,15 @@ def roofline(executed: int, resampled: int, launch_ms: float, peaks: dict, kerne
 SERVE_SIZES = [(512, 512), (1024, 1024), (2048, 2048)]
 SERVE_HBM_BUDGET = 8 << 30  # device bytes of the requests in flight (images + ray queues)
 SERVE_P99_CAP_MS = 33.0     # latency cap of the rate sweep: one frame at 30 frames/s
+# one launch per request; one persistent launch whose warps render (mode 0); one persistent
+# scheduler launch that starts each request's render on the device (mode 1)
+SERVE_KINDS = ("plain", "batched", "launching")
 
 
 def serve_bench(R, torch, vols, tids, runs, brick, seed, p99_cap_ms=SERVE_P99_CAP_MS):
     """Open-loop Poisson load (seeded) of mixed volumes, transfer functions, orbit cameras and
-    image sizes, replayed against the one-launch-per-request server and the persistent
-    batched server for each (offered rate, seconds, warm-up seconds) run; admission by an HBM
+    image sizes, replayed against the one-launch-per-request server and the two persistent
+    batched servers (SERVE_KINDS) for each (offered rate, seconds, warm-up seconds) run; admission by an HBM
     budget for the requests in flight. For each server, `best_at_p99_cap` is the highest
     images/s of a run whose p99 latency stays under the cap."""
     from paper_2005_01442_gb300 import serve, synth
@@ -291,9 +294,9 @@ def serve_bench(R, torch, vols, tids, runs, brick, seed, p99_cap_ms=SERVE_P99_CA
     for rate, seconds, warm in runs:
         reqs = serve.poisson_requests(seed, rate, seconds + warm, list(vols), tids,
                                       SERVE_SIZES, cam_fn, brick=brick)
-        for kind in ("plain", "batched"):
-            srv = serve.BatchedServer(R, max_slots=1024) if kind == "batched" else \
-                serve.PlainServer(R)
+        for kind in SERVE_KINDS:
+            srv = serve.PlainServer(R) if kind == "plain" else \
+                serve.BatchedServer(R, max_slots=1024, mode=1 if kind == "launching" else 0)
             budget = serve.ImageBudget(SERVE_HBM_BUDGET, lambda h, w: torch.empty(
                 (h, w, 4), dtype=torch.float32, device="cuda"), srv.extra_bytes_per_pixel)
             res = serve.run_open_loop(srv, reqs, budget, warmup=warm)
@@ -305,16 +308,17 @@ def serve_bench(R, torch, vols, tids, runs, brick, seed, p99_cap_ms=SERVE_P99_CA
             res["warmup_s"] = warm
             out["runs"].append(res)
     best = {}
-    for kind in ("plain", "batched"):
+    for kind in SERVE_KINDS:
         ok = [r for r in out["runs"] if r["server"] == kind and r["p99_ms"] <= p99_cap_ms]
         top = max(ok, key=lambda r: r["images_per_s"]) if ok else None
         best[kind] = ({"images_per_s": top["images_per_s"], "p99_ms": top["p99_ms"],
                        "p50_ms": top["p50_ms"], "offered_rate": top["offered_rate"]}
                       if top else None)
     out["best_at_p99_cap"] = best
-    if best["plain"] and best["batched"]:
-        out["batched_over_plain_at_p99_cap"] = (best["batched"]["images_per_s"] /
-                                                best["plain"]["images_per_s"])
+    for kind in SERVE_KINDS[1:]:
+        if best["plain"] and best[kind]:
+            out[f"{kind}_over_plain_at_p99_cap"] = (best[kind]["images_per_s"] /
+                                                    best["plain"]["images_per_s"])
     return out
 
 

@@ -287,6 +287,17 @@ vrc_status vrc_render_backward(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_ca
 typedef struct vrc_server vrc_server;
 /* Creates a server on ctx with max_slots requests in flight at most (1..65536). */
 vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **server_out);
+/* vrc_server_create with a choice of how the persistent launch renders (the same FIFO, slots,
+ * submit/pump/poll protocol and bounded waits in both modes):
+ *   mode 0: the persistent kernel's own warps render the requests (as above);
+ *   mode 1: the persistent launch is one scheduler thread that starts each request's split
+ *           render on the device as it arrives (dynamic parallelism: its first phase into the
+ *           fire-and-forget stream, the second as that grid's tail launch), so requests run
+ *           side by side in the plain kernels of vrc_render with the launch record as a kernel
+ *           parameter. params->kernel 0 or 6 only (1: VRC_ERR_ARG). Images equal vrc_render's
+ *           bit for bit.
+ * Other modes: VRC_ERR_ARG. */
+vrc_status vrc_server_create_ex(vrc_ctx *ctx, int max_slots, int mode, vrc_server **server_out);
 /* Queues one render into out_rgba_dev (caller-owned, height x width x 4 floats, 16-byte
  * aligned, untouched by the caller until completion). Returns a ticket for vrc_server_poll.
  * Brick tables for params->brick must exist; the first request of a (volume, transfer

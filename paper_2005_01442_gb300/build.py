@@ -24,6 +24,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # every fused multiply-add in the kernels is written out with fmaf.
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I",
               INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+# Units with device-side kernel launches: relocatable device code, linked on the device with
+# the device runtime (cudadevrt) before the shared library is linked.
+RDC_UNITS = {"k_serve_dl.cu"}
 
 
 def nvcc() -> str:
@@ -50,7 +53,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
-            jobs.append([cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", s, "-o", o])
+            rdc = ["-rdc=true"] if os.path.basename(s) in RDC_UNITS else []
+            jobs.append([cc, *ARCH, *NVCC_FLAGS, *rdc, *extra_flags, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -62,8 +66,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
+        rdc_objs = [o for s, o in zip(srcs, objs) if os.path.basename(s) in RDC_UNITS]
+        dlink = os.path.join(BUILD, "device_link.o")
+        run([cc, *ARCH, "-Xcompiler", "-fPIC", "-dlink", *rdc_objs, "-o", dlink, "-lcudadevrt"])
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+        run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, dlink, "-lcudadevrt"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -1393,6 +1393,8 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
 struct vrc_server {
     vrc_ctx *ctx = nullptr;
     int max_slots = 0, cap = 0, ctas = 0;
+    int mode = 0;       // 0: persistent bodies (k_serve.cu); 1: device-side launches (k_serve_dl.cu)
+    int tail_ctas = 0;  // mode 1: CTAs of a request's second phase
     ServeSlot *d_slots = nullptr;
     ServeEntry *d_queue = nullptr;
     ServeCtl *d_ctl = nullptr;
@@ -1476,15 +1478,22 @@ cudaError_t server_take_region(vrc_server *s, size_t bytes, void **out, size_t *
 }  // namespace
 
 extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server **out) {
+    return vrc_server_create_ex(ctx, max_slots, 0, out);
+}
+
+extern "C" vrc_status vrc_server_create_ex(vrc_ctx *ctx, int max_slots, int mode,
+                                           vrc_server **out) {
     if (!ctx) return VRC_ERR_ARG;
     if (!out) return fail(ctx, VRC_ERR_ARG, "out is NULL");
     if (max_slots < 1 || max_slots > 65536) return fail(ctx, VRC_ERR_ARG, "max_slots must be 1..65536");
+    if (mode != 0 && mode != 1) return fail(ctx, VRC_ERR_ARG, "mode must be 0 or 1");
     *out = nullptr;
     DeviceGuard g(ctx->device);
     vrc_server *s = new (std::nothrow) vrc_server();
     if (!s) return fail(ctx, VRC_ERR_OOM, "server allocation failed");
     s->ctx = ctx;
     s->max_slots = max_slots;
+    s->mode = mode;
     s->cap = 4 * max_slots;
     s->slot_seq.assign(max_slots, -1);
     s->region.assign(max_slots, nullptr);
@@ -1516,6 +1525,15 @@ extern "C" vrc_status vrc_server_create(vrc_ctx *ctx, int max_slots, vrc_server 
         int sms = 0;
         ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
         s->ctas = sms;  // the launches size their grids per SM
+        if (mode == 1) {
+            s->tail_ctas = serve_dl_tail_ctas(e);
+            // two device-side launches per request in flight, and the scheduler's own
+            size_t pending = 0;
+            ck(cudaDeviceGetLimit(&pending, cudaLimitDevRuntimePendingLaunchCount));
+            const size_t need = 2 * (size_t)max_slots + 64;
+            if (e == cudaSuccess && pending < need)
+                ck(cudaDeviceSetLimit(cudaLimitDevRuntimePendingLaunchCount, need));
+        }
         ck(cudaDeviceSynchronize());
     }
     if (e != cudaSuccess) {
@@ -1539,6 +1557,8 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     if (params->kernel != 0 && params->kernel != 1 && params->kernel != 6)
         return fail(ctx, VRC_ERR_ARG, "the server renders with the split render (kernel 0 or 6) "
                                       "or the per-ray kernel (1)");
+    if (s->mode == 1 && params->kernel == 1)
+        return fail(ctx, VRC_ERR_ARG, "a launching server renders with the split render only");
     if (params->interp || params->preclass || params->shade || params->preint)
         return fail(ctx, VRC_ERR_ARG, "the server renders the default variant only");
     DeviceGuard g(ctx->device);
@@ -1573,6 +1593,11 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     }
     rec.L.out = (float4 *)out_rgba_dev;
     rec.L.counters = nullptr;
+    if (s->mode == 1) {  // the second phase's CTAs count themselves in p1_done (zeroed below)
+        rec.L.tail_ctas = s->tail_ctas;
+        rec.L.done_ctr = &s->d_slots[slot].p1_done;
+        rec.L.done_flag = &s->d_done[slot];
+    }
     rec.ntiles = ((cam->width + 7) / 8) * ((cam->height + 3) / 4);
     {
         // a stride near ntiles / golden ratio, made coprime to ntiles
@@ -1585,6 +1610,7 @@ extern "C" vrc_status vrc_server_submit(vrc_server *s, int vol_id, int tf_id,
     const long long seq = s->next_seq++;
     const unsigned useq = (unsigned)(seq & 0x7fffffff);
     rec.seq = (int)useq;
+    rec.L.done_seq = (int)useq;
     rec.state = 0;
     memset(rec.qhead, 0, sizeof(rec.qhead));
     rec.p1_rem = 0;  // nothing to claim until the record is complete on the device
@@ -1638,9 +1664,14 @@ extern "C" vrc_status vrc_server_pump(vrc_server *s, long long budget_ns, long l
             CK(cudaStreamSynchronize(s->s_ctl), "server publish");
             CK(cudaMemsetAsync(&s->d_ctl->leaving, 0, sizeof(int), s->s_ctl), "serve launch");
             CK(cudaStreamSynchronize(s->s_ctl), "serve launch");
-            CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
-                            (unsigned long long)budget_ns, (unsigned long long)idle_ns, s->ctas,
-                            s->s_run), "serve launch");
+            if (s->mode == 1)
+                CK(launch_serve_dl(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_front,
+                                   (unsigned long long)budget_ns, (unsigned long long)idle_ns,
+                                   s->s_run), "serve launch");
+            else
+                CK(launch_serve(s->d_slots, s->d_queue, s->cap, s->d_ctl, s->d_done, s->d_front,
+                                (unsigned long long)budget_ns, (unsigned long long)idle_ns,
+                                s->ctas, s->s_run), "serve launch");
             CK(cudaEventRecord(s->ev_run, s->s_run), "serve launch");
             CK(cudaEventRecord(s->ev_run1, s->s_run), "serve launch");
             s->launched = true;

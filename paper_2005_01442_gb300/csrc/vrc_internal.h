@@ -414,6 +414,12 @@ struct RenderLaunch {
     float *ckpt;
     int ckpt_K, ckpt_seg;
     const void *tma_map;  // host address of the volume's tensor map (kernel 7; launcher only)
+    // serving by device-side launches (k_serve_dl.cu): the second phase's grid, and where its
+    // CTAs count themselves and the last one announces the request's completion (NULL: none)
+    int tail_ctas;
+    int *done_ctr;
+    int *done_flag;
+    int done_seq;
 };
 
 // Checkpoint state of one ray while it is composited (reverse-mode checkpoints).
@@ -591,5 +597,12 @@ cudaError_t launch_serve(ServeSlot *slots, const ServeEntry *queue, int cap, Ser
                          int *done_flags, unsigned long long *front_mirror,
                          unsigned long long budget_ns, unsigned long long idle_ns, int sms,
                          cudaStream_t st);
+// Serving by device-side launches: one scheduler thread launches each request's split render
+// (both phases, plain kernels whose launch record is a kernel parameter) as it arrives.
+cudaError_t launch_serve_dl(ServeSlot *slots, const ServeEntry *queue, int cap, ServeCtl *ctl,
+                            unsigned long long *front_mirror, unsigned long long budget_ns,
+                            unsigned long long idle_ns, cudaStream_t stream);
+// CTAs of a device-launched second phase (fills the device; cached per device).
+int serve_dl_tail_ctas(cudaError_t &e);
 
 }  // namespace vrc

@@ -29,7 +29,7 @@ EXPORTS = [
     "vrc_last_error_message", "vrc_status_str", "vrc_version", "vrc_aabbs_get",
     "vrc_pieces_build", "vrc_pieces_get", "vrc_pieces_free", "vrc_grid_order", "vrc_box_rect",
     "vrc_render_piece", "vrc_composite", "vrc_render_sortlast", "vrc_render_ordered",
-    "vrc_render_host_batch", "vrc_ckpt_bytes", "vrc_microbench",
+    "vrc_render_host_batch", "vrc_ckpt_bytes", "vrc_microbench", "vrc_server_create_ex",
 ]
 
 
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = False):
     L.vrc_render_backward.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params),
                                       vp, vp, vp, vp, vp]
     L.vrc_server_create.argtypes = [vp, ip, C.POINTER(vp)]
+    L.vrc_server_create_ex.argtypes = [vp, ip, ip, C.POINTER(vp)]
     L.vrc_server_submit.argtypes = [vp, ip, ip, C.POINTER(vrc_camera), C.POINTER(vrc_params), vp,
                                     C.POINTER(C.c_longlong)]
     L.vrc_server_pump.argtypes = [vp, C.c_longlong, C.c_longlong, pint]

@@ -93,20 +93,22 @@ class ImageBudget:
 
 
 class BatchedServer:
-    """Continuous batching on the persistent serving kernel (vrc_server_*)."""
-
-    name = "batched"
+    """Continuous batching on one persistent launch (vrc_server_*). mode 0: the persistent
+    kernel's warps render the requests; mode 1 ("launching"): a persistent scheduler starts
+    each request's split render on the device as it arrives (split render only)."""
 
     def __init__(self, renderer, max_slots: int = 1024, budget_ms: float = 250.0,
-                 idle_ms: float = 5.0, kernel: int = 0):
+                 idle_ms: float = 5.0, kernel: int = 0, mode: int = 0):
         self.R = renderer
         self.lib = renderer.lib
         self.kernel = int(kernel)
+        self.mode = int(mode)
+        self.name = "launching" if self.mode == 1 else "batched"
         # device bytes a request holds per pixel besides its image: its ray queue
         self.extra_bytes_per_pixel = 0 if self.kernel == 1 else 112
         ptr = C.c_void_p()
-        native.check(renderer.ctx, self.lib.vrc_server_create(renderer.ctx, int(max_slots),
-                                                              C.byref(ptr)))
+        native.check(renderer.ctx, self.lib.vrc_server_create_ex(
+            renderer.ctx, int(max_slots), self.mode, C.byref(ptr)))
         self.srv = ptr
         self.budget_ns = int(budget_ms * 1e6)
         self.idle_ns = int(idle_ms * 1e6)

@@ -43,7 +43,8 @@ def test_roofline_terms_and_binding_term():
 def test_serve_sweep_summary(monkeypatch):
     from paper_2005_01442_gb300 import serve
     results = {("plain", 200.0): (190.0, 12.0), ("batched", 200.0): (195.0, 10.0),
-               ("plain", 800.0): (600.0, 80.0), ("batched", 800.0): (780.0, 30.0)}
+               ("plain", 800.0): (600.0, 80.0), ("batched", 800.0): (780.0, 30.0),
+               ("launching", 200.0): (200.0, 8.0), ("launching", 800.0): (790.0, 40.0)}
 
     class Srv:
         extra_bytes_per_pixel = 0
@@ -54,7 +55,8 @@ def test_serve_sweep_summary(monkeypatch):
         def close(self):
             pass
 
-    monkeypatch.setattr(serve, "BatchedServer", lambda R, max_slots: Srv("batched"))
+    monkeypatch.setattr(serve, "BatchedServer", lambda R, max_slots, mode=0:
+                        Srv("launching" if mode == 1 else "batched"))
     monkeypatch.setattr(serve, "PlainServer", lambda R: Srv("plain"))
     monkeypatch.setattr(serve, "poisson_requests", lambda *a, **k: [a[1]])
 
@@ -70,4 +72,6 @@ def test_serve_sweep_summary(monkeypatch):
     assert out["best_at_p99_cap"]["plain"]["images_per_s"] == 190.0  # 800/s broke the cap
     assert out["best_at_p99_cap"]["batched"]["images_per_s"] == 780.0
     assert out["batched_over_plain_at_p99_cap"] == pytest.approx(780.0 / 190.0)
-    assert len(out["runs"]) == 4
+    assert out["best_at_p99_cap"]["launching"]["images_per_s"] == 200.0  # 800/s broke the cap
+    assert out["launching_over_plain_at_p99_cap"] == pytest.approx(200.0 / 190.0)
+    assert len(out["runs"]) == 6

@@ -54,11 +54,12 @@ def _requests(vids, tids, dims, n, seed):
     return out
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
-def test_batched_images_equal_alone(env, kernel):
+@pytest.mark.parametrize("kernel,mode", [(0, 0), (1, 0), (0, 1)])
+def test_batched_images_equal_alone(env, kernel, mode):
     torch, R, vids, tids, dims = env
     from paper_2005_01442_gb300 import serve
-    srv = serve.BatchedServer(R, max_slots=64, budget_ms=200.0, idle_ms=5.0, kernel=kernel)
+    srv = serve.BatchedServer(R, max_slots=64, budget_ms=200.0, idle_ms=5.0, kernel=kernel,
+                              mode=mode)
     reqs = _requests(vids, tids, dims, 48, 1)
     outs, handles = [], []
     for r in reqs:  # all submitted back to back: they share the persistent launch
@@ -80,14 +81,15 @@ def test_batched_images_equal_alone(env, kernel):
     srv.close()
 
 
-def test_slots_reused_back_to_back(env):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_slots_reused_back_to_back(env, mode):
     """One slot, many requests submitted back to back into the running kernel: every slot
     reuse must leave the next request complete (no claim may land on a reused slot) and its
     image equal to the render alone."""
     torch, R, vids, tids, dims = env
     from paper_2005_01442_gb300 import serve
     import time
-    srv = serve.BatchedServer(R, max_slots=1, budget_ms=2000.0, idle_ms=50.0)
+    srv = serve.BatchedServer(R, max_slots=1, budget_ms=2000.0, idle_ms=50.0, mode=mode)
     reqs = _requests(vids, tids, dims, 40, 5)
     t0 = time.time()
     for r in reqs:
@@ -104,7 +106,8 @@ def test_slots_reused_back_to_back(env):
     srv.close()
 
 
-def test_served_images_match_the_oracle(env, host_vols, orc):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_served_images_match_the_oracle(env, host_vols, orc, mode):
     """A mixed batch served by one persistent launch -- CT volumes of three sizes, images of
     96 x 80 and 160 x 128, two transfer functions, with and without leaping and early
     termination -- against the FP64 oracle on 1024 seeded pixels of every image: within 1e-4
@@ -122,7 +125,7 @@ def test_served_images_match_the_oracle(env, host_vols, orc):
         cam = synth.orbit_camera(int(rng.integers(1 << 30)), dims[v], w, h)
         reqs.append(serve.Request(0.0, v, [tids[0], tids[2]][k % 2], cam,
                                   ert=[1.0, 0.999][(k // 2) % 2], brick=[0, 8][(k // 6) % 2]))
-    srv = serve.BatchedServer(R, max_slots=16, budget_ms=200.0, idle_ms=5.0)
+    srv = serve.BatchedServer(R, max_slots=16, budget_ms=200.0, idle_ms=5.0, mode=mode)
     outs = [torch.full((r.cam.height, r.cam.width, 4), float("nan"), device="cuda") for r in reqs]
     handles = [srv.submit(r, o) for r, o in zip(reqs, outs)]
     pending = set(range(len(reqs)))
@@ -147,11 +150,12 @@ def test_served_images_match_the_oracle(env, host_vols, orc):
         assert d[flagged].max(initial=0.0) <= 1e-3
 
 
-def test_kernel_leaves_when_idle_and_relaunches(env):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_kernel_leaves_when_idle_and_relaunches(env, mode):
     torch, R, vids, tids, dims = env
     from paper_2005_01442_gb300 import serve
     import time
-    srv = serve.BatchedServer(R, max_slots=8, budget_ms=1000.0, idle_ms=2.0)
+    srv = serve.BatchedServer(R, max_slots=8, budget_ms=1000.0, idle_ms=2.0, mode=mode)
     assert srv.pump() is False  # nothing pending: no launch
     for round_ in range(3):
         r = _requests(vids, tids, dims, 1, 10 + round_)[0]
@@ -170,7 +174,7 @@ def test_kernel_leaves_when_idle_and_relaunches(env):
     srv.close()
 
 
-@pytest.mark.parametrize("kind", ["batched", "plain"])
+@pytest.mark.parametrize("kind", ["batched", "launching", "plain"])
 def test_open_loop_run(env, kind):
     torch, R, vids, tids, dims = env
     from paper_2005_01442_gb300 import serve
@@ -179,7 +183,8 @@ def test_open_loop_run(env, kind):
     t = np.cumsum(rng.exponential(1 / 300.0, len(reqs)))
     for r, a in zip(reqs, t):
         r.arrival = float(a)
-    srv = serve.BatchedServer(R, max_slots=32) if kind == "batched" else serve.PlainServer(R)
+    srv = serve.PlainServer(R) if kind == "plain" else \
+        serve.BatchedServer(R, max_slots=32, mode=1 if kind == "launching" else 0)
     budget = serve.ImageBudget(8 << 20, lambda h, w: torch.empty((h, w, 4), device="cuda"),
                                srv.extra_bytes_per_pixel)
     res = serve.run_open_loop(srv, reqs, budget, warmup=0.02)
@@ -187,3 +192,14 @@ def test_open_loop_run(env, kind):
     assert res["requests"] > 0 and len(res["latencies_s"]) == res["requests"]
     assert res["p50_ms"] > 0 and res["p99_ms"] >= res["p50_ms"]
     assert budget.used == 0
+
+
+def test_launching_server_renders_the_split_render_only(env):
+    torch, R, vids, tids, dims = env
+    from paper_2005_01442_gb300 import native, serve
+    srv = serve.BatchedServer(R, max_slots=4, mode=1, kernel=1)
+    r = _requests(vids, tids, dims, 1, 3)[0]
+    o = torch.empty((r.cam.height, r.cam.width, 4), device="cuda")
+    with pytest.raises(native.VrcError):
+        srv.submit(r, o)
+    srv.close()
