@@ -521,7 +521,7 @@ def main():
             # 1024^2 / 2048^2 images; the nominal 200 req/s stream, then a rate sweep
             vols = serve_volumes(R, synth, B, resident=(vid, dims) if args.tf == "ct" else None)
             tids = [R.set_tf(synth.tf_ct(k), synth.CT_LO, synth.CT_HI) for k in (None, 1, 2, 3)]
-            sweep = [(r, 4.0, 1.0) for r in (400.0, 800.0, 1200.0, 1600.0)]
+            sweep = [(r, 4.0, 1.0) for r in (400.0, 800.0, 1200.0, 1400.0, 1600.0)]
             sampler.rows_clear()  # clock record of the serving runs
             sampler.mark(True)
             line["serving"] = serve_bench(R, torch, vols, tids,
@@ -677,7 +677,7 @@ def run_mode(args, torch, R, synth):
         _mark(True)
         res = serve_bench(R, torch, vols, tids,
                           [(200.0, 60.0, 5.0)] + [(r, 10.0, 2.0) for r in
-                                                  (400.0, 800.0, 1200.0, 1600.0, 2000.0)],
+                                                  (400.0, 800.0, 1200.0, 1400.0, 1600.0, 2000.0)],
                           args.brick, seed=5)
         _mark(False)
         print(json.dumps({"mode": "serve", "metric": "p50/p99 request latency (ms) and images/s",

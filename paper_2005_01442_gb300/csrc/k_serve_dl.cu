@@ -4,7 +4,7 @@
 // persistent serving kernel (k_serve.cu) and starts each request's split render on the device
 // as soon as it is published:
 //
-//   scheduler (one thread, persistent): for every new queue entry, launch the request's first
+//   scheduler (one warp, persistent): for every new queue entry, launch the request's first
 //       phase into the fire-and-forget stream -- requests run side by side, each grid as
 //       soon as SMs free up -- with the request's launch record as the kernel parameter;
 //   first phase (dl_head_kernel): the split render's first phase; its first thread also
@@ -64,59 +64,89 @@ __device__ __forceinline__ T dl_volatile(const T *p) {
     return *(const volatile T *)p;
 }
 
-// One thread. Entries from the front on are launched in order; an entry whose slot already
-// holds a later request (impossible while the host reuses slots only after completion) is
-// passed over.
-__global__ void serve_dl_kernel(ServeSlot *slots, const ServeEntry *queue, int cap,
-                                ServeCtl *ctl, unsigned long long *front_mirror,
-                                unsigned long long budget_ns, unsigned long long idle_ns) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One warp: lane 0 takes every decision; the warp copies a request's launch record into
+// shared memory, from which lane 0 launches it. Entries from the front on are launched in
+// order; an entry whose slot already holds a later request (impossible while the host reuses
+// slots only after completion) is passed over.
+__global__ void __launch_bounds__(32) serve_dl_kernel(ServeSlot *slots, const ServeEntry *queue,
+                                                      int cap, ServeCtl *ctl,
+                                                      unsigned long long *front_mirror,
+                                                      unsigned long long budget_ns,
+                                                      unsigned long long idle_ns) {
+    __shared__ RenderLaunch s_L;
+    if (blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     const unsigned long long start = dl_global_ns();
     unsigned long long idle_since = 0;
-    unsigned sleep_ns = 256;
+    unsigned sleep_ns = 128;
     while (true) {
-        const unsigned long long now = dl_global_ns();
-        if (dl_volatile(&ctl->stop) || dl_volatile(&ctl->leaving)) break;
-        if (now - start > budget_ns) {
-            atomicExch(&ctl->leaving, 1);
-            break;
-        }
-        const unsigned long long f = dl_volatile(&ctl->front);
-        const unsigned long long t = dl_volatile(&ctl->tail);
-        if (f >= t) {  // nothing published: bounded idle wait
-            if (idle_since == 0) idle_since = now;
-            if (now - idle_since > idle_ns) {
+        // action: 0 leave, 1 wait, 2 pass the entry over, 3 launch it
+        int action = 0, es = 0;
+        unsigned long long f = 0;
+        if (lane == 0) {
+            const unsigned long long now = dl_global_ns();
+            if (dl_volatile(&ctl->stop) || dl_volatile(&ctl->leaving)) {
+                action = 0;
+            } else if (now - start > budget_ns) {
                 atomicExch(&ctl->leaving, 1);
-                break;
+                action = 0;
+            } else {
+                f = dl_volatile(&ctl->front);
+                const unsigned long long t = dl_volatile(&ctl->tail);
+                if (f >= t) {  // nothing published: bounded idle wait
+                    if (idle_since == 0) idle_since = now;
+                    if (now - idle_since > idle_ns) {
+                        atomicExch(&ctl->leaving, 1);
+                        action = 0;
+                    } else {
+                        action = 1;
+                    }
+                } else {
+                    idle_since = 0;
+                    const ServeEntry *e = &queue[f % cap];
+                    es = __ldcg(&e->slot);
+                    const int eq = __ldcg(&e->seq);
+                    const ServeSlot *S = slots + es;
+                    action = dl_volatile(&S->seq) == eq && dl_volatile(&S->state) == 0 ? 3 : 2;
+                }
             }
+        }
+        action = __shfl_sync(0xffffffffu, action, 0);
+        if (action == 0) break;
+        if (action == 1) {
             __nanosleep(sleep_ns);
-            sleep_ns = min(sleep_ns * 2u, 32768u);
+            sleep_ns = min(sleep_ns * 2u, 8192u);
             continue;
         }
-        idle_since = 0;
-        sleep_ns = 256;
-        const ServeEntry *e = &queue[f % cap];
-        const int es = __ldcg(&e->slot);
-        const int eq = __ldcg(&e->seq);
-        ServeSlot *S = slots + es;
-        if (dl_volatile(&S->seq) == eq && dl_volatile(&S->state) == 0) {
-            RenderLaunch L;
-            const int *src = (const int *)&S->L;
-            int *dst = (int *)&L;
-            for (int i = 0; i < (int)(sizeof(RenderLaunch) / sizeof(int)); ++i)
+        sleep_ns = 128;
+        if (action == 3) {
+            es = __shfl_sync(0xffffffffu, es, 0);
+            const int *src = (const int *)&slots[es].L;
+            int *dst = (int *)&s_L;
+            for (int i = lane; i < (int)(sizeof(RenderLaunch) / sizeof(int)); i += 32)
                 dst[i] = __ldcg(src + i);
-            const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
-            const unsigned grid = (unsigned)((tiles + SPLIT_RAY_WARPS - 1) / SPLIT_RAY_WARPS);
-            if (L.dist)
-                dl_head_kernel<true><<<grid, 32 * SPLIT_RAY_WARPS, 0, cudaStreamFireAndForget>>>(L);
-            else
-                dl_head_kernel<false><<<grid, 32 * SPLIT_RAY_WARPS, 0, cudaStreamFireAndForget>>>(L);
-            if (cudaGetLastError() != cudaSuccess) atomicExch(L.err, VRC_ERR_CUDA);
-            atomicExch(&S->state, 1);
+            __syncwarp();
+            if (lane == 0) {
+                const RenderLaunch L = s_L;
+                const long tiles = (long)((L.cam.width + 7) / 8) * ((L.cam.height + 3) / 4);
+                const unsigned grid = (unsigned)((tiles + SPLIT_RAY_WARPS - 1) / SPLIT_RAY_WARPS);
+                if (L.dist)
+                    dl_head_kernel<true>
+                        <<<grid, 32 * SPLIT_RAY_WARPS, 0, cudaStreamFireAndForget>>>(L);
+                else
+                    dl_head_kernel<false>
+                        <<<grid, 32 * SPLIT_RAY_WARPS, 0, cudaStreamFireAndForget>>>(L);
+                if (cudaGetLastError() != cudaSuccess) atomicExch(L.err, VRC_ERR_CUDA);
+                atomicExch(&slots[es].state, 1);
+            }
+            __syncwarp();
         }
-        ctl->front = f + 1;
-        *(volatile unsigned long long *)front_mirror = f + 1;
-        __threadfence_system();
+        if (lane == 0) {
+            ctl->front = f + 1;
+            *(volatile unsigned long long *)front_mirror = f + 1;
+            __threadfence_system();
+        }
+        __syncwarp();
     }
 }
 
