@@ -5,6 +5,10 @@
 // per axis and stores min/max over its apron box [bB-1, bB+B+1] clamped to the volume, the
 // overlap a cubic kernel reads. The occupancy of a brick under a transfer function is the
 // integer decision "is any table opacity > 0 on the brick's value range", taken in float32.
+#include <string.h>
+
+#include <type_traits>
+
 #include "vrc_internal.h"
 
 namespace vrc {
@@ -113,16 +117,47 @@ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
-// One CTA per brick row (by, bz): thread x handles brick bx (64 at a time) and sweeps the x
-// apron [bx*B-1, bx*B+B+1] of every row of the (y, z) apron, thread y interleaves those rows;
-// partial min/max are combined through shared memory. Each voxel is read from HBM about once
-// (neighbouring rows of bricks re-read the overlap through L2). Exact for every dtype.
+// Min/max of one row of brick bx's apron, x in [bx*B - 1, bx*B + B + 1]: the padded row's
+// elements bx*B + 1 .. bx*B + B + 3. The pad replicates the edge voxels (also in the rounding
+// of pnx), so reading past either edge adds only edge voxels already in the clamped apron;
+// reads are clamped to the row. The span from padded index bx*B (16-byte aligned for 2-byte
+// voxels of B = 8, and for float) is read with 8- or 16-byte loads when it fits the row.
+template <typename T, int B>
+__device__ __forceinline__ void apron_row(const T *__restrict__ row, int bx, int pnx, T &lo,
+                                          T &hi) {
+    constexpr int SPAN = B + 4;
+    using V = typename std::conditional<sizeof(T) == 2, uint2, uint4>::type;
+    constexpr int PER = (int)(sizeof(V) / sizeof(T));  // elements per vector load
+    static_assert(SPAN % PER == 0, "span must be a whole number of vector loads");
+    T v[SPAN];
+    const int i0 = bx * B;
+    if (i0 + SPAN <= pnx) {
+        const V *p = reinterpret_cast<const V *>(row + i0);
+#pragma unroll
+        for (int k = 0; k < SPAN / PER; ++k) {
+            const V w = __ldg(p + k);
+            memcpy(&v[k * PER], &w, sizeof(V));
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < SPAN; ++e) v[e] = row[min(i0 + e, pnx - 1)];
+    }
+#pragma unroll
+    for (int e = 1; e < SPAN; ++e) {
+        lo = tmin(lo, v[e]);
+        hi = tmax(hi, v[e]);
+    }
+}
+
+// One CTA per brick row (by, bz): thread x handles brick bx (64 at a time) and sweeps the
+// rows of the (y, z) apron, thread y interleaves those rows; partial min/max are combined
+// through shared memory. Each voxel is read from HBM about once (neighbouring rows of bricks
+// re-read the overlap through L2). Exact for every dtype.
 constexpr int BM_TX = 64, BM_TY = 4;
 
-template <typename T>
-__global__ void __launch_bounds__(BM_TX *BM_TY) brick_minmax_kernel(VolView v, int B, int nbx,
-                                                                     int nby, int nbz,
-                                                                     T *__restrict__ mn,
+template <typename T, int B>
+__global__ void __launch_bounds__(BM_TX *BM_TY) brick_minmax_kernel(VolView v, int nbx, int nby,
+                                                                     int nbz, T *__restrict__ mn,
                                                                      T *__restrict__ mx) {
     __shared__ T s_lo[BM_TY][BM_TX], s_hi[BM_TY][BM_TX];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -136,15 +171,10 @@ __global__ void __launch_bounds__(BM_TX *BM_TY) brick_minmax_kernel(VolView v, i
         const int bx = bx0 + tx;
         T lo = Lim<T>::hi(), hi = Lim<T>::lo();
         if (bx < nbx) {
-            const int x0 = max(bx * B - 1, 0), x1 = min(bx * B + B + 1, v.n[0] - 1);
             for (int r = ty; r < rows; r += BM_TY) {
                 const int y = y0 + r % wy, z = z0 + r / wy;
-                const T *row = base + ((long)(z + PAD) * v.pny + (y + PAD)) * v.pnx + PAD;
-                for (int x = x0; x <= x1; ++x) {
-                    const T val = row[x];
-                    lo = tmin(lo, val);
-                    hi = tmax(hi, val);
-                }
+                apron_row<T, B>(base + ((long)(z + PAD) * v.pny + (y + PAD)) * v.pnx, bx, v.pnx,
+                                lo, hi);
             }
         }
         s_lo[ty][tx] = lo;
@@ -164,23 +194,26 @@ __global__ void __launch_bounds__(BM_TX *BM_TY) brick_minmax_kernel(VolView v, i
     }
 }
 
+template <typename T>
+void launch_minmax_t(const VolView &v, int B, const int nb[3], void *mn, void *mx,
+                     cudaStream_t st) {
+    const unsigned blocks = (unsigned)nb[1] * (unsigned)nb[2];
+    const dim3 threads(BM_TX, BM_TY);
+    if (B == 16)
+        brick_minmax_kernel<T, 16><<<blocks, threads, 0, st>>>(v, nb[0], nb[1], nb[2], (T *)mn,
+                                                                (T *)mx);
+    else
+        brick_minmax_kernel<T, 8><<<blocks, threads, 0, st>>>(v, nb[0], nb[1], nb[2], (T *)mn,
+                                                               (T *)mx);
+}
+
 cudaError_t launch_brick_minmax(const VolView &v, int B, void *mn, void *mx, cudaStream_t st) {
     int nb[3];
     for (int k = 0; k < 3; ++k) nb[k] = (v.n[k] + B - 1) / B;
-    const unsigned blocks = (unsigned)nb[1] * (unsigned)nb[2];
-    const dim3 threads(BM_TX, BM_TY);
     switch (v.dtype) {
-    case DT_U16:
-        brick_minmax_kernel<uint16_t><<<blocks, threads, 0, st>>>(
-            v, B, nb[0], nb[1], nb[2], (uint16_t *)mn, (uint16_t *)mx);
-        break;
-    case DT_I16:
-        brick_minmax_kernel<int16_t><<<blocks, threads, 0, st>>>(
-            v, B, nb[0], nb[1], nb[2], (int16_t *)mn, (int16_t *)mx);
-        break;
-    default:
-        brick_minmax_kernel<float><<<blocks, threads, 0, st>>>(
-            v, B, nb[0], nb[1], nb[2], (float *)mn, (float *)mx);
+    case DT_U16: launch_minmax_t<uint16_t>(v, B, nb, mn, mx, st); break;
+    case DT_I16: launch_minmax_t<int16_t>(v, B, nb, mn, mx, st); break;
+    default: launch_minmax_t<float>(v, B, nb, mn, mx, st);
     }
     return cudaGetLastError();
 }
