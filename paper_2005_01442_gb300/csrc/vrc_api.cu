@@ -946,6 +946,7 @@ vrc_status vrc_tf_free(vrc_ctx *ctx, int tf_id) {
                 cudaFree(it->second.dist);
                 cudaFree(it->second.scratch);
                 cudaFree(it->second.cells);
+                cudaFree(it->second.aabb);
                 kv.second.occ.erase(it);
             }
         }

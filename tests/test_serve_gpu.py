@@ -203,3 +203,28 @@ def test_launching_server_renders_the_split_render_only(env):
     with pytest.raises(native.VrcError):
         srv.submit(r, o)
     srv.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_close_with_requests_in_flight(env, mode):
+    """Destroying a server while its launch runs and requests are pending returns (the stop
+    flag ends the persistent launch; work already started finishes), and the context stays
+    usable."""
+    torch, R, vids, tids, dims = env
+    from paper_2005_01442_gb300 import serve
+    import time
+    srv = serve.BatchedServer(R, max_slots=16, budget_ms=2000.0, idle_ms=500.0, mode=mode)
+    reqs = _requests(vids, tids, dims, 12, 21)
+    outs = [torch.empty((r.cam.height, r.cam.width, 4), device="cuda") for r in reqs]
+    for r, o in zip(reqs, outs):
+        srv.submit(r, o)
+    srv.pump()
+    t0 = time.time()
+    srv.close()
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30.0
+    r = reqs[0]
+    img = R.render(r.vol_id, r.tf_id, r.cam, step=r.step, ert=r.ert, brick=r.brick)
+    torch.cuda.synchronize()
+    assert torch.isfinite(img).all()
+    assert R.last_device_error() == 0
