@@ -11,7 +11,7 @@
 // empty space), using the forward-box distance field of its direction octant, and inside
 // occupied bricks it skips samples whose cell is transparent (cell mask: all 64 taps in a
 // zero-opacity range). A sample is skipped only when its opacity is exactly zero (leaps keep
-// a margin of LEAP_MARGIN voxels beyond any rounding of the position), so the image is
+// a margin of a few times any rounding of the position, leap_margin), so the image is
 // identical bit for bit with and without skipping.
 #pragma once
 

@@ -607,6 +607,7 @@ vrc_status prepare_render(vrc_ctx *ctx, int vol_id, int tf_id, const vrc_camera 
         L.cwx = (v->n[0] + 1 + 31) / 32;
         L.bricks.B = b.B;
         L.bricks.shift = b.B == 16 ? 4 : 3;
+        L.bricks.margin = leap_margin(v->n);
         for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b.nb[k];
         L.bricks.mn = b.mn;
         L.bricks.mx = b.mx;
@@ -1375,6 +1376,7 @@ extern "C" vrc_status vrc_render_noalloc(vrc_ctx *ctx, int vol_id, int tf_id,
         L.dist = dist;
         L.bricks.B = b->B;
         L.bricks.shift = b->B == 16 ? 4 : 3;
+        L.bricks.margin = leap_margin(v->n);
         for (int k = 0; k < 3; ++k) L.bricks.nb[k] = b->nb[k];
         L.bricks.mn = b->mn;
         L.bricks.mx = b->mx;

@@ -40,6 +40,7 @@ struct BrickView {
     int B, shift;
     int nb[3];
     const void *mn, *mx;
+    float margin;  // leap and quick-skip margin in voxels (leap_margin)
 };
 
 // Device transfer function: rgba[k] and the forward difference rgba[k+1] - rgba[k].
@@ -51,19 +52,27 @@ struct TfView {
 
 // ------------------------------------------------------------------------------------------
 // Leaping (Sec. "Analysis", Pros (b): auxiliary structures to skip empty space). Decisions use
-// float positions and exit distances whose combined error stays below ~1.5e-3 voxel for
-// coordinates up to 4096; a sample is leapt over only when it sits at least LEAP_MARGIN
-// inside a forward box of empty bricks, where its opacity is exactly zero.
-constexpr float LEAP_MARGIN = 4.0e-3f;
+// float positions pa = fma(m, d, P): the entry point P (|P| <= C, the largest extent of the
+// volume), the direction d and m = (j + 1/2) ds (<= the box diagonal, 1.8 C) each rounded once,
+// and the fma once more, so |pa - p| <= 2^-24 (|P| + 2 m + |pa|) < 3.3e-7 C. A sample is leapt
+// over only when it sits at least the margin inside a forward box of empty bricks, where its
+// opacity is exactly zero; the margin is three times that bound (4.1e-3 voxel at C = 4096),
+// and at least 2.5e-4 voxel.
+inline float leap_margin(const int n[3]) {
+    const int c = (n[0] > n[1] ? (n[0] > n[2] ? n[0] : n[2]) : (n[1] > n[2] ? n[1] : n[2])) + 4;
+    const float m = 1.0e-6f * (float)c;
+    return m > 2.5e-4f ? m : 2.5e-4f;
+}
 
 // Leap mode for sample j on the forward-box distance field `dist` of the ray's direction
 // octant. Returns a value > j when sample j and every sample before the returned index lie
-// LEAP_MARGIN inside such a box, or j itself when sample j needs its exact position.
+// the margin inside such a box, or j itself when sample j needs its exact position.
 // cache_lin / cache_r memoise the last brick looked up (start with cache_lin = -1).
 __device__ __forceinline__ int leap_float(const BrickView &bv, const uint8_t *__restrict__ dist,
                                           const float Pf[3], const float df[3],
                                           const float inv_df[3], float step, float inv_step,
                                           int nseg, int j, int &cache_lin, int &cache_r) {
+    const float margin = bv.margin;
     if (j >= nseg - 1) return j;  // the last segment's midpoint is not (j + 1/2) ds
     const float m = ((float)j + 0.5f) * step;
     float pa[3];
@@ -83,19 +92,19 @@ __device__ __forceinline__ int leap_float(const BrickView &bv, const uint8_t *__
     float texit = INFINITY;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        // sample j must sit LEAP_MARGIN inside its own brick (interior faces only)
+        // sample j must sit the margin inside its own brick (interior faces only)
         const float lo = (float)(b[k] * bv.B), hi = lo + (float)bv.B;
-        if ((b[k] > 0 && pa[k] < lo + LEAP_MARGIN) ||
-            (b[k] < bv.nb[k] - 1 && pa[k] > hi - LEAP_MARGIN))
+        if ((b[k] > 0 && pa[k] < lo + margin) ||
+            (b[k] < bv.nb[k] - 1 && pa[k] > hi - margin))
             return j;
         // exit of the empty forward box of extent r - 1 bricks, face moved inward by the margin
         float face;
         if (df[k] > 0.0f) {
             if (b[k] + r >= bv.nb[k]) continue;
-            face = (float)((b[k] + r) * bv.B) - LEAP_MARGIN;
+            face = (float)((b[k] + r) * bv.B) - margin;
         } else if (df[k] < 0.0f) {
             if (b[k] - r + 1 <= 0) continue;
-            face = (float)((b[k] - r + 1) * bv.B) + LEAP_MARGIN;
+            face = (float)((b[k] - r + 1) * bv.B) + margin;
         } else {
             continue;
         }
@@ -445,9 +454,9 @@ __device__ __forceinline__ bool cell_open(const uint32_t *__restrict__ cells, in
     return (w >> (cx & 31)) & 1u;
 }
 
-// Quick skip test of sample j < nseg - 1 from its float position (the leap path's, within
-// ~1.5e-3 voxel of the exact one for coordinates up to 4096). Away from cell faces (by
-// LEAP_MARGIN) the float cell is the exact cell, so the brick and cell tests need no exact
+// Quick skip test of sample j < nseg - 1 from its float position (the leap path's, within a
+// third of the margin of the exact one). Away from cell faces (by the margin) the float cell
+// is the exact cell, so the brick and cell tests need no exact
 // placement: QS_EMPTY_BRICK and QS_CLEAR_CELL mean opacity zero (skip), QS_OPEN means the
 // sample must be resampled; QS_EXACT (near a face) means take the exact position first.
 // Without a cell mask (cells == NULL) only the brick is tested.
@@ -464,7 +473,7 @@ __device__ __forceinline__ int quick_skip(const BrickView &bv, const uint8_t *__
         const float pk = fmaf(m, df[k], Pf[k]);
         const float fl = floorf(pk);
         const float fr = pk - fl;
-        near |= !(fr >= LEAP_MARGIN && fr <= 1.0f - LEAP_MARGIN);
+        near |= !(fr >= bv.margin && fr <= 1.0f - bv.margin);
         c[k] = min(max((int)fl, -1), n[k] - 1);
     }
     if (near) return QS_EXACT;
