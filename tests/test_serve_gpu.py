@@ -228,3 +228,12 @@ def test_close_with_requests_in_flight(env, mode):
     torch.cuda.synchronize()
     assert torch.isfinite(img).all()
     assert R.last_device_error() == 0
+
+
+def test_server_mode_is_checked(env):
+    torch, R, vids, tids, dims = env
+    import ctypes as C
+    srv = C.c_void_p()
+    for mode in (-1, 2, 7):
+        assert R.lib.vrc_server_create_ex(R.ctx, 4, mode, C.byref(srv)) != 0
+        assert not srv.value
